@@ -1,0 +1,243 @@
+/*
+ * diffuse.h -- C-ABI of the GB300 task-and-kernel-fusion runtime.
+ *
+ * The interface follows the paper's statement of the problem (Section 3,
+ * Fig. 2a; Section 4 opening; Section 5.1):
+ *   - applications (array libraries) create STORES -- rectangular arrays -- and
+ *     aliasing VIEWS of them (Section 3.1, Fig. 1a);
+ *   - they describe how each index task sees a store through a PARTITION:
+ *     None (replicated) or an affine Tiling(shape, offset, projection)
+ *     (Section 3.1, Fig. 3);
+ *   - they SUBMIT index tasks: IndexTask(launch domain, [(store, partition,
+ *     privilege)]) with privileges R, W, RW and Rd (Section 3.2);
+ *   - tasks are buffered in a WINDOW; FLUSH (flush_window, Section 5.1) runs
+ *     the fusion pass -- greedy longest fusible prefixes under the
+ *     launch-domain, true-dependence, anti-dependence and reduction
+ *     constraints (Section 4.2, Fig. 5), temporary-store elimination
+ *     (Def. 4) and memoization of isomorphic windows (Section 5.2) -- and
+ *     launches one generated sm_103a kernel per launch group;
+ *   - RELEASE drops the application's reference; stores stay alive while
+ *     pending tasks use them (the split reference count of Section 5.1).
+ *
+ * Conventions
+ *   - Every entry point returns 0 (DFS_OK) on success or a negative dfs_status.
+ *     dfs_last_error() then describes the failure in text.
+ *   - Handles (dfs_store, dfs_partition) are positive integers owned by the
+ *     context; they are never reused within a context.
+ *   - Submission validates shapes, dtypes, partitions and privileges
+ *     synchronously.  Device-side failures (a grid-barrier timeout) are
+ *     deferred and reported by dfs_sync() or dfs_store_read().
+ *   - All device work of a context is ordered on one CUDA stream.
+ *   - A context is not thread-safe: one host thread at a time.
+ *   - Arrays are row-major; shapes and offsets are in elements.
+ */
+#ifndef DIFFUSE_H
+#define DIFFUSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DFS_MAX_DIM 3
+
+typedef struct dfs_ctx dfs_ctx;
+typedef int64_t dfs_store;     /* > 0 */
+typedef int64_t dfs_partition; /* > 0 */
+
+typedef enum {
+  DFS_OK = 0,
+  DFS_ERR_INVALID = -1,         /* bad argument or illegal task */
+  DFS_ERR_NO_DEVICE = -2,       /* operation needs a device; context is analysis-only */
+  DFS_ERR_CUDA = -3,            /* a CUDA runtime/driver call failed */
+  DFS_ERR_COMPILE = -4,         /* NVRTC failed to compile a generated kernel */
+  DFS_ERR_OOM = -5,             /* device allocation failed */
+  DFS_ERR_BARRIER_TIMEOUT = -6, /* a grid barrier gave up waiting (deferred) */
+  DFS_ERR_STATE = -7,           /* handle released / unknown, or wrong call order */
+  DFS_ERR_BUFFER = -8           /* caller's buffer too small (see *needed) */
+} dfs_status;
+
+typedef enum { DFS_F32 = 0, DFS_F64 = 1, DFS_I32 = 2, DFS_I64 = 3 } dfs_dtype;
+
+/* Privileges of Section 3.2; DFS_PRIV_IMM marks an immediate scalar operand. */
+typedef enum {
+  DFS_PRIV_R = 1,
+  DFS_PRIV_W = 2,
+  DFS_PRIV_RW = 3,
+  DFS_PRIV_RD = 4,
+  DFS_PRIV_IMM = 8
+} dfs_privilege;
+
+typedef enum { DFS_REDOP_NONE = 0, DFS_REDOP_SUM = 1 } dfs_redop;
+
+/*
+ * Task bodies (the array libraries' operators; Section 2, Fig. 1e; Section 6,
+ * Fig. 8a).  Operand order of dfs_submit's args:
+ *   unary element-wise   [in0, out]          out[e] = f(in0[e])
+ *   binary element-wise  [in0, in1, out]     out[e] = in0[e] (op) in1[e]
+ *     in* are store args (R) or immediates (DFS_PRIV_IMM); a 0-d store read
+ *     through the None partition broadcasts.  out is W (or RW).  Every store
+ *     operand of one element-wise task has the same floating dtype, and every
+ *     non-0-d operand's sub-store has the same shape at each point.
+ *     Rounding: every operation rounds once to the store dtype (no
+ *     contraction across operations), so a fused window equals the unfused
+ *     stream bit for bit.
+ *     NCDF(x) = 0.5 * (1 + erf(x * (1/sqrt 2))), evaluated in that order.
+ *   DFS_OP_DOT  [x R, y R, out RD(SUM)]   out (+)= sum_e x[e]*y[e]
+ *   DFS_OP_SUM  [x R, out RD(SUM)]        out (+)= sum_e x[e]
+ *     out is a 0-d store through None.  A reduction into a store that holds
+ *     no value yet starts from zero; otherwise it folds into the value.
+ *     The order of summation is fixed (per point, then over points in
+ *     order), so results are reproducible run to run.
+ *   DFS_OP_SPMV [rowptr R, col R, val R, x R, y W]   y = A x, CSR
+ *     rowptr/col are int32, val/x/y one float dtype; rowptr, col, val and x
+ *     are read through None (any row may touch any column); y through a
+ *     1-D Tiling whose sub-store at each point is the block of rows it owns.
+ */
+typedef enum {
+  DFS_OP_COPY = 1,
+  DFS_OP_NEG = 2,
+  DFS_OP_ABS = 3,
+  DFS_OP_EXP = 4,
+  DFS_OP_LOG = 5,
+  DFS_OP_SQRT = 6,
+  DFS_OP_ERF = 7,
+  DFS_OP_NCDF = 8,
+  DFS_OP_ADD = 32,
+  DFS_OP_SUB = 33,
+  DFS_OP_MUL = 34,
+  DFS_OP_DIV = 35,
+  DFS_OP_POW = 36,
+  DFS_OP_MAX = 37,
+  DFS_OP_MIN = 38,
+  DFS_OP_DOT = 64,
+  DFS_OP_SUM = 65,
+  DFS_OP_SPMV = 96
+} dfs_op;
+
+/* One (store, partition, privilege) triple of IndexTask (Fig. 2a), or an
+ * immediate scalar when privilege == DFS_PRIV_IMM (store/partition ignored). */
+typedef struct {
+  dfs_store store;
+  dfs_partition partition;
+  int32_t privilege; /* dfs_privilege */
+  int32_t redop;     /* dfs_redop; DFS_REDOP_SUM with DFS_PRIV_RD */
+  double imm;        /* value of an immediate */
+} dfs_arg;
+
+typedef enum {
+  /* one kernel per fused task (the paper's execution: one task per prefix) */
+  DFS_LAUNCH_PER_TASK = 0,
+  /* all fused tasks of a flush in one cooperative kernel, grid barriers at
+   * the points where the fusion constraints cut (GB300 execution) */
+  DFS_LAUNCH_PERSISTENT = 1
+} dfs_launch_mode;
+
+typedef struct {
+  int32_t device;            /* CUDA ordinal; -1 = analysis-only (no device) */
+  int32_t fusion;            /* 1: the paper's fusion pass; 0: every task alone, no temporaries */
+  int32_t launch_mode;       /* dfs_launch_mode */
+  int32_t window_size;       /* tasks buffered before the window is analysed (>= 1) */
+  void *stream;              /* cudaStream_t to use; NULL = the context creates one */
+  int32_t block_threads;     /* threads per CTA: 128, 256, 512 or 1024 (0 = 256) */
+  int32_t ctas_per_sm;       /* CTAs per SM for grid sizing (0 = occupancy limit) */
+  int32_t unroll;            /* vectors per thread per loop trip, 1..8 (0 = 2) */
+  double barrier_timeout_s;  /* grid-barrier spin limit in seconds (0 = 2.0) */
+  const char *cache_dir;     /* on-disk cubin cache directory, or NULL */
+  /* Test hook (0 = off): in generated kernels CTA 0 does not arrive at grid
+   * barrier number k, so every CTA's wait runs out after barrier_timeout_s
+   * and the launch ends with DFS_ERR_BARRIER_TIMEOUT at the next dfs_sync. */
+  int32_t debug_skip_arrival;
+} dfs_config;
+
+/* Fills *cfg with the defaults above (device 0, fusion on, persistent). */
+void dfs_config_default(dfs_config *cfg);
+
+/* Creates a context.  With device >= 0 the CUDA device is made current and
+ * the NVRTC compiler is loaded.  On failure *out is NULL. */
+int dfs_init(dfs_ctx **out, const dfs_config *cfg);
+
+/* Flushes, synchronizes and frees every resource of the context (library-
+ * owned device memory included; wrapped memory is not freed).  NULL is ok. */
+int dfs_shutdown(dfs_ctx *ctx);
+
+/* Creates a store of `ndim` (0..3) dimensions.  Device memory is owned by the
+ * library and allocated lazily, at the first flush that must materialise the
+ * store; a store that the fusion pass proves temporary is never allocated. */
+int dfs_store_create(dfs_ctx *ctx, int32_t dtype, int32_t ndim, const int64_t *shape,
+                     dfs_store *out);
+
+/* Creates a store over caller-owned device memory (dense, row-major,
+ * 16-byte alignment recommended).  The memory must outlive every task that
+ * uses the store; such a store is never treated as temporary. */
+int dfs_store_wrap(dfs_ctx *ctx, int32_t dtype, int32_t ndim, const int64_t *shape,
+                   void *dev_ptr, dfs_store *out);
+
+/* Creates an aliasing view: the box [offset, offset+shape) of `parent`
+ * (itself possibly a view), as array slicing does (Fig. 1a). */
+int dfs_store_view(dfs_ctx *ctx, dfs_store parent, const int64_t *offset, const int64_t *shape,
+                   dfs_store *out);
+
+/* Drops the application's reference to a store or view.  Memory is freed
+ * once no application reference and no pending task remain. */
+int dfs_store_release(dfs_ctx *ctx, dfs_store s);
+
+/* Copies `bytes` from host memory into a root store (after flushing pending
+ * work; asynchronous with respect to the host for pinned memory). */
+int dfs_store_write(dfs_ctx *ctx, dfs_store s, const void *host_src, size_t bytes);
+
+/* Flushes, then copies the store (root or 1-/2-D view) to host memory and
+ * synchronizes.  Returns any deferred device error. */
+int dfs_store_read(dfs_ctx *ctx, dfs_store s, void *host_dst, size_t bytes);
+
+/* Flushes, materialises the store's root and returns the device address of
+ * the store's first element (for interoperation with other CUDA code). */
+int dfs_store_device_ptr(dfs_ctx *ctx, dfs_store s, void **out);
+
+/* The None partition: every point of the launch domain sees the whole store. */
+int dfs_partition_none(dfs_ctx *ctx, dfs_partition *out);
+
+/* Tiling(tile, offset, proj) (Section 3.1, Fig. 3e): point p of the launch
+ * domain sees [proj(p)*tile, (proj(p)+1)*tile) + offset, clipped to the
+ * store (or view) it is applied to.  proj[d] names the launch-domain
+ * coordinate that drives store dimension d; NULL means the identity. */
+int dfs_partition_tiling(dfs_ctx *ctx, int32_t ndim, const int64_t *tile, const int64_t *offset,
+                         const int32_t *proj, dfs_partition *out);
+
+/* Appends IndexTask(launch_domain, args) to the window (Section 3.2).  When
+ * the window holds `window_size` tasks it is analysed and its complete fused
+ * groups are launched. */
+int dfs_submit(dfs_ctx *ctx, int32_t op, int32_t ndim, const int64_t *launch_domain,
+               int32_t nargs, const dfs_arg *args);
+
+/* flush_window(): analyses and launches every buffered task; asynchronous. */
+int dfs_flush(dfs_ctx *ctx);
+
+/* Waits for the context's stream; returns deferred device errors. */
+int dfs_sync(dfs_ctx *ctx);
+
+/* Text of the last error on this context (empty if none). */
+const char *dfs_last_error(dfs_ctx *ctx);
+
+/* JSON description of how the buffered window would be fused, without
+ * launching it: {"groups": [[task indices]...], "temporaries": [store ids],
+ * "launches": [[group indices]...], "barriers": n, "key": "..."}.
+ * Writes at most len bytes (NUL-terminated) and the full size to *needed. */
+int dfs_plan_json(dfs_ctx *ctx, char *buf, size_t len, size_t *needed);
+
+/* JSON counters: tasks submitted, fused groups, launches, barriers, plan and
+ * kernel cache hits/misses, NVRTC compile seconds, bytes allocated. */
+int dfs_stats_json(dfs_ctx *ctx, char *buf, size_t len, size_t *needed);
+
+/* Source of the generated CUDA for the most recent launch (debugging). */
+int dfs_last_kernel_source(dfs_ctx *ctx, char *buf, size_t len, size_t *needed);
+
+/* ABI version (major*100 + minor). */
+int dfs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DIFFUSE_H */

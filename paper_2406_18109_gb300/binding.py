@@ -1,0 +1,235 @@
+"""ctypes binding of the C-ABI in ``include/diffuse.h`` (argument marshalling only).
+
+Every function keeps the C name and raises :class:`DfsError` on a negative
+status.  The shared library is the in-tree ``_lib/libdiffuse.so`` built by
+``paper_2406_18109_gb300._build.build()``; importing this module does not
+build it, and calling into a missing library raises at once -- there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import json
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libdiffuse.so")
+
+# enums of diffuse.h
+DFS_OK = 0
+STATUS = {0: "DFS_OK", -1: "DFS_ERR_INVALID", -2: "DFS_ERR_NO_DEVICE", -3: "DFS_ERR_CUDA",
+          -4: "DFS_ERR_COMPILE", -5: "DFS_ERR_OOM", -6: "DFS_ERR_BARRIER_TIMEOUT",
+          -7: "DFS_ERR_STATE", -8: "DFS_ERR_BUFFER"}
+DFS_F32, DFS_F64, DFS_I32, DFS_I64 = 0, 1, 2, 3
+DFS_PRIV_R, DFS_PRIV_W, DFS_PRIV_RW, DFS_PRIV_RD, DFS_PRIV_IMM = 1, 2, 3, 4, 8
+DFS_REDOP_NONE, DFS_REDOP_SUM = 0, 1
+DFS_LAUNCH_PER_TASK, DFS_LAUNCH_PERSISTENT = 0, 1
+OPS = {"COPY": 1, "NEG": 2, "ABS": 3, "EXP": 4, "LOG": 5, "SQRT": 6, "ERF": 7, "NCDF": 8,
+       "ADD": 32, "SUB": 33, "MUL": 34, "DIV": 35, "POW": 36, "MAX": 37, "MIN": 38,
+       "DOT": 64, "SUM": 65, "SPMV": 96}
+MAX_DIM = 3
+
+# every symbol include/diffuse.h declares
+EXPORTS = ("dfs_config_default", "dfs_init", "dfs_shutdown", "dfs_store_create", "dfs_store_wrap",
+           "dfs_store_view", "dfs_store_release", "dfs_store_write", "dfs_store_read",
+           "dfs_store_device_ptr", "dfs_partition_none", "dfs_partition_tiling", "dfs_submit",
+           "dfs_flush", "dfs_sync", "dfs_last_error", "dfs_plan_json", "dfs_stats_json",
+           "dfs_last_kernel_source", "dfs_version")
+
+
+class dfs_config(C.Structure):
+    _fields_ = [("device", C.c_int32), ("fusion", C.c_int32), ("launch_mode", C.c_int32),
+                ("window_size", C.c_int32), ("stream", C.c_void_p), ("block_threads", C.c_int32),
+                ("ctas_per_sm", C.c_int32), ("unroll", C.c_int32), ("barrier_timeout_s", C.c_double),
+                ("cache_dir", C.c_char_p), ("debug_skip_arrival", C.c_int32)]
+
+
+class dfs_arg(C.Structure):
+    _fields_ = [("store", C.c_int64), ("partition", C.c_int64), ("privilege", C.c_int32),
+                ("redop", C.c_int32), ("imm", C.c_double)]
+
+
+class DfsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        self.code = code
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+
+
+_lib = None
+
+
+def lib():
+    """The loaded shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run paper_2406_18109_gb300._build.build() first")
+        L = C.CDLL(LIB_PATH)
+        P, I64, I32 = C.c_void_p, C.c_int64, C.c_int32
+        pI64 = C.POINTER(C.c_int64)
+        sig = {
+            "dfs_config_default": (None, [C.POINTER(dfs_config)]),
+            "dfs_init": (C.c_int, [C.POINTER(P), C.POINTER(dfs_config)]),
+            "dfs_shutdown": (C.c_int, [P]),
+            "dfs_store_create": (C.c_int, [P, I32, I32, pI64, pI64]),
+            "dfs_store_wrap": (C.c_int, [P, I32, I32, pI64, P, pI64]),
+            "dfs_store_view": (C.c_int, [P, I64, pI64, pI64, pI64]),
+            "dfs_store_release": (C.c_int, [P, I64]),
+            "dfs_store_write": (C.c_int, [P, I64, P, C.c_size_t]),
+            "dfs_store_read": (C.c_int, [P, I64, P, C.c_size_t]),
+            "dfs_store_device_ptr": (C.c_int, [P, I64, C.POINTER(P)]),
+            "dfs_partition_none": (C.c_int, [P, pI64]),
+            "dfs_partition_tiling": (C.c_int, [P, I32, pI64, pI64, C.POINTER(C.c_int32), pI64]),
+            "dfs_submit": (C.c_int, [P, I32, I32, pI64, I32, C.POINTER(dfs_arg)]),
+            "dfs_flush": (C.c_int, [P]),
+            "dfs_sync": (C.c_int, [P]),
+            "dfs_last_error": (C.c_char_p, [P]),
+            "dfs_plan_json": (C.c_int, [P, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
+            "dfs_stats_json": (C.c_int, [P, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
+            "dfs_last_kernel_source": (C.c_int, [P, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
+            "dfs_version": (C.c_int, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(ctx, rc: int):
+    if rc != DFS_OK:
+        msg = lib().dfs_last_error(ctx).decode() if ctx else ""
+        raise DfsError(rc, msg)
+
+
+def _i64s(vals):
+    vals = list(vals)
+    return (C.c_int64 * max(1, len(vals)))(*vals)
+
+
+# ------------------------------------------------------------------ C names
+def dfs_config_default() -> dfs_config:
+    cfg = dfs_config()
+    lib().dfs_config_default(C.byref(cfg))
+    return cfg
+
+
+def dfs_init(cfg: dfs_config | None = None):
+    ctx = C.c_void_p()
+    rc = lib().dfs_init(C.byref(ctx), C.byref(cfg) if cfg is not None else None)
+    if rc != DFS_OK:
+        raise DfsError(rc, "dfs_init failed")
+    return ctx
+
+
+def dfs_shutdown(ctx) -> None:
+    _check(None, lib().dfs_shutdown(ctx))
+
+
+def dfs_store_create(ctx, dtype: int, shape) -> int:
+    out = C.c_int64()
+    _check(ctx, lib().dfs_store_create(ctx, dtype, len(shape), _i64s(shape), C.byref(out)))
+    return out.value
+
+
+def dfs_store_wrap(ctx, dtype: int, shape, dev_ptr: int) -> int:
+    out = C.c_int64()
+    _check(ctx, lib().dfs_store_wrap(ctx, dtype, len(shape), _i64s(shape), C.c_void_p(dev_ptr), C.byref(out)))
+    return out.value
+
+
+def dfs_store_view(ctx, parent: int, offset, shape) -> int:
+    out = C.c_int64()
+    _check(ctx, lib().dfs_store_view(ctx, parent, _i64s(offset), _i64s(shape), C.byref(out)))
+    return out.value
+
+
+def dfs_store_release(ctx, store: int) -> None:
+    _check(ctx, lib().dfs_store_release(ctx, store))
+
+
+def dfs_store_write(ctx, store: int, host_ptr: int, nbytes: int) -> None:
+    _check(ctx, lib().dfs_store_write(ctx, store, C.c_void_p(host_ptr), nbytes))
+
+
+def dfs_store_read(ctx, store: int, host_ptr: int, nbytes: int) -> None:
+    _check(ctx, lib().dfs_store_read(ctx, store, C.c_void_p(host_ptr), nbytes))
+
+
+def dfs_store_device_ptr(ctx, store: int) -> int:
+    out = C.c_void_p()
+    _check(ctx, lib().dfs_store_device_ptr(ctx, store, C.byref(out)))
+    return out.value or 0
+
+
+def dfs_partition_none(ctx) -> int:
+    out = C.c_int64()
+    _check(ctx, lib().dfs_partition_none(ctx, C.byref(out)))
+    return out.value
+
+
+def dfs_partition_tiling(ctx, tile, offset=None, proj=None) -> int:
+    out = C.c_int64()
+    nd = len(tile)
+    off = _i64s(offset if offset is not None else [0] * nd)
+    pj = (C.c_int32 * nd)(*proj) if proj is not None else None
+    _check(ctx, lib().dfs_partition_tiling(ctx, nd, _i64s(tile), off, pj, C.byref(out)))
+    return out.value
+
+
+def make_args(args) -> C.Array:
+    """args: list of (store, partition, privilege[, redop]) tuples or floats (immediates)."""
+    arr = (dfs_arg * len(args))()
+    for i, a in enumerate(args):
+        if isinstance(a, (int, float)) and not isinstance(a, bool) and not isinstance(a, tuple):
+            arr[i].privilege = DFS_PRIV_IMM
+            arr[i].imm = float(a)
+        else:
+            arr[i].store = a[0]
+            arr[i].partition = a[1]
+            arr[i].privilege = a[2]
+            arr[i].redop = a[3] if len(a) > 3 else (DFS_REDOP_SUM if a[2] == DFS_PRIV_RD else DFS_REDOP_NONE)
+    return arr
+
+
+def dfs_submit(ctx, op, domain, args) -> None:
+    opc = OPS[op] if isinstance(op, str) else int(op)
+    arr = make_args(args)
+    _check(ctx, lib().dfs_submit(ctx, opc, len(domain), _i64s(domain), len(args), arr))
+
+
+def dfs_flush(ctx) -> None:
+    _check(ctx, lib().dfs_flush(ctx))
+
+
+def dfs_sync(ctx) -> None:
+    _check(ctx, lib().dfs_sync(ctx))
+
+
+def dfs_last_error(ctx) -> str:
+    return lib().dfs_last_error(ctx).decode()
+
+
+def _json_call(fn, ctx) -> str:
+    need = C.c_size_t(0)
+    fn(ctx, None, 0, C.byref(need))
+    buf = C.create_string_buffer(need.value + 1)
+    _check(ctx, fn(ctx, buf, need.value + 1, C.byref(need)))
+    return buf.value.decode()
+
+
+def dfs_plan_json(ctx) -> dict:
+    return json.loads(_json_call(lib().dfs_plan_json, ctx))
+
+
+def dfs_stats_json(ctx) -> dict:
+    return json.loads(_json_call(lib().dfs_stats_json, ctx))
+
+
+def dfs_last_kernel_source(ctx) -> str:
+    return _json_call(lib().dfs_last_kernel_source, ctx)
+
+
+def dfs_version() -> int:
+    return lib().dfs_version()

@@ -1,0 +1,676 @@
+// codegen.cpp -- CUDA source for one launch group.
+//
+// The fused task body is the composition of the task bodies in program order
+// (Section 4.2.2); loops of consecutive tasks with the same iteration space
+// are fused and their temporaries become registers (Section 6.3, Fig. 8:
+// compose, eliminate temporaries, fuse and parallelise loops, remove local
+// allocations).  On the GPU:
+//   * the launch domain is the set of work units (points); CTAs take points
+//     in grid-stride order, so a fused group needs no communication between
+//     CTAs (the fusion constraints guarantee point-wise dependencies);
+//   * a launch holding several fused groups (persistent mode) separates them
+//     by grid barriers wherever the previous group was not a replicated
+//     scalar group; scalar groups (all stores 0-d) run redundantly in every
+//     CTA on register copies of the 0-d values;
+//   * reductions keep one partial per point, finished in a fixed order after
+//     the next barrier (or by the last CTA to exit), so every result is
+//     reproducible and identical between fused and unfused execution.
+// Every shape, tile and offset is a compile-time constant of the generated
+// source; pointers and immediate values are kernel parameters, so isomorphic
+// windows share one compiled kernel (Section 5.2).
+#include <algorithm>
+#include <cstdio>
+#include <functional>
+#include <sstream>
+#include <stdexcept>
+
+#include "runtime.hpp"
+
+namespace dfs {
+
+size_t dtype_size(int dt) {
+  switch (dt) {
+    case DFS_F32: return 4;
+    case DFS_F64: return 8;
+    case DFS_I32: return 4;
+    case DFS_I64: return 8;
+  }
+  return 0;
+}
+const char* dtype_cname(int dt) {
+  switch (dt) {
+    case DFS_F32: return "float";
+    case DFS_F64: return "double";
+    case DFS_I32: return "int";
+    case DFS_I64: return "long long";
+  }
+  return "void";
+}
+bool dtype_is_float(int dt) { return dt == DFS_F32 || dt == DFS_F64; }
+
+namespace {
+
+const char* op_fn(int op) {
+  switch (op) {
+    case DFS_OP_COPY: return "op_copy";
+    case DFS_OP_NEG: return "op_neg";
+    case DFS_OP_ABS: return "op_abs";
+    case DFS_OP_EXP: return "op_exp";
+    case DFS_OP_LOG: return "op_log";
+    case DFS_OP_SQRT: return "op_sqrt";
+    case DFS_OP_ERF: return "op_erf";
+    case DFS_OP_NCDF: return "op_ncdf";
+    case DFS_OP_ADD: return "op_add";
+    case DFS_OP_SUB: return "op_sub";
+    case DFS_OP_MUL: return "op_mul";
+    case DFS_OP_DIV: return "op_div";
+    case DFS_OP_POW: return "op_pow";
+    case DFS_OP_MAX: return "op_max";
+    case DFS_OP_MIN: return "op_min";
+  }
+  return nullptr;
+}
+
+bool is_elementwise(int op) { return op_fn(op) != nullptr; }
+bool is_reduction(int op) { return op == DFS_OP_DOT || op == DFS_OP_SUM; }
+
+// The argument whose sub-store drives the task's loop.
+const Arg& space_arg(const Task& t) {
+  if (is_reduction(t.op)) return t.args[0];
+  if (t.op == DFS_OP_SPMV) return t.args[4];
+  return t.args.back();
+}
+
+std::string akey(const Arg& a) { return std::to_string(a.root) + "@" + a.part.key(); }
+
+struct Nest {
+  int first, last;  // task indices [first, last)
+  int dims;         // 1 (flat) or 2 (row loop)
+  int vec;          // elements per vector access
+};
+
+class Gen {
+ public:
+  explicit Gen(const LaunchSpec& s) : S(s) {}
+
+  KernelCode run();
+
+ private:
+  const LaunchSpec& S;
+  std::ostringstream o;
+  KernelCode kc;
+  std::map<int64_t, int> ptr_of;          // root -> pointer param index
+  std::map<int64_t, std::string> sreg;    // 0-d root -> register name
+  std::map<int64_t, bool> have;           // 0-d root holds a value in registers
+  struct Red { int slot; int64_t root; int dtype; int64_t points; };
+  std::vector<Red> pending_red;           // reductions awaiting finalisation
+  int nbar = 0;
+
+  const LaunchRoot& R(int64_t root) const { return S.roots[S.root_index.at(root)]; }
+  bool temp_in(int g, int64_t root) const;
+  std::string ptr(int64_t root) const { return "r" + std::to_string(ptr_of.at(root)); }
+  std::string T(int dt) const { return dtype_cname(dt); }
+
+  void emit_params();
+  void emit_prologue();
+  void emit_group(int g);
+  void emit_scalar_group(int g);
+  void emit_vector_group(int g);
+  void emit_nest(int g, const Nest& n, const std::string& red_pt);
+  void emit_finalise(const char* indent);
+  std::vector<Nest> nests_of(int g);
+  std::string imm_expr(int task, int arg, int dt);
+};
+
+bool Gen::temp_in(int g, int64_t root) const {
+  (void)g;
+  const LaunchRoot& r = R(root);
+  return r.temp;
+}
+
+std::string Gen::imm_expr(int task, int arg, int dt) {
+  const int k = kc.nimm++;
+  kc.imms.push_back(S.tasks[task].args[arg].immv);
+  kc.imm_src.push_back({task, arg});
+  return "((" + T(dt) + ")P.imm[" + std::to_string(k) + "])";
+}
+
+void Gen::emit_params() {
+  // pointer params: every root with memory
+  for (const LaunchRoot& r : S.roots) {
+    if (r.param < 0) continue;
+    ptr_of[r.root] = r.param;
+  }
+  kc.nptr = 0;
+  for (const LaunchRoot& r : S.roots)
+    if (r.param >= 0) kc.nptr = std::max(kc.nptr, r.param + 1);
+  kc.ptr_roots.assign(kc.nptr, 0);
+  for (const LaunchRoot& r : S.roots)
+    if (r.param >= 0) kc.ptr_roots[r.param] = r.root;
+}
+
+void Gen::emit_prologue() {
+  // typed root pointers
+  for (const LaunchRoot& r : S.roots) {
+    if (r.param < 0) continue;
+    o << "  " << T(r.dtype) << "* __restrict__ " << ptr(r.root) << " = (" << T(r.dtype) << "*)P.p["
+      << r.param << "];\n";
+  }
+  // 0-d registers
+  int k = 0;
+  for (const LaunchRoot& r : S.roots) {
+    if (!r.zero_d) continue;
+    const std::string nm = "s" + std::to_string(k++);
+    sreg[r.root] = nm;
+    const bool load = r.valid_before && r.param >= 0;
+    o << "  " << T(r.dtype) << " " << nm << " = " << (load ? "ld(" + ptr(r.root) + ")" : T(r.dtype) + "(0)")
+      << ";\n";
+    have[r.root] = load;
+  }
+}
+
+std::vector<Nest> Gen::nests_of(int g) {
+  const Group& G = S.groups[g];
+  std::vector<Nest> v;
+  int i = G.begin;
+  while (i < G.end) {
+    const std::string key = iteration_space_key(S.tasks[i]);
+    int j = i + 1;
+    while (j < G.end && iteration_space_key(S.tasks[j]) == key) ++j;
+    Nest n;
+    n.first = i;
+    n.last = j;
+    // dimensionality and vector width
+    const Arg& sa = space_arg(S.tasks[i]);
+    const int nd = sa.nd;
+    // collapse a 2-D space into a flat one when every access spans whole root rows
+    bool flat = nd <= 1;
+    if (nd == 2) {
+      flat = true;
+      for (int t = i; t < j && flat; ++t)
+        for (const Arg& a : S.tasks[t].args) {
+          if (a.imm || a.nd == 0) continue;
+          if (S.tasks[t].op == DFS_OP_SPMV && &a != &S.tasks[t].args[4]) continue;
+          const LaunchRoot& r = R(a.root);
+          if (a.part.kind != 1 || a.part.vlo[1] != 0 || a.part.vhi[1] != r.shape[1] ||
+              a.part.off[1] > 0 || a.part.tile[1] < r.shape[1])
+            flat = false;
+        }
+    }
+    if (nd > 2) throw std::runtime_error("3-D element-wise iteration spaces are not supported");
+    n.dims = flat ? 1 : 2;
+    // widest element over the memory accesses of the nest
+    size_t esz = 0;
+    bool aligned = true;
+    for (int t = i; t < j; ++t) {
+      const Task& tk = S.tasks[t];
+      for (size_t ai = 0; ai < tk.args.size(); ++ai) {
+        const Arg& a = tk.args[ai];
+        if (a.imm || a.nd == 0) continue;
+        if (tk.op == DFS_OP_SPMV && ai != 4) continue;  // gathered, not streamed
+        esz = std::max(esz, dtype_size(a.dtype));
+      }
+    }
+    int vec = esz ? (int)(16 / esz) : 1;
+    for (int t = i; t < j && vec > 1; ++t) {
+      const Task& tk = S.tasks[t];
+      for (size_t ai = 0; ai < tk.args.size(); ++ai) {
+        const Arg& a = tk.args[ai];
+        if (a.imm || a.nd == 0) continue;
+        if (tk.op == DFS_OP_SPMV && ai != 4) continue;
+        const LaunchRoot& r = R(a.root);
+        if ((int)(16 / dtype_size(a.dtype)) != vec) aligned = false;
+        if (!r.temp && !r.aligned16) aligned = false;
+        if (n.dims == 1) {
+          for (int d = 0; d < a.nd; ++d) {
+            const int64_t st = r.stride[d];
+            if ((a.part.tile[d] * st) % vec || (a.part.off[d] * st) % vec || (a.part.vlo[d] * st) % vec)
+              aligned = false;
+          }
+        } else {
+          if (r.stride[0] % vec || a.part.tile[1] % vec || a.part.off[1] % vec || a.part.vlo[1] % vec ||
+              (a.part.vhi[1] - a.part.vlo[1]) % vec)
+            aligned = false;
+        }
+      }
+    }
+    n.vec = aligned ? vec : 1;
+    v.push_back(n);
+    i = j;
+  }
+  return v;
+}
+
+void Gen::emit_group(int g) {
+  if (S.groups[g].scalar)
+    emit_scalar_group(g);
+  else
+    emit_vector_group(g);
+}
+
+// A group of scalar tasks: every thread of every CTA evaluates it on the
+// register copies of the 0-d stores.
+void Gen::emit_scalar_group(int g) {
+  const Group& G = S.groups[g];
+  o << "    { // group " << g << " (scalar, replicated)\n";
+  for (int i = G.begin; i < G.end; ++i) {
+    const Task& t = S.tasks[i];
+    const Arg& out = t.args.back();
+    const int dt = out.dtype;
+    std::vector<std::string> ins;
+    for (size_t k = 0; k + 1 < t.args.size(); ++k) {
+      const Arg& a = t.args[k];
+      if (a.imm) ins.push_back(imm_expr(i, (int)k, dt));
+      else ins.push_back("(" + T(dt) + ")" + sreg.at(a.root));
+    }
+    o << "      " << sreg.at(out.root) << " = " << op_fn(t.op) << "(";
+    for (size_t k = 0; k < ins.size(); ++k) o << (k ? ", " : "") << ins[k];
+    o << ");\n";
+    have[out.root] = true;
+  }
+  o << "    }\n";
+}
+
+void Gen::emit_vector_group(int g) {
+  const Group& G = S.groups[g];
+  const Task& t0 = S.tasks[G.begin];
+  const int64_t npts = t0.npoints();
+  kc.max_points = std::max(kc.max_points, npts);
+  std::vector<Nest> nests = nests_of(g);
+  o << "    { // group " << g << ": tasks " << G.begin << ".." << G.end - 1 << ", " << nests.size()
+    << " loop nest(s), " << npts << " points\n";
+  o << "      for (i64 pt = blockIdx.x; pt < " << npts << "LL; pt += gridDim.x) {\n";
+  // point coordinates
+  {
+    int64_t rem = 1;
+    for (int d = t0.dnd - 1; d >= 0; --d) {
+      o << "        const i64 q" << d << " = (pt / " << rem << "LL) % " << t0.dom[d] << "LL;\n";
+      rem *= t0.dom[d];
+    }
+  }
+  for (size_t k = 0; k < nests.size(); ++k) {
+    if (k) o << "        __syncthreads();\n";
+    emit_nest(g, nests[k], "pt");
+  }
+  o << "      }\n";
+  o << "    }\n";
+}
+
+void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar) {
+  const int BD = S.block;
+  const int U = std::max(1, S.unroll);
+  const int V = n.vec;
+  const Task& first = S.tasks[n.first];
+  const Arg& sa = space_arg(first);
+  const int nd = sa.nd;
+  const std::string ind = "        ";
+  o << ind << "{ // nest: tasks " << n.first << ".." << n.last - 1 << ", vec " << V << ", "
+    << (n.dims == 1 ? "flat" : "rows") << "\n";
+  // ---- per-access base offsets (root coordinates flattened)
+  std::map<std::string, std::string> base;  // akey -> base variable
+  int nb = 0;
+  auto box_lo = [&](const Arg& a, int d) {
+    std::ostringstream s;
+    if (a.part.kind == 0) {
+      s << a.part.vlo[d] << "LL";
+    } else {
+      s << "max(q" << a.part.proj[d] << " * " << a.part.tile[d] << "LL + (" << a.part.off[d] << "LL), "
+        << a.part.vlo[d] << "LL)";
+    }
+    return s.str();
+  };
+  auto need_base = [&](const Arg& a) {
+    const std::string k = akey(a);
+    if (base.count(k)) return base[k];
+    const std::string nm = "b" + std::to_string(nb++);
+    const LaunchRoot& r = R(a.root);
+    o << ind << "  const i64 " << nm << " = ";
+    for (int d = 0; d < a.nd; ++d) o << (d ? " + " : "") << "(" << box_lo(a, d) << ") * " << r.stride[d] << "LL";
+    if (a.nd == 0) o << "0";
+    o << ";\n";
+    base[k] = nm;
+    return nm;
+  };
+  // ---- extents of the iteration space
+  for (int d = 0; d < nd; ++d) {
+    if (sa.part.kind == 0) {
+      o << ind << "  const i64 ext" << d << " = " << (sa.part.vhi[d] - sa.part.vlo[d]) << "LL;\n";
+    } else {
+      o << ind << "  const i64 ext" << d << " = min(q" << sa.part.proj[d] << " * " << sa.part.tile[d]
+        << "LL + (" << sa.part.off[d] << "LL) + " << sa.part.tile[d] << "LL, " << sa.part.vhi[d]
+        << "LL) - max(q" << sa.part.proj[d] << " * " << sa.part.tile[d] << "LL + (" << sa.part.off[d]
+        << "LL), " << sa.part.vlo[d] << "LL);\n";
+    }
+  }
+  // ---- classify accesses
+  // reads from memory: distinct (root, partition) read before any in-nest write of it
+  struct Rd { std::string key; const Arg* a; std::string var; bool ro; };
+  std::vector<Rd> reads;
+  std::map<std::string, int> read_idx;
+  std::set<std::string> written_keys;
+  // reduction accumulators
+  struct Acc { int task; int slot; std::string var; int dt; };
+  std::vector<Acc> accs;
+  for (int i = n.first; i < n.last; ++i) {
+    const Task& t = S.tasks[i];
+    for (size_t ai = 0; ai < t.args.size(); ++ai) {
+      const Arg& a = t.args[ai];
+      if (a.imm || a.nd == 0) continue;
+      if (t.op == DFS_OP_SPMV && ai != 4) continue;
+      const std::string k = akey(a);
+      if (a.is_r() && !(t.op != DFS_OP_SPMV && is_elementwise(t.op) && ai + 1 == t.args.size())) {
+        if (!written_keys.count(k) && !read_idx.count(k)) {
+          read_idx[k] = (int)reads.size();
+          const LaunchRoot& r = R(a.root);
+          reads.push_back({k, &a, "m" + std::to_string(reads.size()), !r.written});
+          need_base(a);
+        }
+      }
+      const bool is_out = (is_elementwise(t.op) && ai + 1 == t.args.size()) || (t.op == DFS_OP_SPMV && ai == 4);
+      if (is_out) {
+        written_keys.insert(k);
+        if (!R(a.root).temp) need_base(a);
+      }
+    }
+    if (is_reduction(t.op)) {
+      const Arg& out = t.args.back();
+      Acc ac;
+      ac.task = i;
+      ac.slot = kc.nred++;
+      ac.var = "acc" + std::to_string(ac.slot);
+      ac.dt = out.dtype;
+      accs.push_back(ac);
+      kc.red_points.push_back(t.npoints());
+      pending_red.push_back({ac.slot, out.root, out.dtype, t.npoints()});
+      o << ind << "  " << T(ac.dt) << " " << ac.var << " = " << T(ac.dt) << "(0);\n";
+    }
+  }
+  // SpMV gathered operands: bases of rowptr/col/val/x (None partitions)
+  for (int i = n.first; i < n.last; ++i) {
+    const Task& t = S.tasks[i];
+    if (t.op != DFS_OP_SPMV) continue;
+    for (int ai = 0; ai < 4; ++ai) need_base(t.args[ai]);
+  }
+  // immediates hoisted once per nest
+  std::map<std::pair<int, int>, std::string> immv;
+  for (int i = n.first; i < n.last; ++i) {
+    const Task& t = S.tasks[i];
+    const int dt = t.args.back().dtype;
+    for (size_t ai = 0; ai < t.args.size(); ++ai) {
+      const Arg& a = t.args[ai];
+      if (!a.imm) continue;
+      const std::string nm = "k" + std::to_string(i) + "_" + std::to_string(ai);
+      o << ind << "  const " << T(dt) << " " << nm << " = " << imm_expr(i, (int)ai, dt) << ";\n";
+      immv[{i, (int)ai}] = nm;
+    }
+  }
+
+  // ---- body generator for one element group: `u` unroll slot, lanes V,
+  // element offset expression `eoff` (flat) or (row, col) expressions
+  auto addr = [&](const Arg& a, const std::string& e_flat, const std::string& row, const std::string& col) {
+    const LaunchRoot& r = R(a.root);
+    if (n.dims == 1) return ptr(a.root) + " + " + base.at(akey(a)) + " + " + e_flat;
+    return ptr(a.root) + " + " + base.at(akey(a)) + " + (" + row + ") * " + std::to_string(r.stride[0]) + "LL + " + col;
+  };
+  // emits loads for slot u (vector width w), compute, stores; returns nothing
+  auto body = [&](int w, const std::vector<std::string>& slots, const std::vector<std::string>& eflat,
+                  const std::vector<std::string>& erow, const std::vector<std::string>& ecol,
+                  const std::string& pad) {
+    const int ns = (int)slots.size();
+    // loads
+    for (int s = 0; s < ns; ++s) {
+      for (const Rd& rd : reads) {
+        const Arg& a = *rd.a;
+        const std::string ad = addr(a, eflat[s], erow[s], ecol[s]);
+        const std::string v = rd.var + "_" + slots[s];
+        if (w == 4 && a.dtype == DFS_F32) {
+          o << pad << "const f32x4 " << v << " = " << (rd.ro ? "ld4ro(" : "ld4(") << ad << ");\n";
+        } else if (w == 2 && a.dtype == DFS_F64) {
+          o << pad << "const f64x2 " << v << " = " << (rd.ro ? "ld2ro(" : "ld2(") << ad << ");\n";
+        } else {
+          o << pad << "const " << T(a.dtype) << " " << v << " = " << (rd.ro ? "ldro(" : "ld(") << ad << ");\n";
+        }
+      }
+    }
+    // compute: per slot, per lane
+    std::map<std::string, std::vector<std::string>> outvars;  // akey -> per (slot*w+lane) value
+    for (int s = 0; s < ns; ++s) {
+      std::map<std::string, std::string> fwd;  // akey -> lane-0 var prefix (per lane suffix)
+      for (int l = 0; l < w; ++l) {
+        std::map<std::string, std::string> cur;  // akey -> value expr for this lane
+        for (const Rd& rd : reads) {
+          const std::string v = rd.var + "_" + slots[s];
+          cur[rd.key] = (w > 1) ? v + ".v[" + std::to_string(l) + "]" : v;
+        }
+        for (int i = n.first; i < n.last; ++i) {
+          const Task& t = S.tasks[i];
+          const int dt = t.args.back().dtype;
+          auto val = [&](size_t ai) -> std::string {
+            const Arg& a = t.args[ai];
+            if (a.imm) return immv.at({i, (int)ai});
+            if (a.nd == 0) return "(" + T(dt) + ")" + sreg.at(a.root);
+            return cur.at(akey(a));
+          };
+          const std::string res = "v" + std::to_string(i) + "_" + slots[s] + "_" + std::to_string(l);
+          if (is_elementwise(t.op)) {
+            o << pad << "const " << T(dt) << " " << res << " = " << op_fn(t.op) << "(" << val(0);
+            if (t.args.size() == 3) o << ", " << val(1);
+            o << ");\n";
+            cur[akey(t.args.back())] = res;
+          } else if (t.op == DFS_OP_SPMV) {
+            const Arg& y = t.args[4];
+            const std::string row = "(" + base.at(akey(y)) + " - " + std::to_string(y.part.vlo[0]) + "LL + " +
+                                    eflat[s] + " + " + std::to_string(l) + ")";
+            o << pad << "const " << T(dt) << " " << res << " = spmv_row<" << T(dt) << ">(" << ptr(t.args[0].root)
+              << " + " << base.at(akey(t.args[0])) << ", " << ptr(t.args[1].root) << " + "
+              << base.at(akey(t.args[1])) << ", " << ptr(t.args[2].root) << " + " << base.at(akey(t.args[2]))
+              << ", " << ptr(t.args[3].root) << " + " << base.at(akey(t.args[3])) << ", " << row << ");\n";
+            cur[akey(y)] = res;
+          } else if (is_reduction(t.op)) {
+            const Acc* ac = nullptr;
+            for (const Acc& x : accs)
+              if (x.task == i) ac = &x;
+            if (t.op == DFS_OP_DOT)
+              o << pad << ac->var << " = red_fma(" << val(0) << ", " << val(1) << ", " << ac->var << ");\n";
+            else
+              o << pad << ac->var << " = " << ac->var << " + " << val(0) << ";\n";
+          }
+        }
+        // collect outputs to store
+        for (int i = n.first; i < n.last; ++i) {
+          const Task& t = S.tasks[i];
+          const Arg* out = nullptr;
+          if (is_elementwise(t.op)) out = &t.args.back();
+          if (t.op == DFS_OP_SPMV) out = &t.args[4];
+          if (!out || R(out->root).temp) continue;
+          const std::string k = akey(*out);
+          auto& vv = outvars[k];
+          if (vv.size() < (size_t)(ns * w)) vv.resize(ns * w);
+          vv[s * w + l] = cur.at(k);
+        }
+      }
+    }
+    // stores (the last value written to each (root, partition) in the nest)
+    for (auto& kv : outvars) {
+      const Arg* a = nullptr;
+      for (int i = n.first; i < n.last && !a; ++i) {
+        const Task& t = S.tasks[i];
+        for (size_t ai = 0; ai < t.args.size(); ++ai)
+          if (!t.args[ai].imm && akey(t.args[ai]) == kv.first) a = &t.args[ai];
+      }
+      for (int s = 0; s < ns; ++s) {
+        const std::string ad = addr(*a, eflat[s], erow[s], ecol[s]);
+        if (w == 4 && a->dtype == DFS_F32) {
+          o << pad << "st4(" << ad << ", f32x4{{" << kv.second[s * w] << ", " << kv.second[s * w + 1] << ", "
+            << kv.second[s * w + 2] << ", " << kv.second[s * w + 3] << "}});\n";
+        } else if (w == 2 && a->dtype == DFS_F64) {
+          o << pad << "st2(" << ad << ", f64x2{{" << kv.second[s * w] << ", " << kv.second[s * w + 1] << "}});\n";
+        } else {
+          o << pad << "*(" << ad << ") = " << kv.second[s * w] << ";\n";
+        }
+      }
+    }
+  };
+
+  if (n.dims == 1) {
+    // flat: n elements; vectors of V; main loop unrolled U
+    o << ind << "  const i64 n = ";
+    for (int d = 0; d < nd; ++d) o << (d ? " * " : "") << "ext" << d;
+    o << ";\n";
+    o << ind << "  if (n > 0) {\n";
+    if (V > 1) {
+      o << ind << "    const i64 nv = n / " << V << ";\n";
+      o << ind << "    i64 v = threadIdx.x;\n";
+      if (U > 1) {
+        o << ind << "    for (; v + " << (U - 1) * BD << " < nv; v += " << U * BD << ") {\n";
+        std::vector<std::string> sl, ef, er, ec;
+        for (int u = 0; u < U; ++u) {
+          sl.push_back("u" + std::to_string(u));
+          ef.push_back("(v + " + std::to_string(u * BD) + ") * " + std::to_string(V));
+          er.push_back("");
+          ec.push_back("");
+        }
+        body(V, sl, ef, er, ec, ind + "      ");
+        o << ind << "    }\n";
+      }
+      o << ind << "    for (; v < nv; v += " << BD << ") {\n";
+      body(V, {"r"}, {"v * " + std::to_string(V)}, {""}, {""}, ind + "      ");
+      o << ind << "    }\n";
+      o << ind << "    for (i64 e = nv * " << V << " + threadIdx.x; e < n; e += " << BD << ") {\n";
+      body(1, {"t"}, {"e"}, {""}, {""}, ind + "      ");
+      o << ind << "    }\n";
+    } else {
+      o << ind << "    i64 e = threadIdx.x;\n";
+      if (U > 1) {
+        o << ind << "    for (; e + " << (U - 1) * BD << " < n; e += " << U * BD << ") {\n";
+        std::vector<std::string> sl, ef, er, ec;
+        for (int u = 0; u < U; ++u) {
+          sl.push_back("u" + std::to_string(u));
+          ef.push_back("(e + " + std::to_string(u * BD) + ")");
+          er.push_back("");
+          ec.push_back("");
+        }
+        body(1, sl, ef, er, ec, ind + "      ");
+        o << ind << "    }\n";
+      }
+      o << ind << "    for (; e < n; e += " << BD << ") {\n";
+      body(1, {"t"}, {"e"}, {""}, {""}, ind + "      ");
+      o << ind << "    }\n";
+    }
+    o << ind << "  }\n";
+  } else {
+    // rows: each row of ext1 elements is swept by the whole block
+    o << ind << "  for (i64 i = 0; i < ext0; ++i) {\n";
+    if (V > 1) {
+      o << ind << "    const i64 nv = ext1 / " << V << ";\n";
+      o << ind << "    for (i64 v = threadIdx.x; v < nv; v += " << BD << ") {\n";
+      body(V, {"r"}, {""}, {"i"}, {"v * " + std::to_string(V)}, ind + "      ");
+      o << ind << "    }\n";
+    } else {
+      o << ind << "    i64 j = threadIdx.x;\n";
+      if (U > 1) {
+        o << ind << "    for (; j + " << (U - 1) * BD << " < ext1; j += " << U * BD << ") {\n";
+        std::vector<std::string> sl, ef, er, ec;
+        for (int u = 0; u < U; ++u) {
+          sl.push_back("u" + std::to_string(u));
+          ef.push_back("");
+          er.push_back("i");
+          ec.push_back("(j + " + std::to_string(u * BD) + ")");
+        }
+        body(1, sl, ef, er, ec, ind + "      ");
+        o << ind << "    }\n";
+      }
+      o << ind << "    for (; j < ext1; j += " << BD << ") {\n";
+      body(1, {"t"}, {""}, {"i"}, {"j"}, ind + "      ");
+      o << ind << "    }\n";
+    }
+    o << ind << "  }\n";
+  }
+  // per-point partials of the reductions
+  for (const Acc& ac : accs) {
+    o << ind << "  { const " << T(ac.dt) << " tot = block_sum(" << ac.var << ", (" << T(ac.dt) << "*)red_buf);\n";
+    o << ind << "    if (threadIdx.x == 0) ((" << T(ac.dt) << "*)P.partials)[" << ac.slot << "LL * P.red_stride + "
+      << ptvar << "] = tot; }\n";
+  }
+  o << ind << "}\n";
+  (void)g;
+}
+
+// Finishes every pending reduction: sum of the per-point partials in point
+// order, folded into the register copy of the target.
+void Gen::emit_finalise(const char* ind) {
+  for (const Red& r : pending_red) {
+    const std::string nm = sreg.at(r.root);
+    o << ind << "{ const " << T(r.dtype) << " tot = sum_partials((const " << T(r.dtype) << "*)P.partials + "
+      << r.slot << "LL * P.red_stride, " << r.points << "LL);\n";
+    if (have[r.root])
+      o << ind << "  " << nm << " = op_add(" << nm << ", tot); }\n";
+    else
+      o << ind << "  " << nm << " = tot; }\n";
+    have[r.root] = true;
+  }
+  pending_red.clear();
+}
+
+KernelCode Gen::run() {
+  emit_params();
+  std::ostringstream body;
+  // the kernel body is generated into `o`; header assembled afterwards
+  o << "  __shared__ double red_buf[" << S.block / 32 << "];\n";
+  o << "  Ctl* ctl = P.ctl;\n";
+  emit_prologue();
+  o << "  do {\n";
+  for (int g = 0; g < (int)S.groups.size(); ++g) {
+    if (g > 0 && !S.groups[g - 1].scalar) {
+      ++nbar;
+      o << "    if (!grid_barrier(ctl, " << nbar << "u, P.timeout_ns"
+        << (S.debug_skip == nbar ? ", blockIdx.x != 0" : "") << ")) break;\n";
+      emit_finalise("    ");
+    }
+    emit_group(g);
+  }
+  o << "  } while (0);\n";
+  o << "  if (last_cta(ctl)) {\n";
+  if (!pending_red.empty()) {
+    o << "    if (ld_relaxed_int(&ctl->err) == 0) {\n";
+    emit_finalise("      ");
+    o << "    }\n";
+  }
+  o << "    if (threadIdx.x == 0) {\n";
+  for (const LaunchRoot& r : S.roots) {
+    if (!r.zero_d || !r.live_out || r.param < 0) continue;
+    o << "      *" << ptr(r.root) << " = " << sreg.at(r.root) << ";\n";
+  }
+  o << "    }\n";
+  o << "    ctl_reset(ctl);\n";
+  o << "  }\n";
+  kc.nbarriers = nbar;
+
+  std::ostringstream src;
+  src << "#include \"dfs_device.cuh\"\nusing namespace dfs;\n";
+  src << "struct Params {\n  void* p[" << std::max(1, kc.nptr) << "];\n  double imm[" << std::max(1, kc.nimm)
+      << "];\n  void* partials;\n  Ctl* ctl;\n  u64 timeout_ns;\n  i64 red_stride;\n};\n";
+  const std::string body_s = o.str();
+  const size_t h = std::hash<std::string>{}(body_s);
+  char nm[64];
+  snprintf(nm, sizeof nm, "dfs_k%016zx", h);
+  kc.name = nm;
+  src << "extern \"C\" __global__ void __launch_bounds__(" << S.block << ") " << kc.name
+      << "(const __grid_constant__ Params P) {\n"
+      << body_s << "}\n";
+  kc.source = src.str();
+  kc.key = kc.source;
+  int64_t stride = 1;
+  for (int64_t p : kc.red_points) stride = std::max(stride, p);
+  kc.partial_bytes = (size_t)kc.nred * (size_t)stride * 8;
+  return kc;
+}
+
+}  // namespace
+
+KernelCode generate(const LaunchSpec& spec) {
+  Gen g(spec);
+  return g.run();
+}
+
+}  // namespace dfs

@@ -1,0 +1,252 @@
+// dfs_device.cuh -- per-operator device templates composed by the code
+// generator into one sm_103a kernel per launch group.
+//
+// The paper builds a fused task body by composing the bodies of the tasks of
+// a fusible prefix in program order, then fusing their loops and keeping the
+// temporaries local (Section 6.3, Fig. 8).  Here each task body is one of the
+// device functions below applied to one element (or one CSR row); the
+// generator emits one loop nest per run of tasks with the same iteration
+// space, in which temporaries are registers.
+//
+// Rounding: every element operation rounds once to its dtype through the
+// explicitly rounded intrinsics (__fadd_rn, __dmul_rn, ...).  The compiler
+// never contracts those into FMAs, so a fused kernel computes exactly what
+// the unfused kernels compute through memory.  Library math functions
+// (expf, logf, erff, ...) are called, never re-implemented.
+//
+// This file is embedded in the library and handed to NVRTC; it is also
+// compiled by nvcc at build time as a syntax and target check.
+#pragma once
+
+namespace dfs {
+
+typedef long long i64;
+typedef unsigned long long u64;
+typedef unsigned int u32;
+
+// ---------------------------------------------------------------- element ops
+__device__ __forceinline__ float op_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double op_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float op_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double op_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float op_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double op_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float op_div(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double op_div(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float op_pow(float a, float b) { return powf(a, b); }
+__device__ __forceinline__ double op_pow(double a, double b) { return pow(a, b); }
+__device__ __forceinline__ float op_max(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double op_max(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float op_min(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double op_min(double a, double b) { return fmin(a, b); }
+
+__device__ __forceinline__ float op_copy(float a) { return a; }
+__device__ __forceinline__ double op_copy(double a) { return a; }
+__device__ __forceinline__ float op_neg(float a) { return -a; }
+__device__ __forceinline__ double op_neg(double a) { return -a; }
+__device__ __forceinline__ float op_abs(float a) { return fabsf(a); }
+__device__ __forceinline__ double op_abs(double a) { return fabs(a); }
+__device__ __forceinline__ float op_exp(float a) { return expf(a); }
+__device__ __forceinline__ double op_exp(double a) { return exp(a); }
+__device__ __forceinline__ float op_log(float a) { return logf(a); }
+__device__ __forceinline__ double op_log(double a) { return log(a); }
+__device__ __forceinline__ float op_sqrt(float a) { return __fsqrt_rn(a); }
+__device__ __forceinline__ double op_sqrt(double a) { return __dsqrt_rn(a); }
+__device__ __forceinline__ float op_erf(float a) { return erff(a); }
+__device__ __forceinline__ double op_erf(double a) { return erf(a); }
+// Standard normal CDF through erf: 0.5 * (1 + erf(x * (1/sqrt 2))).
+__device__ __forceinline__ float op_ncdf(float a) {
+  return op_mul(0.5f, op_add(1.0f, op_erf(op_mul(a, 0.70710678118654752440f))));
+}
+__device__ __forceinline__ double op_ncdf(double a) {
+  return op_mul(0.5, op_add(1.0, op_erf(op_mul(a, 0.70710678118654752440))));
+}
+
+// Reduction step and CSR row product: contraction into FMA is intended here
+// (one task's own arithmetic).
+__device__ __forceinline__ float red_fma(float a, float b, float acc) { return fmaf(a, b, acc); }
+__device__ __forceinline__ double red_fma(double a, double b, double acc) { return fma(a, b, acc); }
+
+// ------------------------------------------------------------ memory access
+// Plain (coherent) loads: data written by an earlier phase of the same kernel
+// must not be served by the non-coherent read-only path.
+template <typename T> __device__ __forceinline__ T ld(const T* p) { return *p; }
+// Read-only path, for stores nothing in the kernel writes.
+template <typename T> __device__ __forceinline__ T ldro(const T* p) { return __ldg(p); }
+
+struct f32x4 { float v[4]; };
+struct f64x2 { double v[2]; };
+
+__device__ __forceinline__ f32x4 ld4(const float* p) {
+  float4 t = *reinterpret_cast<const float4*>(p);
+  f32x4 r; r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w; return r;
+}
+__device__ __forceinline__ f32x4 ld4ro(const float* p) {
+  float4 t = __ldg(reinterpret_cast<const float4*>(p));
+  f32x4 r; r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w; return r;
+}
+// Streaming load (evict-first): inputs read exactly once.
+__device__ __forceinline__ f32x4 ld4cs(const float* p) {
+  float4 t = __ldcs(reinterpret_cast<const float4*>(p));
+  f32x4 r; r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w; return r;
+}
+__device__ __forceinline__ void st4(float* p, const f32x4& r) {
+  *reinterpret_cast<float4*>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
+}
+__device__ __forceinline__ void st4cs(float* p, const f32x4& r) {
+  __stcs(reinterpret_cast<float4*>(p), make_float4(r.v[0], r.v[1], r.v[2], r.v[3]));
+}
+__device__ __forceinline__ f64x2 ld2(const double* p) {
+  double2 t = *reinterpret_cast<const double2*>(p);
+  f64x2 r; r.v[0] = t.x; r.v[1] = t.y; return r;
+}
+__device__ __forceinline__ f64x2 ld2ro(const double* p) {
+  double2 t = __ldg(reinterpret_cast<const double2*>(p));
+  f64x2 r; r.v[0] = t.x; r.v[1] = t.y; return r;
+}
+__device__ __forceinline__ f64x2 ld2cs(const double* p) {
+  double2 t = __ldcs(reinterpret_cast<const double2*>(p));
+  f64x2 r; r.v[0] = t.x; r.v[1] = t.y; return r;
+}
+__device__ __forceinline__ void st2(double* p, const f64x2& r) {
+  *reinterpret_cast<double2*>(p) = make_double2(r.v[0], r.v[1]);
+}
+__device__ __forceinline__ void st2cs(double* p, const f64x2& r) {
+  __stcs(reinterpret_cast<double2*>(p), make_double2(r.v[0], r.v[1]));
+}
+
+// ---------------------------------------------------------------- CSR row
+// y_r = sum_k val[k] * x[col[k]] over k in [rowptr[r], rowptr[r+1]).
+template <typename T>
+__device__ __forceinline__ T spmv_row(const int* __restrict__ rowptr, const int* __restrict__ col,
+                                      const T* __restrict__ val, const T* x, i64 r) {
+  const int k0 = __ldg(rowptr + r), k1 = __ldg(rowptr + r + 1);
+  T acc = T(0);
+  int k = k0;
+  for (; k + 1 < k1; k += 2) {
+    const int c0 = __ldg(col + k), c1 = __ldg(col + k + 1);
+    const T v0 = __ldg(val + k), v1 = __ldg(val + k + 1);
+    const T x0 = ld(x + c0), x1 = ld(x + c1);
+    acc = red_fma(v0, x0, acc);
+    acc = red_fma(v1, x1, acc);
+  }
+  if (k < k1) acc = red_fma(__ldg(val + k), ld(x + __ldg(col + k)), acc);
+  return acc;
+}
+
+// ----------------------------------------------------------- control block
+// One per context, zero-initialised; every kernel leaves it zeroed on exit.
+struct Ctl {
+  u32 bar_arrive;   // grid-barrier arrivals (monotone within a launch)
+  u32 exit_arrive;  // CTAs that finished the launch
+  int err;          // first device error (0 = none)
+  int err_where;    // barrier index that timed out
+  u64 pad[2];
+};
+
+__device__ __forceinline__ u64 globaltimer_ns() {
+  u64 t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ u32 ld_acquire_u32(const u32* p) {
+  u32 v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_relaxed_int(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+enum { ERR_BARRIER_TIMEOUT = 1 };
+
+// Grid-wide barrier among the co-resident CTAs of a cooperative launch.
+// Arrivals count up; barrier k of the launch completes when gridDim.x * k
+// CTAs have arrived.  The wait gives up after `timeout_ns` (or as soon as any
+// CTA has recorded an error), records the failure and returns false; callers
+// then skip the rest of the kernel, so no CTA ever waits forever.
+// `arrive` is false only under the test hook that withholds one arrival.
+__device__ __forceinline__ bool grid_barrier(Ctl* ctl, u32 k, u64 timeout_ns, bool arrive = true) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    if (arrive) atomicAdd(&ctl->bar_arrive, 1u);
+    const u32 target = gridDim.x * k;
+    const u64 t0 = globaltimer_ns();
+    while (ld_acquire_u32(&ctl->bar_arrive) < target) {
+      if (ld_relaxed_int(&ctl->err) != 0) { ok = 0; break; }
+      if (globaltimer_ns() - t0 > timeout_ns) {
+        if (atomicCAS(&ctl->err, 0, (int)ERR_BARRIER_TIMEOUT) == 0) ctl->err_where = (int)k;
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Kernel exit: returns true in exactly one CTA -- the last to arrive -- after
+// every other CTA's writes are visible.  That CTA finishes pending
+// reductions, writes the 0-d results and then calls ctl_reset().
+__device__ __forceinline__ bool last_cta(Ctl* ctl) {
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const u32 n = atomicAdd(&ctl->exit_arrive, 1u);
+    s_last = (n + 1 == gridDim.x);
+    if (s_last) __threadfence();
+  }
+  __syncthreads();
+  return s_last != 0;
+}
+__device__ __forceinline__ void ctl_reset(Ctl* ctl) {
+  if (threadIdx.x == 0) {
+    ctl->bar_arrive = 0;
+    ctl->exit_arrive = 0;
+    __threadfence();
+  }
+}
+
+// --------------------------------------------------------------- reductions
+template <typename T> __device__ __forceinline__ T warp_sum_xor(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum of one value per thread in a fixed order; the result is returned to
+// thread 0 only.  `buf` holds blockDim.x/32 values.
+template <typename T> __device__ __forceinline__ T block_sum(T v, T* buf) {
+  v = warp_sum_xor(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) buf[w] = v;
+  __syncthreads();
+  T r = T(0);
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    r = (l < nw) ? buf[l] : T(0);
+    r = warp_sum_xor(r);
+  }
+  __syncthreads();
+  return r;
+}
+
+// Sum of partials[0..n) in a fixed order (lane-strided, then a butterfly);
+// every thread of every warp computes the same value, so any CTA may use it.
+template <typename T> __device__ __forceinline__ T sum_partials(const T* partials, i64 n) {
+  const int l = threadIdx.x & 31;
+  T acc = T(0);
+  for (i64 i = l; i < n; i += 32) acc += ld(partials + i);
+  return warp_sum_xor(acc);
+}
+
+}  // namespace dfs

@@ -1,0 +1,970 @@
+// runtime.cpp -- the C-ABI of diffuse.h: stores, views, partitions, task
+// submission, and flush_window() (Section 5.1) with memoised analysis and
+// code generation (Section 5.2).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <sstream>
+#include <stdexcept>
+
+#include "jit.hpp"
+#include "runtime.hpp"
+
+namespace dfs {
+
+int64_t StoreRec::nelem() const {
+  int64_t n = 1;
+  for (int d = 0; d < ndim; ++d) n *= shape[d];
+  return n;
+}
+
+// One launch of a cached window: a compiled kernel and how to fill its
+// parameters from a window isomorphic to the one it was generated for.
+struct CachedLaunch {
+  const Compiled* k = nullptr;
+  std::string name;
+  int block = 256;
+  int grid = 1;
+  bool cooperative = false;
+  int nbarriers = 0;
+  int nptr = 0, nimm = 0;
+  std::vector<int> ptr_canon;                 // canonical root id per pointer param
+  std::vector<std::pair<int, int>> imm_src;   // (window task, arg) per immediate param
+  int64_t red_stride = 1;
+  size_t partial_bytes = 0;
+  int first_task = 0, last_task = 0;
+  std::string source;
+};
+
+struct CachedWindow {
+  Plan plan;
+  std::vector<CachedLaunch> launches;
+  std::vector<int> materialise;  // canonical ids that need device memory
+  std::vector<int> made_valid;   // canonical ids holding a value afterwards
+};
+
+struct Stats {
+  int64_t tasks = 0, groups = 0, launches = 0, barriers = 0, flushes = 0;
+  int64_t plan_hits = 0, plan_misses = 0, temporaries = 0;
+  int last_regs = 0, last_occupancy = 0, last_grid = 0, last_block = 0;
+  int64_t bytes_allocated = 0, allocations = 0;
+  double analysis_s = 0.0;
+};
+
+}  // namespace dfs
+
+struct dfs_ctx {
+  dfs_config cfg{};
+  bool device = false;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int sms = 0;
+  dfs::Driver drv;
+  std::unique_ptr<dfs::Jit> jit;
+  std::map<int64_t, dfs::StoreRec> stores;
+  std::map<int64_t, dfs::PartRec> parts;
+  int64_t next_handle = 1;
+  std::vector<dfs::Task> window;
+  int64_t seq = 0;
+  std::string err;
+  dfs::Ctl* ctl = nullptr;
+  void* partials = nullptr;
+  size_t partials_cap = 0;
+  std::unordered_map<std::string, std::unique_ptr<dfs::CachedWindow>> wcache;
+  dfs::Stats st;
+  std::string last_source;
+};
+
+namespace dfs {
+namespace {
+
+int fail(dfs_ctx* c, int code, const std::string& m) {
+  if (c) c->err = m;
+  return code;
+}
+
+#define CUDA_OK(expr)                                                                         \
+  do {                                                                                        \
+    cudaError_t e_ = (expr);                                                                  \
+    if (e_ != cudaSuccess) return fail(c, DFS_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+StoreRec* find_store(dfs_ctx* c, int64_t h) {
+  auto it = c->stores.find(h);
+  if (it == c->stores.end() || it->second.released) return nullptr;
+  return &it->second;
+}
+StoreRec& root_of(dfs_ctx* c, const StoreRec& s) { return c->stores.at(s.root); }
+
+void maybe_free(dfs_ctx* c, int64_t root) {
+  auto it = c->stores.find(root);
+  if (it == c->stores.end()) return;
+  StoreRec& r = it->second;
+  if (r.app_refs > 0 || r.pending > 0) return;
+  if (r.owned && r.ptr && c->device) cudaFreeAsync(r.ptr, c->stream);
+  c->stores.erase(it);
+}
+
+int materialise(dfs_ctx* c, StoreRec& r) {
+  if (r.ptr) return DFS_OK;
+  if (!c->device) return fail(c, DFS_ERR_NO_DEVICE, "analysis-only context has no device memory");
+  const size_t bytes = std::max<size_t>(r.nbytes, 16);
+  cudaError_t e = cudaMallocAsync(&r.ptr, bytes, c->stream);
+  if (e != cudaSuccess) {
+    r.ptr = nullptr;
+    return fail(c, DFS_ERR_OOM, std::string("cudaMallocAsync(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+  }
+  r.owned = true;
+  c->st.bytes_allocated += (int64_t)bytes;
+  c->st.allocations += 1;
+  return DFS_OK;
+}
+
+// --------------------------------------------------------- submit validation
+bool arity_ok(int op, int nargs) {
+  if (op >= DFS_OP_COPY && op <= DFS_OP_NCDF) return nargs == 2;
+  if (op >= DFS_OP_ADD && op <= DFS_OP_MIN) return nargs == 3;
+  if (op == DFS_OP_DOT) return nargs == 3;
+  if (op == DFS_OP_SUM) return nargs == 2;
+  if (op == DFS_OP_SPMV) return nargs == 5;
+  return false;
+}
+bool elementwise(int op) { return (op >= DFS_OP_COPY && op <= DFS_OP_NCDF) || (op >= DFS_OP_ADD && op <= DFS_OP_MIN); }
+
+// Shape of a non-0-d argument's sub-store as a function of the point.
+std::string shape_key(const Arg& a) {
+  std::ostringstream o;
+  o << a.part.kind;
+  for (int d = 0; d < a.nd; ++d) {
+    o << "[" << (a.part.vhi[d] - a.part.vlo[d]);
+    if (a.part.kind) o << "," << a.part.tile[d] << "," << (a.part.off[d] - a.part.vlo[d]) << "," << a.part.proj[d];
+    o << "]";
+  }
+  return o.str();
+}
+
+int validate(dfs_ctx* c, const Task& t) {
+  const int op = t.op;
+  const auto& A = t.args;
+  auto bad = [&](const std::string& m) { return fail(c, DFS_ERR_INVALID, m); };
+  const bool scalar_task = t.scalar();
+  if (scalar_task && t.npoints() != 1) return bad("a task over 0-d stores only must have a single-point launch domain");
+  for (const Arg& a : A) {
+    if (a.imm) continue;
+    if (a.part.kind == 1) {
+      for (int d = 0; d < a.nd; ++d)
+        if (a.part.proj[d] < 0 || a.part.proj[d] >= t.dnd) return bad("tiling projection names a missing launch-domain coordinate");
+    }
+    if (a.nd == 0 && a.part.kind != 0) return bad("0-d stores are accessed through the None partition");
+    if (a.is_w()) {
+      if (a.part.kind == 0 && t.npoints() != 1 && a.nd != 0) return bad("a write through None needs a single-point launch domain (point tasks would interfere)");
+      if (a.part.kind == 0 && a.nd == 0 && t.npoints() != 1) return bad("a 0-d store can only be written by a single-point task");
+      if (a.part.kind == 1) {
+        for (int cdim = 0; cdim < t.dnd; ++cdim) {
+          if (t.dom[cdim] <= 1) continue;
+          bool used = false;
+          for (int d = 0; d < a.nd; ++d) used |= a.part.proj[d] == cdim;
+          if (!used) return bad("a write through a tiling whose projection drops a launch-domain coordinate interferes");
+        }
+      }
+    }
+  }
+  // aliasing inside one task: accesses to one root must agree when one writes,
+  // and a reduced root is not read or written by the same task
+  for (size_t i = 0; i < A.size(); ++i)
+    for (size_t j = 0; j < A.size(); ++j) {
+      if (i == j || A[i].imm || A[j].imm || A[i].root != A[j].root) continue;
+      if (A[i].is_w() && A[i].part != A[j].part) return bad("a task writes a store and accesses an aliasing view of it");
+      if (A[i].is_rd() && (A[j].is_r() || A[j].is_w())) return bad("a task reads or writes a store it reduces to");
+    }
+  if (elementwise(op)) {
+    const Arg& out = A.back();
+    if (out.imm || !out.is_w() || out.is_rd()) return bad("element-wise output must be a store with W or RW");
+    if (!dtype_is_float(out.dtype)) return bad("element-wise ops need a floating dtype");
+    std::string key;
+    for (size_t k = 0; k + 1 < A.size(); ++k)
+      if (!A[k].imm && A[k].priv != DFS_PRIV_R) return bad("element-wise inputs are read (R) or immediates");
+    for (const Arg& a : A) {
+      if (a.imm) continue;
+      if (a.dtype != out.dtype) return bad("element-wise operands must share one dtype");
+      if (a.nd == 0) continue;
+      const std::string k = shape_key(a);
+      if (key.empty()) key = k;
+      else if (k != key) return bad("element-wise operands must have equal sub-store shapes at every point");
+    }
+    if (out.nd == 0 && !scalar_task) return bad("a 0-d output needs every operand 0-d");
+    if (out.nd != 0 && out.part.kind == 0 && t.npoints() != 1) return bad("array operands need a tiling when the domain has several points");
+  } else if (op == DFS_OP_DOT || op == DFS_OP_SUM) {
+    const Arg& out = A.back();
+    if (out.imm || !out.is_rd() || out.redop != DFS_REDOP_SUM || out.nd != 0) return bad("reduction output must be a 0-d store with RD(SUM)");
+    for (size_t k = 0; k + 1 < A.size(); ++k) {
+      if (A[k].imm || A[k].priv != DFS_PRIV_R || A[k].nd == 0) return bad("reduction inputs are non-0-d stores read (R)");
+      if (A[k].dtype != out.dtype || !dtype_is_float(out.dtype)) return bad("reduction operands must share one floating dtype");
+    }
+    if (op == DFS_OP_DOT && shape_key(A[0]) != shape_key(A[1])) return bad("DOT operands must have equal sub-store shapes");
+    if (A[0].part.kind == 0 && t.npoints() != 1) return bad("reduction inputs need a tiling when the domain has several points");
+  } else if (op == DFS_OP_SPMV) {
+    for (int k = 0; k < 5; ++k)
+      if (A[k].imm) return bad("SPMV takes no immediates");
+    const Arg &rp = A[0], &col = A[1], &val = A[2], &x = A[3], &y = A[4];
+    if (rp.dtype != DFS_I32 || col.dtype != DFS_I32) return bad("SPMV rowptr and col are int32");
+    if (!dtype_is_float(val.dtype) || x.dtype != val.dtype || y.dtype != val.dtype) return bad("SPMV val, x and y share one floating dtype");
+    for (int k = 0; k < 4; ++k)
+      if (A[k].priv != DFS_PRIV_R || A[k].part.kind != 0 || A[k].nd != 1) return bad("SPMV rowptr, col, val and x are 1-D, read (R) through None");
+    if (!y.is_w() || y.nd != 1 || (y.part.kind != 1 && t.npoints() != 1)) return bad("SPMV y is 1-D, written through a tiling");
+    const int64_t rows = y.part.vhi[0] - y.part.vlo[0];
+    if (rp.part.vhi[0] - rp.part.vlo[0] != rows + 1) return bad("SPMV rowptr must have rows(y) + 1 entries");
+    if (col.part.vhi[0] - col.part.vlo[0] != val.part.vhi[0] - val.part.vlo[0]) return bad("SPMV col and val lengths differ");
+  } else {
+    return bad("unknown op");
+  }
+  return DFS_OK;
+}
+
+// -------------------------------------------------------------- flushing
+struct WindowInfo {
+  std::map<int64_t, RootInfo> roots;
+  std::map<int64_t, int> canon;   // root -> canonical id
+  std::vector<int64_t> by_canon;  // canonical id -> root
+  std::string key;
+};
+
+WindowInfo window_info(dfs_ctx* c) {
+  WindowInfo wi;
+  for (const Task& t : c->window)
+    for (const Arg& a : t.args) {
+      if (a.imm) continue;
+      if (!wi.canon.count(a.root)) {
+        wi.canon[a.root] = (int)wi.by_canon.size();
+        wi.by_canon.push_back(a.root);
+      }
+      if (wi.roots.count(a.root)) continue;
+      const StoreRec& r = c->stores.at(a.root);
+      RootInfo ri;
+      ri.root = a.root;
+      ri.ndim = r.ndim;
+      for (int d = 0; d < MAXD; ++d) ri.shape[d] = d < r.ndim ? r.shape[d] : 0;
+      ri.app_live = r.app_refs > 0;
+      ri.wrapped = r.wrapped;
+      ri.valid = r.valid;
+      wi.roots[a.root] = ri;
+    }
+  std::ostringstream k;
+  k << "f" << c->cfg.fusion << "m" << c->cfg.launch_mode << "b" << c->cfg.block_threads << "u" << c->cfg.unroll
+    << "x" << c->cfg.debug_skip_arrival
+    << "c" << c->cfg.ctas_per_sm << "|";
+  for (int64_t r : wi.by_canon) {
+    const StoreRec& s = c->stores.at(r);
+    const bool al = s.ptr ? ((uintptr_t)s.ptr % 16 == 0) : true;
+    k << (al ? "a" : "u");
+  }
+  k << "|" << canonical_key(c->window, wi.roots);
+  wi.key = k.str();
+  return wi;
+}
+
+std::string plan_json(const Plan& p, const std::vector<Task>& w, const WindowInfo& wi) {
+  std::ostringstream o;
+  o << "{\"groups\": [";
+  for (size_t g = 0; g < p.groups.size(); ++g) {
+    o << (g ? ", " : "") << "[";
+    for (int i = p.groups[g].begin; i < p.groups[g].end; ++i) o << (i > p.groups[g].begin ? ", " : "") << i;
+    o << "]";
+  }
+  o << "], \"temporaries\": [";
+  // roots temporary in every group that references them
+  std::map<int64_t, std::pair<int, int>> cnt;  // root -> (groups referencing, groups temp)
+  for (size_t g = 0; g < p.groups.size(); ++g) {
+    std::set<int64_t> seen;
+    for (int i = p.groups[g].begin; i < p.groups[g].end; ++i)
+      for (const Arg& a : w[i].args)
+        if (!a.imm) seen.insert(a.root);
+    for (int64_t r : seen) {
+      cnt[r].first++;
+      if (p.temps.count({(int)g, r})) cnt[r].second++;
+    }
+  }
+  bool first = true;
+  for (int64_t r : wi.by_canon) {
+    auto it = cnt.find(r);
+    if (it != cnt.end() && it->second.first == it->second.second) {
+      o << (first ? "" : ", ") << r;
+      first = false;
+    }
+  }
+  o << "], \"launches\": [";
+  for (size_t l = 0; l < p.launches.size(); ++l) {
+    o << (l ? ", " : "") << "[";
+    for (int g = p.launches[l].first; g < p.launches[l].second; ++g) o << (g > p.launches[l].first ? ", " : "") << g;
+    o << "]";
+  }
+  int bars = 0;
+  for (const auto& L : p.launches)
+    for (int g = L.first + 1; g < L.second; ++g)
+      if (!p.groups[g - 1].scalar) ++bars;
+  o << "], \"scalar_groups\": [";
+  first = true;
+  for (size_t g = 0; g < p.groups.size(); ++g)
+    if (p.groups[g].scalar) {
+      o << (first ? "" : ", ") << g;
+      first = false;
+    }
+  o << "], \"barriers\": " << bars << "}";
+  return o.str();
+}
+
+// Builds the cached form of a window: plan, generated and compiled kernels.
+int build_window(dfs_ctx* c, const WindowInfo& wi, std::unique_ptr<CachedWindow>& out) {
+  const auto& w = c->window;
+  auto cw = std::make_unique<CachedWindow>();
+  cw->plan = analyse(w, wi.roots, c->cfg.fusion != 0, c->cfg.launch_mode);
+  const Plan& P = cw->plan;
+  // value state through the window: valid before each launch
+  std::map<int64_t, bool> valid;
+  for (const auto& kv : wi.roots) valid[kv.first] = kv.second.valid;
+  std::set<int64_t> need_mem;
+  for (size_t li = 0; li < P.launches.size(); ++li) {
+    const int g0 = P.launches[li].first, g1 = P.launches[li].second;
+    const int t0 = P.groups[g0].begin, t1 = P.groups[g1 - 1].end;
+    LaunchSpec spec;
+    spec.block = c->cfg.block_threads;
+    spec.unroll = c->cfg.unroll;
+    spec.persistent = (g1 - g0) > 1;
+    spec.debug_skip = c->cfg.debug_skip_arrival;
+    for (int i = t0; i < t1; ++i) spec.tasks.push_back(w[i]);
+    for (int g = g0; g < g1; ++g) {
+      Group G = P.groups[g];
+      G.begin -= t0;
+      G.end -= t0;
+      spec.groups.push_back(G);
+    }
+    // roots of the launch
+    std::map<int64_t, std::pair<int, int>> tcount;  // groups referencing / temp in
+    for (int g = g0; g < g1; ++g) {
+      std::set<int64_t> seen;
+      for (int i = P.groups[g].begin; i < P.groups[g].end; ++i)
+        for (const Arg& a : w[i].args)
+          if (!a.imm) seen.insert(a.root);
+      for (int64_t r : seen) {
+        tcount[r].first++;
+        if (P.temps.count({g, r})) tcount[r].second++;
+      }
+    }
+    int nparam = 0;
+    for (int i = t0; i < t1; ++i)
+      for (const Arg& a : w[i].args) {
+        if (a.imm || spec.root_index.count(a.root)) continue;
+        const StoreRec& s = c->stores.at(a.root);
+        LaunchRoot lr{};
+        lr.root = a.root;
+        lr.dtype = s.dtype;
+        lr.ndim = s.ndim;
+        for (int d = 0; d < MAXD; ++d) {
+          lr.shape[d] = d < s.ndim ? s.shape[d] : 1;
+          lr.stride[d] = d < s.ndim ? s.stride[d] : 1;
+        }
+        lr.zero_d = s.ndim == 0;
+        lr.valid_before = valid[a.root];
+        lr.aligned16 = s.ptr ? ((uintptr_t)s.ptr % 16 == 0) : true;
+        lr.param = -1;
+        spec.root_index[a.root] = (int)spec.roots.size();
+        spec.roots.push_back(lr);
+      }
+    for (LaunchRoot& lr : spec.roots) {
+      for (int i = t0; i < t1; ++i)
+        for (const Arg& a : w[i].args) {
+          if (a.imm || a.root != lr.root) continue;
+          lr.written |= a.is_w() || a.is_rd();
+          lr.read |= a.is_r();
+        }
+      const auto& tc = tcount[lr.root];
+      const RootInfo& ri = wi.roots.at(lr.root);
+      if (lr.zero_d) {
+        // 0-d values live in registers; memory is needed to load a prior value
+        // or to publish the result beyond this launch
+        bool used_later = false;
+        for (int i = t1; i < (int)w.size(); ++i)
+          for (const Arg& a : w[i].args)
+            if (!a.imm && a.root == lr.root && (a.is_r() || a.is_rd())) used_later = true;
+        lr.live_out = lr.written && (ri.app_live || ri.wrapped || used_later);
+        lr.temp = !lr.live_out;
+        bool load = false;
+        if (lr.valid_before) {
+          // first access in program order decides whether the old value is used
+          for (int i = t0; i < t1 && !load; ++i) {
+            bool touched = false;
+            for (const Arg& a : w[i].args) {
+              if (a.imm || a.root != lr.root) continue;
+              touched = true;
+              if (a.is_r() || a.is_rd()) load = true;
+            }
+            if (touched) break;
+          }
+        }
+        lr.valid_before = lr.valid_before && load;
+        if (load || lr.live_out) lr.param = nparam++;
+      } else {
+        lr.temp = c->cfg.fusion && tc.first > 0 && tc.first == tc.second;
+        if (!lr.temp) lr.param = nparam++;
+      }
+      if (lr.param >= 0) need_mem.insert(lr.root);
+    }
+    KernelCode kc;
+    try {
+      kc = generate(spec);
+    } catch (const std::exception& e) {
+      return fail(c, DFS_ERR_INVALID, std::string("code generation: ") + e.what());
+    }
+    std::string err;
+    c->last_source = kc.source;
+    if (!c->device) {
+      // analysis-only context: check that the kernel compiles for the target
+      if (!c->jit->compile_only(kc.source, kc.name, err)) return fail(c, DFS_ERR_COMPILE, err);
+      continue;
+    }
+    const Compiled* comp = c->jit->get(kc.source, kc.name, spec.block, err);
+    if (!comp) return fail(c, DFS_ERR_COMPILE, err);
+    CachedLaunch L;
+    L.k = comp;
+    L.name = kc.name;
+    L.block = spec.block;
+    L.nbarriers = kc.nbarriers;
+    L.cooperative = kc.nbarriers > 0;
+    bool all_scalar = true;
+    for (const Group& G : spec.groups) all_scalar &= G.scalar;
+    int64_t want = all_scalar ? 1 : kc.max_points;
+    int per_sm = comp->occupancy > 0 ? comp->occupancy : 1;
+    if (c->cfg.ctas_per_sm > 0) per_sm = std::min(per_sm, c->cfg.ctas_per_sm);
+    const int64_t cap = (int64_t)per_sm * c->sms;
+    if (L.cooperative && comp->occupancy <= 0) return fail(c, DFS_ERR_CUDA, "generated kernel cannot be resident for a cooperative launch");
+    L.grid = (int)std::max<int64_t>(1, std::min(want, cap));
+    L.nptr = kc.nptr;
+    L.nimm = kc.nimm;
+    for (int64_t r : kc.ptr_roots) L.ptr_canon.push_back(wi.canon.at(r));
+    for (const auto& s : kc.imm_src) L.imm_src.push_back({s.first + t0, s.second});
+    int64_t stride = 1;
+    for (int64_t p : kc.red_points) stride = std::max(stride, p);
+    L.red_stride = stride;
+    L.partial_bytes = kc.partial_bytes;
+    L.first_task = t0;
+    L.last_task = t1;
+    L.source = kc.source;
+    cw->launches.push_back(L);
+    for (const LaunchRoot& lr : spec.roots)
+      if (lr.written && lr.param >= 0) valid[lr.root] = true;
+  }
+  for (int64_t r : need_mem) cw->materialise.push_back(wi.canon.at(r));
+  for (const auto& kv : valid)
+    if (kv.second && need_mem.count(kv.first)) cw->made_valid.push_back(wi.canon.at(kv.first));
+  out = std::move(cw);
+  return DFS_OK;
+}
+
+int run_window(dfs_ctx* c, const CachedWindow& cw, const WindowInfo& wi) {
+  for (int id : cw.materialise) {
+    StoreRec& r = c->stores.at(wi.by_canon[id]);
+    int rc = materialise(c, r);
+    if (rc) return rc;
+  }
+  for (const CachedLaunch& L : cw.launches) {
+    if (L.partial_bytes > c->partials_cap) {
+      if (c->partials) cudaFreeAsync(c->partials, c->stream);
+      c->partials = nullptr;
+      size_t cap = std::max<size_t>(L.partial_bytes, 4096);
+      CUDA_OK(cudaMallocAsync(&c->partials, cap, c->stream));
+      c->partials_cap = cap;
+    }
+    std::vector<uint64_t> blob((size_t)std::max(1, L.nptr) + (size_t)std::max(1, L.nimm) + 4, 0);
+    for (int i = 0; i < L.nptr; ++i) {
+      const StoreRec& r = c->stores.at(wi.by_canon[L.ptr_canon[i]]);
+      void* p = r.ptr;
+      std::memcpy(&blob[i], &p, sizeof p);
+    }
+    const size_t ib = (size_t)std::max(1, L.nptr);
+    for (int i = 0; i < L.nimm; ++i) {
+      const double v = c->window[L.imm_src[i].first].args[L.imm_src[i].second].immv;
+      std::memcpy(&blob[ib + i], &v, sizeof v);
+    }
+    const size_t tb = ib + (size_t)std::max(1, L.nimm);
+    void* pp = c->partials;
+    std::memcpy(&blob[tb], &pp, sizeof pp);
+    void* cp = c->ctl;
+    std::memcpy(&blob[tb + 1], &cp, sizeof cp);
+    const uint64_t to = (uint64_t)(c->cfg.barrier_timeout_s * 1e9);
+    blob[tb + 2] = to;
+    const int64_t rs = L.red_stride;
+    std::memcpy(&blob[tb + 3], &rs, sizeof rs);
+    void* bp = blob.data();
+    void* params[] = {bp};
+    // the kernel takes one struct parameter: pass its bytes as the argument
+    CUresult cr;
+    if (L.cooperative)
+      cr = c->drv.LaunchCooperativeKernel(L.k->fn, L.grid, 1, 1, L.block, 1, 1, 0, (CUstream)c->stream, params);
+    else
+      cr = c->drv.LaunchKernel(L.k->fn, L.grid, 1, 1, L.block, 1, 1, 0, (CUstream)c->stream, params, nullptr);
+    if (cr != CUDA_SUCCESS) {
+      const char* s = nullptr;
+      c->drv.GetErrorString(cr, &s);
+      return fail(c, DFS_ERR_CUDA, std::string("launch of ") + L.name + ": " + (s ? s : "?"));
+    }
+    c->st.launches += 1;
+    c->st.last_regs = L.k->regs;
+    c->st.last_occupancy = L.k->occupancy;
+    c->st.last_grid = L.grid;
+    c->st.last_block = L.block;
+    c->st.barriers += L.nbarriers;
+  }
+  for (int id : cw.made_valid) c->stores.at(wi.by_canon[id]).valid = true;
+  return DFS_OK;
+}
+
+void release_window(dfs_ctx* c) {
+  std::vector<int64_t> roots;
+  for (const Task& t : c->window)
+    for (const Arg& a : t.args)
+      if (!a.imm) {
+        auto it = c->stores.find(a.root);
+        if (it != c->stores.end()) it->second.pending -= 1;
+        roots.push_back(a.root);
+      }
+  c->window.clear();
+  std::sort(roots.begin(), roots.end());
+  roots.erase(std::unique(roots.begin(), roots.end()), roots.end());
+  for (int64_t r : roots) maybe_free(c, r);
+}
+
+int flush(dfs_ctx* c) {
+  if (c->window.empty()) return DFS_OK;
+  c->st.flushes += 1;
+  const auto t0 = std::chrono::steady_clock::now();
+  WindowInfo wi = window_info(c);
+  CachedWindow* cw = nullptr;
+  auto it = c->wcache.find(wi.key);
+  if (it != c->wcache.end()) {
+    c->st.plan_hits += 1;
+    cw = it->second.get();
+  } else {
+    c->st.plan_misses += 1;
+    std::unique_ptr<CachedWindow> built;
+    int rc = build_window(c, wi, built);
+    if (rc) {
+      release_window(c);
+      return rc;
+    }
+    if (!c->device) {
+      c->st.groups += (int64_t)built->plan.groups.size();
+      release_window(c);
+      return fail(c, DFS_ERR_NO_DEVICE, "analysis-only context: window analysed, kernels compiled, not launched");
+    }
+    cw = built.get();
+    c->wcache[wi.key] = std::move(built);
+  }
+  c->st.groups += (int64_t)cw->plan.groups.size();
+  c->st.temporaries += (int64_t)cw->plan.temps.size();
+  c->st.analysis_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (!cw->launches.empty()) c->last_source = cw->launches.back().source;
+  int rc = run_window(c, *cw, wi);
+  release_window(c);
+  return rc;
+}
+
+int write_json(const std::string& s, char* buf, size_t len, size_t* needed) {
+  if (needed) *needed = s.size() + 1;
+  if (!buf || len < s.size() + 1) {
+    if (buf && len) buf[0] = 0;
+    return DFS_ERR_BUFFER;
+  }
+  std::memcpy(buf, s.c_str(), s.size() + 1);
+  return DFS_OK;
+}
+
+}  // namespace
+}  // namespace dfs
+
+using namespace dfs;
+
+extern "C" {
+
+int dfs_version(void) { return 100; }
+
+void dfs_config_default(dfs_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof *cfg);
+  cfg->device = 0;
+  cfg->fusion = 1;
+  cfg->launch_mode = DFS_LAUNCH_PERSISTENT;
+  cfg->window_size = 256;
+  cfg->stream = nullptr;
+  cfg->block_threads = 256;
+  cfg->ctas_per_sm = 0;
+  cfg->unroll = 2;
+  cfg->barrier_timeout_s = 2.0;
+  cfg->cache_dir = nullptr;
+}
+
+int dfs_init(dfs_ctx** out, const dfs_config* cfg_in) {
+  if (!out) return DFS_ERR_INVALID;
+  *out = nullptr;
+  auto c = std::make_unique<dfs_ctx>();
+  dfs_config cfg;
+  dfs_config_default(&cfg);
+  if (cfg_in) cfg = *cfg_in;
+  if (cfg.window_size < 1) cfg.window_size = 1;
+  if (cfg.block_threads == 0) cfg.block_threads = 256;
+  if (cfg.block_threads != 128 && cfg.block_threads != 256 && cfg.block_threads != 512 && cfg.block_threads != 1024)
+    return DFS_ERR_INVALID;
+  if (cfg.unroll <= 0) cfg.unroll = 2;
+  if (cfg.unroll > 8) cfg.unroll = 8;
+  if (cfg.barrier_timeout_s <= 0) cfg.barrier_timeout_s = 2.0;
+  if (cfg.launch_mode != DFS_LAUNCH_PER_TASK && cfg.launch_mode != DFS_LAUNCH_PERSISTENT) return DFS_ERR_INVALID;
+  c->cfg = cfg;
+  std::string cache_dir = cfg.cache_dir ? cfg.cache_dir : "";
+  c->cfg.cache_dir = nullptr;
+  if (cfg.device >= 0) {
+    dfs_ctx* cp = c.get();
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n <= cfg.device) return fail(nullptr, DFS_ERR_NO_DEVICE, "");
+    if (cudaSetDevice(cfg.device) != cudaSuccess) return DFS_ERR_CUDA;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, cfg.device) != cudaSuccess) return DFS_ERR_CUDA;
+    c->sms = prop.multiProcessorCount;
+    std::string err;
+    if (!driver_load(c->drv, err)) return DFS_ERR_CUDA;
+    char arch[32];
+    snprintf(arch, sizeof arch, "sm_%d%d%s", prop.major, prop.minor, prop.major >= 9 ? "a" : "");
+    c->jit = std::make_unique<Jit>(&c->drv, arch, cache_dir);
+    if (cfg.stream) {
+      c->stream = (cudaStream_t)cfg.stream;
+    } else {
+      if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return DFS_ERR_CUDA;
+      c->own_stream = true;
+    }
+    if (cudaMalloc(&c->ctl, sizeof(Ctl)) != cudaSuccess) return DFS_ERR_OOM;
+    if (cudaMemset(c->ctl, 0, sizeof(Ctl)) != cudaSuccess) return DFS_ERR_CUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) return DFS_ERR_CUDA;
+    c->device = true;
+    (void)cp;
+  } else {
+    // analysis-only: NVRTC still compiles generated kernels for sm_103a
+    c->sms = 152;
+    c->jit = std::make_unique<Jit>(&c->drv, "sm_103a", "");
+  }
+  *out = c.release();
+  return DFS_OK;
+}
+
+int dfs_shutdown(dfs_ctx* c) {
+  if (!c) return DFS_OK;
+  int rc = DFS_OK;
+  if (c->device) {
+    rc = flush(c);
+    cudaStreamSynchronize(c->stream);
+    for (auto& kv : c->stores)
+      if (kv.second.owned && kv.second.ptr) cudaFreeAsync(kv.second.ptr, c->stream);
+    if (c->partials) cudaFreeAsync(c->partials, c->stream);
+    cudaStreamSynchronize(c->stream);
+    if (c->ctl) cudaFree(c->ctl);
+    c->jit.reset();
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+  }
+  delete c;
+  return rc;
+}
+
+static int new_store(dfs_ctx* c, int32_t dtype, int32_t ndim, const int64_t* shape, dfs_store* out) {
+  if (!c || !out) return DFS_ERR_INVALID;
+  if (dtype < DFS_F32 || dtype > DFS_I64) return fail(c, DFS_ERR_INVALID, "bad dtype");
+  if (ndim < 0 || ndim > MAXD || (ndim > 0 && !shape)) return fail(c, DFS_ERR_INVALID, "bad ndim");
+  StoreRec r;
+  r.handle = c->next_handle++;
+  r.dtype = dtype;
+  r.ndim = ndim;
+  r.root = r.handle;
+  for (int d = 0; d < ndim; ++d) {
+    if (shape[d] < 0) return fail(c, DFS_ERR_INVALID, "negative extent");
+    r.shape[d] = shape[d];
+  }
+  int64_t s = 1;
+  for (int d = ndim - 1; d >= 0; --d) {
+    r.stride[d] = s;
+    s *= r.shape[d];
+  }
+  r.nbytes = (size_t)r.nelem() * dtype_size(dtype);
+  r.app_refs = 1;
+  c->stores[r.handle] = r;
+  *out = r.handle;
+  return DFS_OK;
+}
+
+int dfs_store_create(dfs_ctx* c, int32_t dtype, int32_t ndim, const int64_t* shape, dfs_store* out) {
+  return new_store(c, dtype, ndim, shape, out);
+}
+
+int dfs_store_wrap(dfs_ctx* c, int32_t dtype, int32_t ndim, const int64_t* shape, void* dev_ptr, dfs_store* out) {
+  if (!c) return DFS_ERR_INVALID;
+  if (!dev_ptr) return fail(c, DFS_ERR_INVALID, "null device pointer");
+  int rc = new_store(c, dtype, ndim, shape, out);
+  if (rc) return rc;
+  StoreRec& r = c->stores.at(*out);
+  r.ptr = dev_ptr;
+  r.wrapped = true;
+  r.valid = true;
+  return DFS_OK;
+}
+
+int dfs_store_view(dfs_ctx* c, dfs_store parent, const int64_t* offset, const int64_t* shape, dfs_store* out) {
+  if (!c || !out) return DFS_ERR_INVALID;
+  StoreRec* p = find_store(c, parent);
+  if (!p) return fail(c, DFS_ERR_STATE, "unknown or released parent store");
+  if (p->ndim > 0 && (!offset || !shape)) return fail(c, DFS_ERR_INVALID, "view needs offset and shape");
+  StoreRec v;
+  v.handle = c->next_handle++;
+  v.dtype = p->dtype;
+  v.ndim = p->ndim;
+  v.root = p->root;
+  for (int d = 0; d < p->ndim; ++d) {
+    if (offset[d] < 0 || shape[d] < 0 || offset[d] + shape[d] > p->shape[d])
+      return fail(c, DFS_ERR_INVALID, "view box outside its parent");
+    v.shape[d] = shape[d];
+    v.off[d] = p->off[d] + offset[d];
+  }
+  StoreRec& root = c->stores.at(p->root);
+  root.app_refs += 1;
+  c->stores[v.handle] = v;
+  *out = v.handle;
+  return DFS_OK;
+}
+
+int dfs_store_release(dfs_ctx* c, dfs_store s) {
+  if (!c) return DFS_ERR_INVALID;
+  StoreRec* r = find_store(c, s);
+  if (!r) return fail(c, DFS_ERR_STATE, "unknown or already released store");
+  const int64_t root = r->root;
+  r->released = true;
+  StoreRec& rr = c->stores.at(root);
+  rr.app_refs -= 1;
+  if (r->handle != root) c->stores.erase(s);
+  maybe_free(c, root);
+  return DFS_OK;
+}
+
+int dfs_store_write(dfs_ctx* c, dfs_store s, const void* host_src, size_t bytes) {
+  if (!c) return DFS_ERR_INVALID;
+  StoreRec* r = find_store(c, s);
+  if (!r) return fail(c, DFS_ERR_STATE, "unknown or released store");
+  if (r->root != r->handle) return fail(c, DFS_ERR_INVALID, "write a root store, not a view");
+  if (bytes != r->nbytes) return fail(c, DFS_ERR_INVALID, "byte count does not match the store");
+  if (!c->device) return fail(c, DFS_ERR_NO_DEVICE, "analysis-only context");
+  int rc = flush(c);
+  if (rc) return rc;
+  rc = materialise(c, *r);
+  if (rc) return rc;
+  CUDA_OK(cudaMemcpyAsync(r->ptr, host_src, bytes, cudaMemcpyHostToDevice, c->stream));
+  r->valid = true;
+  return DFS_OK;
+}
+
+static int check_device_error(dfs_ctx* c) {
+  Ctl h;
+  CUDA_OK(cudaMemcpy(&h, c->ctl, sizeof h, cudaMemcpyDeviceToHost));
+  if (h.err != 0) {
+    cudaMemset(c->ctl, 0, sizeof(Ctl));
+    cudaDeviceSynchronize();
+    return fail(c, DFS_ERR_BARRIER_TIMEOUT, "a grid barrier timed out (barrier " + std::to_string(h.err_where) + ")");
+  }
+  return DFS_OK;
+}
+
+int dfs_store_read(dfs_ctx* c, dfs_store s, void* host_dst, size_t bytes) {
+  if (!c) return DFS_ERR_INVALID;
+  StoreRec* r = find_store(c, s);
+  if (!r) return fail(c, DFS_ERR_STATE, "unknown or released store");
+  if (!c->device) return fail(c, DFS_ERR_NO_DEVICE, "analysis-only context");
+  const size_t es = dtype_size(r->dtype);
+  if (bytes != (size_t)r->nelem() * es) return fail(c, DFS_ERR_INVALID, "byte count does not match the store");
+  int rc = flush(c);
+  if (rc) return rc;
+  StoreRec& root = c->stores.at(r->root);
+  if (!root.ptr) return fail(c, DFS_ERR_STATE, "store has no value");
+  if (bytes) {
+    if (r->ndim <= 1) {
+      const char* src = (const char*)root.ptr + (size_t)(r->ndim ? r->off[0] : 0) * es;
+      CUDA_OK(cudaMemcpyAsync(host_dst, src, bytes, cudaMemcpyDeviceToHost, c->stream));
+    } else if (r->ndim == 2) {
+      const char* src = (const char*)root.ptr + ((size_t)r->off[0] * root.stride[0] + (size_t)r->off[1]) * es;
+      CUDA_OK(cudaMemcpy2DAsync(host_dst, (size_t)r->shape[1] * es, src, (size_t)root.stride[0] * es,
+                                (size_t)r->shape[1] * es, (size_t)r->shape[0], cudaMemcpyDeviceToHost, c->stream));
+    } else {
+      for (int64_t i = 0; i < r->shape[0]; ++i) {
+        const char* src = (const char*)root.ptr +
+                          ((size_t)(r->off[0] + i) * root.stride[0] + (size_t)r->off[1] * root.stride[1] + (size_t)r->off[2]) * es;
+        CUDA_OK(cudaMemcpy2DAsync((char*)host_dst + (size_t)i * r->shape[1] * r->shape[2] * es, (size_t)r->shape[2] * es,
+                                  src, (size_t)root.stride[1] * es, (size_t)r->shape[2] * es, (size_t)r->shape[1],
+                                  cudaMemcpyDeviceToHost, c->stream));
+      }
+    }
+  }
+  CUDA_OK(cudaStreamSynchronize(c->stream));
+  return check_device_error(c);
+}
+
+int dfs_store_device_ptr(dfs_ctx* c, dfs_store s, void** out) {
+  if (!c || !out) return DFS_ERR_INVALID;
+  StoreRec* r = find_store(c, s);
+  if (!r) return fail(c, DFS_ERR_STATE, "unknown or released store");
+  int rc = flush(c);
+  if (rc) return rc;
+  StoreRec& root = c->stores.at(r->root);
+  rc = materialise(c, root);
+  if (rc) return rc;
+  size_t off = 0;
+  for (int d = 0; d < r->ndim; ++d) off += (size_t)r->off[d] * root.stride[d];
+  *out = (char*)root.ptr + off * dtype_size(r->dtype);
+  return DFS_OK;
+}
+
+int dfs_partition_none(dfs_ctx* c, dfs_partition* out) {
+  if (!c || !out) return DFS_ERR_INVALID;
+  PartRec p;
+  p.kind = 0;
+  const int64_t h = c->next_handle++;
+  c->parts[h] = p;
+  *out = h;
+  return DFS_OK;
+}
+
+int dfs_partition_tiling(dfs_ctx* c, int32_t ndim, const int64_t* tile, const int64_t* offset, const int32_t* proj,
+                         dfs_partition* out) {
+  if (!c || !out) return DFS_ERR_INVALID;
+  if (ndim < 1 || ndim > MAXD || !tile) return fail(c, DFS_ERR_INVALID, "bad tiling rank");
+  PartRec p;
+  p.kind = 1;
+  p.ndim = ndim;
+  for (int d = 0; d < ndim; ++d) {
+    if (tile[d] <= 0) return fail(c, DFS_ERR_INVALID, "tile extents must be positive");
+    p.tile[d] = tile[d];
+    p.off[d] = offset ? offset[d] : 0;
+    p.proj[d] = proj ? proj[d] : d;
+    if (p.proj[d] < 0 || p.proj[d] >= MAXD) return fail(c, DFS_ERR_INVALID, "bad projection");
+  }
+  const int64_t h = c->next_handle++;
+  c->parts[h] = p;
+  *out = h;
+  return DFS_OK;
+}
+
+int dfs_submit(dfs_ctx* c, int32_t op, int32_t ndim, const int64_t* dom, int32_t nargs, const dfs_arg* args) {
+  if (!c) return DFS_ERR_INVALID;
+  if (!arity_ok(op, nargs) || !args) return fail(c, DFS_ERR_INVALID, "unknown op or wrong argument count");
+  if (ndim < 1 || ndim > MAXD || !dom) return fail(c, DFS_ERR_INVALID, "launch domain rank must be 1..3");
+  Task t;
+  t.op = op;
+  t.dnd = ndim;
+  for (int d = 0; d < ndim; ++d) {
+    if (dom[d] < 1) return fail(c, DFS_ERR_INVALID, "launch domain extents must be >= 1");
+    t.dom[d] = dom[d];
+  }
+  t.seq = c->seq;
+  for (int i = 0; i < nargs; ++i) {
+    const dfs_arg& in = args[i];
+    Arg a;
+    if (in.privilege == DFS_PRIV_IMM) {
+      a.imm = true;
+      a.immv = in.imm;
+      a.priv = DFS_PRIV_IMM;
+      t.args.push_back(a);
+      continue;
+    }
+    if (in.privilege != DFS_PRIV_R && in.privilege != DFS_PRIV_W && in.privilege != DFS_PRIV_RW &&
+        in.privilege != DFS_PRIV_RD)
+      return fail(c, DFS_ERR_INVALID, "bad privilege");
+    if (in.privilege == DFS_PRIV_RD && in.redop != DFS_REDOP_SUM) return fail(c, DFS_ERR_INVALID, "RD needs a reduction operator");
+    StoreRec* s = find_store(c, in.store);
+    if (!s) return fail(c, DFS_ERR_STATE, "task names an unknown or released store");
+    auto pit = c->parts.find(in.partition);
+    if (pit == c->parts.end()) return fail(c, DFS_ERR_STATE, "task names an unknown partition");
+    const PartRec& P = pit->second;
+    a.store = in.store;
+    a.root = s->root;
+    a.priv = in.privilege;
+    a.redop = in.redop;
+    a.dtype = s->dtype;
+    a.nd = s->ndim;
+    a.part.kind = P.kind;
+    a.part.nd = s->ndim;
+    if (P.kind == 1 && P.ndim != s->ndim) return fail(c, DFS_ERR_INVALID, "tiling rank differs from the store's");
+    for (int d = 0; d < s->ndim; ++d) {
+      a.part.vlo[d] = s->off[d];
+      a.part.vhi[d] = s->off[d] + s->shape[d];
+      if (P.kind == 1) {
+        a.part.tile[d] = P.tile[d];
+        a.part.off[d] = s->off[d] + P.off[d];
+        a.part.proj[d] = P.proj[d];
+      }
+    }
+    t.args.push_back(a);
+  }
+  int rc = validate(c, t);
+  if (rc) return rc;
+  for (const Arg& a : t.args)
+    if (!a.imm) c->stores.at(a.root).pending += 1;
+  c->window.push_back(std::move(t));
+  c->seq += 1;
+  c->st.tasks += 1;
+  if ((int)c->window.size() >= c->cfg.window_size) return flush(c);
+  return DFS_OK;
+}
+
+int dfs_flush(dfs_ctx* c) {
+  if (!c) return DFS_ERR_INVALID;
+  return flush(c);
+}
+
+int dfs_sync(dfs_ctx* c) {
+  if (!c) return DFS_ERR_INVALID;
+  if (!c->device) return DFS_OK;
+  int rc = flush(c);
+  if (rc) return rc;
+  CUDA_OK(cudaStreamSynchronize(c->stream));
+  return check_device_error(c);
+}
+
+const char* dfs_last_error(dfs_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int dfs_plan_json(dfs_ctx* c, char* buf, size_t len, size_t* needed) {
+  if (!c) return DFS_ERR_INVALID;
+  WindowInfo wi = window_info(c);
+  Plan p = analyse(c->window, wi.roots, c->cfg.fusion != 0, c->cfg.launch_mode);
+  std::string s = plan_json(p, c->window, wi);
+  s.insert(s.size() - 1, ", \"key\": \"" + std::to_string(std::hash<std::string>{}(wi.key)) + "\"");
+  return write_json(s, buf, len, needed);
+}
+
+int dfs_stats_json(dfs_ctx* c, char* buf, size_t len, size_t* needed) {
+  if (!c) return DFS_ERR_INVALID;
+  std::ostringstream o;
+  const Stats& s = c->st;
+  o << "{\"tasks\": " << s.tasks << ", \"groups\": " << s.groups << ", \"launches\": " << s.launches
+    << ", \"barriers\": " << s.barriers << ", \"flushes\": " << s.flushes << ", \"plan_hits\": " << s.plan_hits
+    << ", \"plan_misses\": " << s.plan_misses << ", \"temporaries\": " << s.temporaries
+    << ", \"bytes_allocated\": " << s.bytes_allocated << ", \"allocations\": " << s.allocations
+    << ", \"analysis_s\": " << s.analysis_s;
+  if (c->jit)
+    o << ", \"compile_s\": " << c->jit->compile_seconds() << ", \"kernels_compiled\": " << c->jit->compiles()
+      << ", \"kernel_cache_hits\": " << c->jit->hits() << ", \"kernel_disk_hits\": " << c->jit->disk_hits();
+  o << ", \"last_regs\": " << s.last_regs << ", \"last_occupancy\": " << s.last_occupancy
+    << ", \"last_grid\": " << s.last_grid << ", \"last_block\": " << s.last_block;
+  o << ", \"sms\": " << c->sms << "}";
+  return write_json(o.str(), buf, len, needed);
+}
+
+int dfs_last_kernel_source(dfs_ctx* c, char* buf, size_t len, size_t* needed) {
+  if (!c) return DFS_ERR_INVALID;
+  return write_json(c->last_source, buf, len, needed);
+}
+
+}  // extern "C"

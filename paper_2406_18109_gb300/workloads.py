@@ -1,0 +1,133 @@
+"""The evaluated programs written naturally against the array front end.
+
+Each line is one array operation, hence one index task, as an application of
+the array libraries would issue them (Section 7.1): the runtime decides what
+fuses.  The task counts are those of the unfused streams.
+
+  * Black-Scholes call/put pricing: 23 tasks per batch.
+  * Conjugate gradients: 11 tasks per iteration (SpMV, two dots, two scalar
+    divides, three scaled updates written as multiply + add/sub).
+  * The Fig. 1a stencil (Jacobi relaxation over five aliased views): 6 tasks
+    per sweep.
+  * BiCGSTAB: 4 dots, 2 SpMVs, scalar arithmetic and vector updates per
+    iteration.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+from . import arrays as A
+from .arrays import Array, CSR, Runtime
+
+BLACK_SCHOLES_TASKS = 23
+CG_TASKS_PER_ITERATION = 11
+JACOBI_TASKS_PER_SWEEP = 6
+
+
+def black_scholes(S: Array, K: Array, T: Array, r: float, sigma: float):
+    """European call and put under Black-Scholes, N(x) = 0.5 (1 + erf(x/sqrt 2))."""
+    mu = r + 0.5 * sigma * sigma
+    t1 = S / K
+    t2 = A.log(t1)
+    t3 = A.sqrt(T)
+    v = sigma * t3
+    t5 = mu * T
+    t6 = t2 + t5
+    d1 = t6 / v
+    d2 = d1 - v
+    t9 = (-r) * T
+    disc = A.exp(t9)
+    kd = K * disc
+    n1 = A.ncdf(d1)
+    n2 = A.ncdf(d2)
+    c1 = S * n1
+    c2 = kd * n2
+    call = c1 - c2
+    m1 = -d1
+    nm1 = A.ncdf(m1)
+    m2 = -d2
+    nm2 = A.ncdf(m2)
+    p1 = kd * nm2
+    p2 = S * nm1
+    put = p1 - p2
+    return call, put
+
+
+@dataclass
+class CGState:
+    x: Array
+    r: Array
+    p: Array
+    rho: Array
+
+
+def cg_start(b: Array) -> CGState:
+    """x0 = 0, r0 = b, p0 = r0, rho0 = r0.r0."""
+    x = A.full(b.rt, b.shape, 0.0, b.dtype)
+    r = A.copy(b)
+    p = A.copy(b)
+    rho = A.dot(r, r)
+    return CGState(x, r, p, rho)
+
+
+def cg_iteration(Amat: CSR, s: CGState) -> None:
+    """One CG iteration as a naturally written NumPy/SciPy program."""
+    q = Amat @ s.p
+    alpha = s.rho / A.dot(s.p, q)
+    s.x += alpha * s.p
+    s.r -= alpha * q
+    rho_new = A.dot(s.r, s.r)
+    beta = rho_new / s.rho
+    s.rho = rho_new
+    s.p = s.r + beta * s.p
+
+
+def jacobi_views(grid: Array):
+    """center, north, east, west, south views of an (N+2)x(N+2) grid (Fig. 1a)."""
+    return (grid[1:-1, 1:-1], grid[0:-2, 1:-1], grid[1:-1, 2:], grid[1:-1, 0:-2], grid[2:, 1:-1])
+
+
+def jacobi_sweep(views) -> None:
+    center, north, east, west, south = views
+    avg = center + north + east + west + south
+    work = 0.2 * avg
+    center[:] = work
+
+
+@dataclass
+class BiCGState:
+    x: Array
+    r: Array
+    rhat: Array
+    p: Array
+    v: Array
+    rho: Array
+    alpha: Array
+    omega: Array
+
+
+def bicgstab_start(b: Array) -> BiCGState:
+    rt = b.rt
+    x = A.full(rt, b.shape, 0.0, b.dtype)
+    r = A.copy(b)
+    rhat = A.copy(b)
+    p = A.full(rt, b.shape, 0.0, b.dtype)
+    v = A.full(rt, b.shape, 0.0, b.dtype)
+    one = rt.scalar(1.0, b.dtype)
+    return BiCGState(x, r, rhat, p, v, one, A.copy(one), A.copy(one))
+
+
+def bicgstab_iteration(Amat: CSR, s: BiCGState) -> Array:
+    """One BiCGSTAB iteration (van der Vorst); returns r.r of the new residual."""
+    rho = A.dot(s.rhat, s.r)
+    beta = (rho / s.rho) * (s.alpha / s.omega)
+    s.p = s.r + beta * (s.p - s.omega * s.v)
+    s.v = Amat @ s.p
+    s.alpha = rho / A.dot(s.rhat, s.v)
+    sv = s.r - s.alpha * s.v
+    t = Amat @ sv
+    s.omega = A.dot(t, sv) / A.dot(t, t)
+    s.x += s.alpha * s.p + s.omega * sv
+    s.r = sv - s.omega * t
+    s.rho = rho
+    return A.dot(s.r, s.r)

@@ -1,0 +1,178 @@
+"""C-ABI checks that need no GPU: the library loads, exports every declared
+symbol, validates submissions, and its fusion pass produces the paper's plans.
+Analysis-only contexts (device = -1) also compile every generated kernel with
+NVRTC for sm_103a, which checks the code generator without a GPU."""
+import re
+
+import numpy as np
+import pytest
+
+from paper_2406_18109_gb300 import binding as B
+from paper_2406_18109_gb300 import arrays as A
+from paper_2406_18109_gb300 import workloads as W
+from tests.helpers import HEADER, ensure_built
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    ensure_built()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dfs_[a-z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol():
+    names = declared_functions()
+    assert set(names) == set(B.EXPORTS)
+    lib = B.lib()
+    for n in names:
+        assert hasattr(lib, n), n
+    assert B.dfs_version() >= 100
+
+
+def test_config_default_matches_header():
+    cfg = B.dfs_config_default()
+    assert cfg.fusion == 1 and cfg.launch_mode == B.DFS_LAUNCH_PERSISTENT
+    assert cfg.block_threads == 256 and cfg.barrier_timeout_s == 2.0
+    assert cfg.debug_skip_arrival == 0
+
+
+def rt0(**kw):
+    return A.Runtime(device=-1, **kw)
+
+
+def expect_invalid(fn):
+    with pytest.raises(B.DfsError) as e:
+        fn()
+    assert e.value.code in (-1, -7)
+
+
+def test_submission_validation():
+    rt = rt0(tile=4)
+    a = rt.empty((8,), np.float32)
+    b = rt.empty((8,), np.float64)
+    s = rt.empty((), np.float32)
+    T4 = rt.tiling((4,))
+    none = rt.none
+    # dtype mismatch
+    expect_invalid(lambda: rt.submit("ADD", (2,), [(a.handle, T4, 1), (b.handle, T4, 1), (a.handle, T4, 2)]))
+    # write through None with several points interferes
+    expect_invalid(lambda: rt.submit("COPY", (2,), [1.0, (a.handle, none, 2)]))
+    # 0-d output of a multi-point task
+    expect_invalid(lambda: rt.submit("COPY", (2,), [(a.handle, T4, 1), (s.handle, none, 2)]))
+    # reduction output must be RD(SUM) 0-d
+    expect_invalid(lambda: rt.submit("DOT", (2,), [(a.handle, T4, 1), (a.handle, T4, 1), (s.handle, none, 2)]))
+    # reading a store a task reduces to
+    expect_invalid(lambda: rt.submit("DOT", (1,), [(s.handle, none, 1), (s.handle, none, 1), (s.handle, none, 4)]))
+    # write one view while reading an aliasing one in the same task
+    v1, v2 = a[0:4], a[2:6]
+    T2 = rt.tiling((2,))
+    expect_invalid(lambda: rt.submit("COPY", (2,), [(v1.handle, T2, 1), (v2.handle, T2, 2)]))
+    # unknown op / wrong arity
+    expect_invalid(lambda: B.dfs_submit(rt.ctx, 999, (1,), [1.0, (a.handle, T4, 2)]))
+    expect_invalid(lambda: rt.submit("ADD", (2,), [(a.handle, T4, 1), (a.handle, T4, 2)]))
+    # released stores cannot be used
+    c = rt.empty((8,), np.float32)
+    h = c.handle
+    c.release()
+    expect_invalid(lambda: rt.submit("COPY", (2,), [1.0, (h, T4, 2)]))
+    assert rt.plan()["groups"] == []
+
+
+def test_view_bounds_checked():
+    rt = rt0()
+    g = rt.empty((4, 4), np.float32)
+    with pytest.raises(B.DfsError):
+        B.dfs_store_view(rt.ctx, g.handle, [1, 1], [4, 4])
+
+
+def test_fig1_plan_and_kernel_compiles():
+    rt = rt0(rows=2)
+    g = rt.empty((6, 6), np.float32)
+    views = W.jacobi_views(g)
+    W.jacobi_sweep(views)
+    p = rt.plan()
+    assert p["groups"] == [[0, 1, 2, 3, 4], [5]]
+    assert len(p["temporaries"]) == 4
+    assert p["barriers"] == 1
+    with pytest.raises(B.DfsError) as e:
+        rt.flush()
+    assert e.value.code == -2      # compiled, not launched: no device here
+    assert "grid_barrier" in rt.kernel_source()
+
+
+def test_black_scholes_plan_fuses_everything():
+    rt = rt0(tile=8)
+    S, K, T = (rt.empty((30,), np.float32) for _ in range(3))
+    call, put = W.black_scholes(S, K, T, 0.02, 0.3)
+    p = rt.plan()
+    assert p["groups"] == [list(range(W.BLACK_SCHOLES_TASKS))]
+    assert len(p["temporaries"]) == W.BLACK_SCHOLES_TASKS - 2
+    assert call.handle not in p["temporaries"] and put.handle not in p["temporaries"]
+    with pytest.raises(B.DfsError):
+        rt.flush()
+    src = rt.kernel_source()
+    # four N() tasks per element, replicated over vector lanes and loop variants
+    assert src.count("op_ncdf(") % 4 == 0 and "ld4" in src and "st4" in src
+    # only the two outputs are stored: the 21 temporaries live in registers
+    assert src.count("st4(") == src.count("st4(r3") + src.count("st4(r4")
+
+
+def test_black_scholes_unfused_plan():
+    rt = rt0(tile=8, fusion=False, launch="per_task")
+    S, K, T = (rt.empty((30,), np.float32) for _ in range(3))
+    W.black_scholes(S, K, T, 0.02, 0.3)
+    p = rt.plan()
+    assert len(p["groups"]) == W.BLACK_SCHOLES_TASKS and p["temporaries"] == []
+    assert len(p["launches"]) == W.BLACK_SCHOLES_TASKS
+
+
+def _cg_rt(**kw):
+    rt = rt0(tile=8, **kw)
+    Am = A.CSR.__new__(A.CSR)
+    Am.rt, Am.nrows, Am.ncols, Am.nnz = rt, 16, 16, 40
+    Am.rowptr = rt.empty((17,), np.int32)
+    Am.col = rt.empty((40,), np.int32)
+    Am.val = rt.empty((40,), np.float64)
+    Am.dtype = np.dtype(np.float64)
+    st = W.CGState(rt.empty((16,)), rt.empty((16,)), rt.empty((16,)), rt.empty(()))
+    return rt, Am, st
+
+
+def test_cg_plan():
+    rt, Am, st = _cg_rt()
+    W.cg_iteration(Am, st)
+    p = rt.plan()
+    # [SpMV, dot] | [alpha] | [x+=, r-=, dot] | [beta] | [p=]
+    assert p["groups"] == [[0, 1], [2], [3, 4, 5, 6, 7], [8], [9, 10]]
+    assert p["scalar_groups"] == [1, 3]
+    assert p["launches"] == [[0, 1, 2, 3, 4]] and p["barriers"] == 2
+    assert len(p["temporaries"]) == 3          # alpha*p, alpha*q, beta*p
+    with pytest.raises(B.DfsError):
+        rt.flush()
+
+
+def test_cg_plan_two_iterations_memo_key():
+    rt, Am, st = _cg_rt()
+    W.cg_iteration(Am, st)
+    k1 = rt.plan()["key"]
+    with pytest.raises(B.DfsError):
+        rt.flush()
+    W.cg_iteration(Am, st)
+    k2 = rt.plan()["key"]
+    # isomorphic windows over different stores share one canonical key (Section 5.2)
+    assert k1 == k2
+
+
+def test_window_size_triggers_analysis():
+    rt = rt0(tile=4, window_size=3)
+    a = rt.empty((8,), np.float32)
+    b = a + 1.0
+    c = b * 2.0
+    with pytest.raises(B.DfsError):
+        d = c - 3.0                              # third task: window full, analysed
+    st = rt.stats()
+    assert st["flushes"] == 1 and st["tasks"] == 3

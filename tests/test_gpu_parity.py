@@ -1,0 +1,282 @@
+"""GPU parity: the generated sm_103a kernels against the CPU oracle.
+
+Every comparison runs the same seeded inputs through the CUDA path (via the
+C-ABI) and through ``oracle/``.  Tolerances: FP64 reductions/solvers 1e-12
+norm-wise relative; FP32 Black-Scholes |diff| <= 1e-5 (S + K) per option;
+element-wise FP32 work whose operations round the same way on both sides
+(the Jacobi stencil: adds and a multiply) bit for bit.  Fused execution must
+equal unfused execution bit for bit (every element operation rounds once).
+"""
+import numpy as np
+import pytest
+
+from oracle import programs
+from oracle.interp import Imm, Machine, XTask
+from oracle.ir import Arg, IDENTITY, Tiling
+from paper_2406_18109_gb300 import arrays as A
+from paper_2406_18109_gb300 import binding as B
+from paper_2406_18109_gb300 import configs
+from paper_2406_18109_gb300 import workloads as W
+from synth import inputs
+from tests.helpers import MODES, gpu_runtime
+
+pytestmark = pytest.mark.gpu
+
+BS = configs.BLACK_SCHOLES
+
+
+def _bits(a):
+    return np.ascontiguousarray(a).view(np.uint32 if a.dtype == np.float32 else np.uint64)
+
+
+# ----------------------------------------------------------- Black-Scholes
+def _bs_gpu(mode, S, K, T, **kw):
+    with gpu_runtime(mode, **kw) as rt:
+        call, put = W.black_scholes(rt.array(S), rt.array(K), rt.array(T), BS["r"], BS["sigma"])
+        return call.numpy(), put.numpy(), rt.stats()
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_black_scholes_matches_oracle(mode):
+    n = 100_003                                  # 25 tiles of 4096 and a ragged tail
+    S, K, T = inputs.bs_inputs(n, seed=BS["seed"])
+    c, p, st = _bs_gpu(mode, S, K, T, tile=4096)
+    scale = S.astype(np.float64) + K.astype(np.float64)
+    for dt in (np.float32, np.float64):
+        c_o, p_o = programs.black_scholes(S, K, T, BS["r"], BS["sigma"], dt)
+        assert np.all(np.abs(c - c_o) <= 1e-5 * scale)
+        assert np.all(np.abs(p - p_o) <= 1e-5 * scale)
+    if mode == "persistent":
+        assert st["launches"] == 1
+    if mode == "unfused":
+        assert st["launches"] == W.BLACK_SCHOLES_TASKS
+
+
+def test_black_scholes_fused_equals_unfused_bitwise():
+    n = 50_001
+    S, K, T = inputs.bs_inputs(n, seed=3)
+    res = {m: _bs_gpu(m, S, K, T, tile=2048)[:2] for m in MODES}
+    for m in MODES[1:]:
+        assert np.array_equal(_bits(res[m][0]), _bits(res["persistent"][0]))
+        assert np.array_equal(_bits(res[m][1]), _bits(res["persistent"][1]))
+
+
+def test_black_scholes_full_size_sampled():
+    """2^26 options in the benchmark's launch configuration; sampled options
+    are priced one by one by the oracle."""
+    n = BS["n"]
+    S, K, T = inputs.bs_inputs(n, seed=BS["seed"])
+    c, p, _ = _bs_gpu("persistent", S, K, T, tile=BS["tile"], block=BS["block"], unroll=BS["unroll"])
+    rng = np.random.default_rng(99)
+    idx = np.concatenate([rng.integers(0, n, 4000), np.arange(8), np.arange(n - 8, n)])
+    c_o, p_o = programs.black_scholes(S[idx], K[idx], T[idx], BS["r"], BS["sigma"], np.float64)
+    scale = S[idx].astype(np.float64) + K[idx].astype(np.float64)
+    assert np.all(np.abs(c[idx] - c_o) <= 1e-5 * scale)
+    assert np.all(np.abs(p[idx] - p_o) <= 1e-5 * scale)
+    # put-call parity holds at every one of the 2^26 options
+    lhs = c.astype(np.float64) - p.astype(np.float64)
+    rhs = S.astype(np.float64) - K.astype(np.float64) * np.exp(-BS["r"] * T.astype(np.float64))
+    assert np.all(np.abs(lhs - rhs) <= 1e-5 * (S.astype(np.float64) + K.astype(np.float64)))
+
+
+# ---------------------------------------------------------------------- CG
+def _cg_gpu(mode, m, iters, tile, seed=0, **kw):
+    rp, col, val, xs = inputs.cg_inputs(m=m, seed=seed)
+    with gpu_runtime(mode, tile=tile, **kw) as rt:
+        Am = A.CSR(rt, rp, col, val)
+        b = Am @ rt.array(xs)                   # b = A x*, computed on the device
+        st = W.cg_start(b)
+        rt.flush()
+        for _ in range(iters):
+            W.cg_iteration(Am, st)
+            rt.flush()
+        return st.x.numpy(), st.r.numpy(), st.rho.item(), b.numpy(), rt.stats()
+
+
+def _cg_oracle(m, iters, seed=0):
+    rp, col, val, xs = inputs.cg_inputs(m=m, seed=seed)
+    b = programs.spmv(rp, col, val, xs)
+    x, r, rho = programs.cg(rp, col, val, b, iters)
+    return x, r, rho, b
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_cg_matches_oracle(mode):
+    m, iters = 61, 50                           # n = 3721: 15 tiles of 256 and a ragged tail
+    x, r, rho, b, st = _cg_gpu(mode, m, iters, tile=256)
+    xo, ro, rhoo, bo = _cg_oracle(m, iters)
+    assert _rel(b, bo) < 1e-14
+    assert _rel(x, xo) < 1e-12
+    assert _rel(r, ro) < 1e-10 * max(1.0, np.linalg.norm(bo) / np.linalg.norm(ro))
+    assert abs(rho - rhoo) <= 1e-10 * abs(rhoo) + 1e-30
+    if mode == "persistent":
+        # b = A x* and the CG start share one flush, then one launch per iteration
+        assert st["launches"] == iters + 1 and st["barriers"] == 2 * iters
+
+
+def test_cg_fused_equals_unfused_bitwise():
+    res = {m: _cg_gpu(m, 40, 20, tile=256) for m in MODES}
+    for m in MODES[1:]:
+        assert np.array_equal(_bits(res[m][0]), _bits(res["persistent"][0]))
+        assert res[m][2] == res["persistent"][2]
+
+
+def test_cg_full_size():
+    cfg = configs.CG
+    x, r, rho, b, st = _cg_gpu("persistent", cfg["m"], cfg["iters"], tile=cfg["tile"],
+                               block=cfg["block"], unroll=cfg["unroll"])
+    xo, ro, rhoo, bo = _cg_oracle(cfg["m"], cfg["iters"])
+    assert _rel(x, xo) < 1e-12
+    assert abs(rho - rhoo) <= 1e-10 * abs(rhoo)
+    assert st["kernels_compiled"] + st["kernel_disk_hits"] <= 4    # isomorphic iterations share one kernel
+    assert st["plan_hits"] >= cfg["iters"] - 1
+
+
+# ------------------------------------------------------------------ Jacobi
+def _jacobi_gpu(mode, grid, sweeps, rows, per_flush=1, **kw):
+    with gpu_runtime(mode, rows=rows, **kw) as rt:
+        g = rt.array(grid)
+        views = W.jacobi_views(g)
+        for s in range(sweeps):
+            W.jacobi_sweep(views)
+            if (s + 1) % per_flush == 0:
+                rt.flush()
+        return g.numpy(), rt.stats()
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_jacobi_matches_oracle_bitwise(mode):
+    grid = inputs.jacobi_grid(62, seed=2)        # 64x64: 4 bands of 16 rows, the last ragged
+    out, st = _jacobi_gpu(mode, grid, 12, rows=16, per_flush=3)
+    want = programs.jacobi(grid, 12, np.float32)
+    assert np.array_equal(_bits(out), _bits(want))
+
+
+def test_jacobi_full_size_sampled():
+    """8192^2 grid, benchmark launch configuration, 3 sweeps: every sampled
+    point is recomputed by the oracle on its (2k+3)^2 neighbourhood (values
+    farther than k cells cannot reach it in k sweeps)."""
+    cfg = configs.JACOBI
+    k = 3
+    grid = inputs.jacobi_grid(cfg["N"], seed=cfg["seed"])
+    out, _ = _jacobi_gpu("persistent", grid, k, rows=cfg["rows"], block=cfg["block"], unroll=cfg["unroll"])
+    assert out.min() >= grid.min() and out.max() <= 1.0
+    n = grid.shape[0]
+    rng = np.random.default_rng(5)
+    pts = [(1, 1), (n - 2, n - 2), (1, n - 2), (n - 2, 1), (n // 2, n // 2)]
+    pts += [tuple(x) for x in rng.integers(1, n - 1, (60, 2))]
+    R = k + 1
+    for (i, j) in pts:
+        i0, i1 = max(0, i - R), min(n, i + R + 1)
+        j0, j1 = max(0, j - R), min(n, j + R + 1)
+        sub = programs.jacobi(grid[i0:i1, j0:j1], k, np.float32)
+        assert _bits(out[i:i + 1, j:j + 1]) == _bits(sub[i - i0:i - i0 + 1, j - j0:j - j0 + 1]), (i, j)
+
+
+# ------------------------------------------------------ random windows
+OPS1 = ["NEG", "EXP", "SQRT", "ABS", "LOG", "NCDF", "ERF", "COPY"]
+OPS2 = ["ADD", "SUB", "MUL", "DIV", "MAX", "MIN"]
+
+
+def _random_stream(rng, nstores):
+    stream = []
+    for _ in range(rng.integers(3, 12)):
+        out = int(rng.integers(0, nstores))
+        if rng.random() < 0.4:
+            stream.append((str(rng.choice(OPS1)), out, [int(rng.integers(0, nstores))]))
+        else:
+            b = int(rng.integers(0, nstores)) if rng.random() < 0.7 else float(rng.uniform(0.5, 2))
+            stream.append((str(rng.choice(OPS2)), out, [int(rng.integers(0, nstores)), b]))
+    return stream
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_random_elementwise_windows(dtype):
+    rng = np.random.default_rng(2024)
+    n, tile, ns = 3001, 512, 4
+    dom = ((n + tile - 1) // tile,)
+    for trial in range(6):
+        stream = _random_stream(rng, ns)
+        init = [inputs.uniform(100 + trial * 10 + s, 0.5, 2.0, n, dtype) for s in range(ns)]
+        outs = {}
+        for mode in MODES:
+            with gpu_runtime(mode, tile=tile) as rt:
+                arrs = [rt.array(x) for x in init]
+                for op, o, ins in stream:
+                    opnds = [arrs[i]._arg(B.DFS_PRIV_R) if isinstance(i, int) else i for i in ins]
+                    rt.submit(op, dom, opnds + [arrs[o]._arg(B.DFS_PRIV_W)])
+                outs[mode] = [a.numpy() for a in arrs]
+        for mode in MODES[1:]:
+            for s in range(ns):
+                assert np.array_equal(_bits(outs[mode][s]), _bits(outs["persistent"][s])), (trial, mode, s)
+        m = Machine("stored")
+        P = Tiling((tile,), (0,), IDENTITY, ((0,), (n,)))
+        for s in range(ns):
+            m.add(s, init[s])
+        for op, o, ins in stream:
+            opnds = [Arg(i, P, "R") if isinstance(i, int) else Imm(i) for i in ins]
+            m.run(XTask(op, dom, opnds + [Arg(o, P, "W")]))
+        for s in range(ns):
+            want = m.arrays[s]
+            got = outs["persistent"][s]
+            ok = np.isclose(got, want, rtol=2e-6 if dtype == np.float32 else 1e-14, atol=0, equal_nan=True)
+            assert ok.all(), (trial, s)
+
+
+# ---------------------------------------------------- reductions, SpMV
+@pytest.mark.parametrize("n", [1, 5, 255, 256, 257, 10007])
+def test_dot_and_sum(n):
+    x = inputs.uniform(1, -1, 1, n)
+    y = inputs.uniform(2, -1, 1, n)
+    with gpu_runtime("persistent", tile=256) as rt:
+        X, Y = rt.array(x), rt.array(y)
+        d = A.dot(X, Y).item()
+        s = A.asum(X).item()
+        nr = A.norm(X).item()
+    assert abs(d - x @ y) <= 1e-13 * np.abs(x * y).sum() + 1e-300
+    assert abs(s - x.sum()) <= 1e-13 * np.abs(x).sum() + 1e-300
+    assert abs(nr - np.linalg.norm(x)) <= 1e-14 * np.linalg.norm(x)
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_spmv_random_spd(dtype):
+    rp, col, val = inputs.random_spd_csr(2000, seed=4)
+    x = inputs.uniform(6, -1, 1, 2000, dtype)
+    with gpu_runtime("persistent", tile=256) as rt:
+        Am = A.CSR(rt, rp, col, val.astype(dtype))
+        y = (Am @ rt.array(x)).numpy()
+    want = programs.spmv(rp, col, val, x.astype(np.float64))
+    tol = 1e-13 if dtype == np.float64 else 1e-5
+    assert np.max(np.abs(y - want)) <= tol * np.max(np.abs(want))
+
+
+# ------------------------------------------------------- runtime behaviour
+def test_temporaries_are_never_allocated():
+    n = 1 << 16
+    S, K, T = inputs.bs_inputs(n, seed=1)
+    _, _, fused = _bs_gpu("persistent", S, K, T, tile=4096)
+    _, _, unfused = _bs_gpu("unfused", S, K, T, tile=4096)
+    assert fused["allocations"] == 5            # S, K, T, call, put
+    assert unfused["allocations"] == 3 + W.BLACK_SCHOLES_TASKS
+
+
+def test_barrier_timeout_is_reported_and_context_survives():
+    rp, col, val, xs = inputs.cg_inputs(m=32, seed=0)
+    with gpu_runtime("persistent", tile=256, timeout_s=0.05, debug_skip_arrival=1) as rt:
+        Am = A.CSR(rt, rp, col, val)
+        b = rt.array(xs)
+        st = W.cg_start(b)
+        rt.flush()
+        W.cg_iteration(Am, st)
+        with pytest.raises(B.DfsError) as e:
+            rt.sync()
+        assert e.value.code == -6
+        rt.sync()                                # error consumed; context usable
+    # a fresh context on the same device computes correctly
+    x, *_ = _cg_gpu("persistent", 32, 5, tile=256)
+    xo, *_ = _cg_oracle(32, 5)
+    assert _rel(x, xo) < 1e-12
