@@ -6,9 +6,11 @@ as the 23-task array program, fused by the runtime into one sm_103a kernel.
 One step = issue the task window through the API + flush + the fused kernel,
 inputs resident in HBM (1.34 GB per step, larger than the 129 MB L2, so no
 flush of L2 is needed between steps).  Also measured in the same run: the
-unfused per-task path (23 kernels, every temporary in HBM), the end-to-end
-path with host buffers (H2D of S,K,T and D2H of call,put every step), and the
-CPU oracle on a bounded sample.
+unfused per-task path (23 kernels, every temporary in HBM), the fused
+one-kernel-per-fused-task path, the end-to-end path with host buffers (H2D of
+S, K, T and D2H of call, put every step), and the CPU oracle on a bounded
+sample.  Kernel durations come from CUDA events the runtime records
+immediately around each launch on the launching stream.
 
   python bench.py [--steps K] [--warmup W] [--workload bs|cg|jacobi]
   python bench.py --impl reference     # the CPU oracle as the reference arm
@@ -33,9 +35,11 @@ sys.path.insert(0, ROOT)
 from paper_2406_18109_gb300 import configs  # noqa: E402
 from synth import inputs  # noqa: E402
 
-METRIC_BS = "Black-Scholes options/s (fused window, 2^26 FP32)"
-METRIC_CG = "CG iterations/s (fused windows, 256^2 Poisson FP64)"
-METRIC_JAC = "Jacobi sweeps/s (fused windows, 8192^2 FP32)"
+METRIC = {"bs": ("Black-Scholes options/s (fused window, 2^26 FP32)", "options/s", "f32"),
+          "cg": ("CG iterations/s (fused windows, 256^2 Poisson FP64)", "iterations/s", "f64"),
+          "jacobi": ("Jacobi sweeps/s (fused windows, 8192^2 FP32)", "sweeps/s", "f32")}
+WORKLOAD = {"bs": "black-scholes-2^26-fp32", "cg": "cg-poisson2d-256x256-fp64-50it",
+            "jacobi": "jacobi-fig1-stencil-8192x8192-fp32-200sweeps"}
 
 
 def load_peaks():
@@ -81,7 +85,7 @@ class Clocks:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.t.join(timeout=2)
-        sm, mx, reasons = [], [], set()
+        sm, mx, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
@@ -90,13 +94,14 @@ class Clocks:
             try:
                 sm.append(float(f[1]))
                 mx.append(float(f[2]))
+                pw.append(float(f[3]))
             except ValueError:
                 continue
             for nm, v in zip(names, f[4:8]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons), "samples": len(sm)}
 
 
 # ------------------------------------------------------------------ oracle
@@ -115,7 +120,7 @@ def oracle_rate(workload: str, budget_s: float = 10.0):
             if time.perf_counter() > t_end:
                 break
         dt = time.perf_counter() - t0
-        return done / dt, "options/s", f"{done} options in batches of 2^20 from the 2^26-option seed-1 draw law"
+        return done / dt, "options/s", f"{done} options in batches of 2^20 drawn like the 2^26 workload (seed 1)"
     if workload == "cg":
         cfg = configs.CG
         rp, col, val, xs = inputs.cg_inputs(m=cfg["m"], seed=cfg["seed"])
@@ -142,147 +147,118 @@ def oracle_rate(workload: str, budget_s: float = 10.0):
 
 
 # ---------------------------------------------------------------- GPU arms
-def run_bs(rt_kwargs, steps, warmup, torch, stream, e2e=False):
-    from paper_2406_18109_gb300 import arrays as A
-    from paper_2406_18109_gb300 import workloads as W
-    cfg = configs.BLACK_SCHOLES
-    n = cfg["n"]
-    S, K, T = inputs.bs_inputs(n, seed=cfg["seed"])
-    rt = A.Runtime(device=torch.cuda.current_device(), stream=stream.cuda_stream, **rt_kwargs)
-    dS, dK, dT = rt.array(S), rt.array(K), rt.array(T)
-    rt.sync()
-    h2d = d2h = 0
-    if e2e:
-        pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
-        hS, hK, hT = pin(S), pin(K), pin(T)
-        hc = torch.empty(n, dtype=torch.float32).pin_memory().numpy()
-        hp = torch.empty(n, dtype=torch.float32).pin_memory().numpy()
+def kernel_delta(before: dict, after: dict) -> dict:
+    out = {}
+    for k, v in after.items():
+        b = before.get(k, {"ms": 0.0, "launches": 0})
+        n = v["launches"] - b["launches"]
+        if n > 0:
+            out[k] = {"ms": v["ms"] - b["ms"], "launches": n}
+    return out
 
-    def step():
-        nonlocal h2d, d2h
-        if e2e:
-            dS.write(hS)
-            dK.write(hK)
-            dT.write(hT)
-        call, put = W.black_scholes(dS, dK, dT, cfg["r"], cfg["sigma"])
-        rt.flush()
-        if e2e:
-            call.read_into(hc)
-            put.read_into(hp)
-        return call, put
 
-    for _ in range(warmup):
-        step()
-    rt.sync()
-    launches0 = rt.stats()["launches"]
-    k_ev = []
-    torch.cuda.synchronize()
-    start = torch.cuda.Event(enable_timing=True)
-    end = torch.cuda.Event(enable_timing=True)
-    start.record(stream)
-    t0 = time.perf_counter()
-    keep = None
-    for _ in range(steps):
-        if not e2e:
-            # events around the flush time its launch(es) on the launching stream
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            c_, p_ = W.black_scholes(dS, dK, dT, cfg["r"], cfg["sigma"])
-            a.record(stream)
-            rt.flush()
-            b.record(stream)
-            k_ev.append((a, b))
-            keep = (c_, p_)
+class Arm:
+    """One timed configuration of a workload: build state, warm up, time K steps."""
+
+    def __init__(self, workload, rt_kwargs, torch, stream, e2e=False):
+        from paper_2406_18109_gb300 import arrays as A
+        from paper_2406_18109_gb300 import dist as D
+        from paper_2406_18109_gb300 import workloads as W
+        self.W, self.torch, self.stream, self.e2e = W, torch, stream, e2e
+        self.rt = A.Runtime(device=torch.cuda.current_device(), stream=stream.cuda_stream,
+                            time_launches=True, **rt_kwargs)
+        self.h2d = self.d2h = 0
+        rank = int(os.environ.get("RANK", "0"))
+        if workload == "bs":
+            cfg = self.cfg = configs.BLACK_SCHOLES
+            n = cfg["n"]
+            # weak scaling: every rank prices its own, independent batch
+            S, K, T = inputs.bs_inputs(n, seed=D.rank_seed(cfg["seed"], rank))
+            self.dS, self.dK, self.dT = self.rt.array(S), self.rt.array(K), self.rt.array(T)
+            self.units = n
+            if e2e:
+                pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+                self.hS, self.hK, self.hT = pin(S), pin(K), pin(T)
+                self.hc = torch.empty(n, dtype=torch.float32).pin_memory().numpy()
+                self.hp = torch.empty(n, dtype=torch.float32).pin_memory().numpy()
+                self.h2d, self.d2h = 3 * n * 4, 2 * n * 4
+            self.step = self._bs
+        elif workload == "cg":
+            cfg = self.cfg = configs.CG
+            rp, col, val, xs = inputs.cg_inputs(m=cfg["m"], seed=cfg["seed"])
+            self.Am = A.CSR(self.rt, rp, col, val)
+            self.b = self.Am @ self.rt.array(xs)
+            self.units = cfg["iters"]
+            self.step = self._cg
         else:
-            keep = step()
-    end.record(stream)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
-    ms = start.elapsed_time(end)
-    launches = rt.stats()["launches"] - launches0
-    kern_ms = [a.elapsed_time(b) for a, b in k_ev]
-    if e2e:
-        h2d = 3 * n * 4
-        d2h = 2 * n * 4
-    del keep
-    st = rt.stats()
-    rt.close()
-    return {"ms": ms, "wall_s": wall, "launches": launches, "kernel_ms": kern_ms, "stats": st,
-            "h2d": h2d, "d2h": d2h, "units": n * steps}
+            cfg = self.cfg = configs.JACOBI
+            grid = inputs.jacobi_grid(cfg["N"], seed=cfg["seed"])
+            self.g = self.rt.array(grid)
+            self.views = W.jacobi_views(self.g)
+            self.units = cfg["sweeps"]
+            self.step = self._jacobi
+        self.rt.sync()
+        self.keep = None
 
+    def _bs(self):
+        c = self.cfg
+        if self.e2e:
+            self.dS.write(self.hS)
+            self.dK.write(self.hK)
+            self.dT.write(self.hT)
+        call, put = self.W.black_scholes(self.dS, self.dK, self.dT, c["r"], c["sigma"])
+        self.rt.flush()
+        if self.e2e:
+            call.read_into(self.hc)
+            put.read_into(self.hp)
+        self.keep = (call, put)
 
-def run_cg(rt_kwargs, steps, warmup, torch, stream):
-    from paper_2406_18109_gb300 import arrays as A
-    from paper_2406_18109_gb300 import workloads as W
-    cfg = configs.CG
-    rp, col, val, xs = inputs.cg_inputs(m=cfg["m"], seed=cfg["seed"])
-    rt = A.Runtime(device=torch.cuda.current_device(), stream=stream.cuda_stream, **rt_kwargs)
-    Am = A.CSR(rt, rp, col, val)
-    b = Am @ rt.array(xs)
-    rt.sync()
+    def _cg(self):
+        st = self.W.cg_start(self.b)
+        self.rt.flush()
+        for _ in range(self.cfg["iters"]):
+            self.W.cg_iteration(self.Am, st)
+            self.rt.flush()
+        self.keep = st
 
-    def solve():
-        st = W.cg_start(b)
-        rt.flush()
-        for _ in range(cfg["iters"]):
-            W.cg_iteration(Am, st)
-            rt.flush()
-        return st
+    def _jacobi(self):
+        per = self.cfg["sweeps_per_flush"]
+        for s in range(self.cfg["sweeps"]):
+            self.W.jacobi_sweep(self.views)
+            if (s + 1) % per == 0:
+                self.rt.flush()
+        self.rt.flush()
 
-    for _ in range(warmup):
-        solve()
-    rt.sync()
-    l0 = rt.stats()["launches"]
-    torch.cuda.synchronize()
-    start = torch.cuda.Event(enable_timing=True)
-    end = torch.cuda.Event(enable_timing=True)
-    start.record(stream)
-    for _ in range(steps):
-        st = solve()
-    end.record(stream)
-    torch.cuda.synchronize()
-    ms = start.elapsed_time(end)
-    launches = rt.stats()["launches"] - l0
-    out = {"ms": ms, "launches": launches, "stats": rt.stats(), "units": cfg["iters"] * steps,
-           "kernel_ms": [ms / (steps * cfg["iters"])]}
-    rt.close()
-    return out
+    def run(self, steps, warmup):
+        torch, stream, rt = self.torch, self.stream, self.rt
+        for _ in range(warmup):
+            self.step()
+        rt.sync()
+        s0 = rt.stats()
+        torch.cuda.synchronize()
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            self.step()
+        end.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        rt.sync()
+        s1 = rt.stats()
+        ms = start.elapsed_time(end)
+        kd = kernel_delta(s0["kernel_times"], s1["kernel_times"])
+        dom = max(kd.items(), key=lambda kv: kv[1]["ms"]) if kd else (None, {"ms": 0.0, "launches": 1})
+        out = {"ms": ms, "wall_s": wall, "launches": s1["launches"] - s0["launches"],
+               "units": self.units * steps, "kernels": kd, "dominant": dom[0],
+               "dominant_ms": dom[1]["ms"] / max(1, dom[1]["launches"]),
+               "dominant_launches": dom[1]["launches"], "stats": s1}
+        return out
 
-
-def run_jacobi(rt_kwargs, steps, warmup, torch, stream):
-    from paper_2406_18109_gb300 import arrays as A
-    from paper_2406_18109_gb300 import workloads as W
-    cfg = configs.JACOBI
-    grid = inputs.jacobi_grid(cfg["N"], seed=cfg["seed"])
-    rt = A.Runtime(device=torch.cuda.current_device(), stream=stream.cuda_stream, **rt_kwargs)
-    g = rt.array(grid)
-    views = W.jacobi_views(g)
-    rt.sync()
-    sweeps = cfg["sweeps"]
-
-    def run(k):
-        for s in range(k):
-            W.jacobi_sweep(views)
-            if (s + 1) % cfg["sweeps_per_flush"] == 0:
-                rt.flush()
-        rt.flush()
-
-    run(warmup)
-    rt.sync()
-    l0 = rt.stats()["launches"]
-    torch.cuda.synchronize()
-    start = torch.cuda.Event(enable_timing=True)
-    end = torch.cuda.Event(enable_timing=True)
-    start.record(stream)
-    for _ in range(steps):
-        run(sweeps)
-    end.record(stream)
-    torch.cuda.synchronize()
-    ms = start.elapsed_time(end)
-    out = {"ms": ms, "launches": rt.stats()["launches"] - l0, "stats": rt.stats(), "units": sweeps * steps,
-           "kernel_ms": [ms / (steps * sweeps)]}
-    rt.close()
-    return out
+    def close(self):
+        self.keep = None
+        self.rt.close()
 
 
 def main():
@@ -299,10 +275,7 @@ def main():
         configs.BLACK_SCHOLES["n"] = args.bs_n
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
-    metric, unit = {"bs": (METRIC_BS, "options/s"), "cg": (METRIC_CG, "iterations/s"),
-                    "jacobi": (METRIC_JAC, "sweeps/s")}[args.workload]
-    workload_name = {"bs": "black-scholes-2^26-fp32", "cg": "cg-poisson2d-256x256-fp64-50it",
-                     "jacobi": "jacobi-fig1-stencil-8192x8192-fp32-200sweeps"}[args.workload]
+    metric, unit, dtype = METRIC[args.workload]
 
     if args.impl == "reference":
         if rank != 0:
@@ -310,8 +283,8 @@ def main():
         v, u, sample = oracle_rate(args.workload, budget_s=max(5.0, min(60.0, 2.0 * args.steps)))
         line = {"metric": metric, "value": v, "unit": unit, "n_gpus": args.gpus, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32" if args.workload != "cg" else "f64", "data": "synthetic",
-                "impl": "reference", "config": {"workload": workload_name},
+                "vs_baseline": None, "dtype": dtype, "data": "synthetic", "impl": "reference",
+                "config": {"workload": WORKLOAD[args.workload]},
                 "cpu_baseline": {"value": v, "unit": u, "cores": 1, "kind": "oracle", "sample": sample},
                 "e2e": {"value": v, "unit": u, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -329,71 +302,71 @@ def main():
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     cache = os.path.join(ROOT, "gpurun_out", "cubins") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None
+    if cache:
+        os.makedirs(cache, exist_ok=True)
 
     from paper_2406_18109_gb300 import _build
+    from paper_2406_18109_gb300 import dist as D
     _build.build()
 
-    if args.workload == "bs":
-        cfg = configs.BLACK_SCHOLES
-        base = dict(tile=cfg["tile"], block=cfg["block"], unroll=cfg["unroll"], sms=sms, cache_dir=cache)
-        runner = lambda kw, s, w, **x: run_bs(kw, s, w, torch, stream, **x)
-    elif args.workload == "cg":
-        cfg = configs.CG
-        base = dict(tile=cfg["tile"], block=cfg["block"], unroll=cfg["unroll"], sms=sms, cache_dir=cache)
-        runner = lambda kw, s, w, **x: run_cg(kw, s, w, torch, stream)
-    else:
-        cfg = configs.JACOBI
-        base = dict(rows=cfg["rows"], block=cfg["block"], unroll=cfg["unroll"], sms=sms, cache_dir=cache)
-        runner = lambda kw, s, w, **x: run_jacobi(kw, s, w, torch, stream)
+    cfg = {"bs": configs.BLACK_SCHOLES, "cg": configs.CG, "jacobi": configs.JACOBI}[args.workload]
+    base = dict(block=cfg["block"], unroll=cfg["unroll"], sms=sms, cache_dir=cache)
+    if "tile" in cfg:
+        base["tile"] = cfg["tile"]
+    if "rows" in cfg:
+        base["rows"] = cfg["rows"]
 
+    def arm(kw, steps, warmup, e2e=False):
+        a = Arm(args.workload, kw, torch, stream, e2e=e2e)
+        try:
+            return a.run(steps, warmup)
+        finally:
+            a.close()
+
+    fused_arm = Arm(args.workload, dict(base, fusion=True, launch="persistent"), torch, stream)
     clocks = Clocks(dev)
     if world > 1:
         torch.distributed.barrier()
     clocks.start()
-    fused = runner(dict(base, fusion=True, launch="persistent"), args.steps, args.warmup)
+    fused = fused_arm.run(args.steps, args.warmup)
     clk = clocks.stop()
+    fused_arm.close()
+    value, fused["ms"], _ = D.combine(fused["ms"], fused["units"], device="cuda" if world > 1 else None)
     ms_step = fused["ms"] / args.steps
-    if world > 1:
-        t = torch.tensor([fused["ms"]], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        fused["ms"] = float(t.item())
-        ms_step = fused["ms"] / args.steps
-    value = fused["units"] * world / (fused["ms"] / 1e3)
 
     extra = {}
     if not args.quick:
         k2 = max(3, args.steps // 4)
-        unf = runner(dict(base, fusion=False, launch="per_task"), k2, 2)
-        pt = runner(dict(base, fusion=True, launch="per_task"), k2, 2)
+        unf = arm(dict(base, fusion=False, launch="per_task"), k2, 2)
+        pt = arm(dict(base, fusion=True, launch="per_task"), k2, 2)
         extra["unfused"] = {"value": unf["units"] / (unf["ms"] / 1e3), "ms_per_step": unf["ms"] / k2,
-                            "launches_per_step": unf["launches"] / k2}
+                            "launches_per_step": unf["launches"] / k2,
+                            "kernel_ms_per_step": sum(v["ms"] for v in unf["kernels"].values()) / k2}
         extra["fused_per_task"] = {"value": pt["units"] / (pt["ms"] / 1e3), "ms_per_step": pt["ms"] / k2,
-                                   "launches_per_step": pt["launches"] / k2}
+                                   "launches_per_step": pt["launches"] / k2,
+                                   "kernel_ms_per_step": sum(v["ms"] for v in pt["kernels"].values()) / k2}
         extra["fused_vs_unfused"] = value / world / extra["unfused"]["value"]
+        extra["fused_kernel_ms_per_step"] = sum(v["ms"] for v in fused["kernels"].values()) / args.steps
         if args.workload == "bs":
-            e = runner(dict(base, fusion=True, launch="persistent"), max(3, args.steps // 4), 2, e2e=True)
+            e = arm(dict(base, fusion=True, launch="persistent"), k2, 2, e2e=True)
             extra["e2e"] = {"value": e["units"] / (e["ms"] / 1e3), "unit": unit,
-                            "h2d_bytes_per_step": e["h2d"], "d2h_bytes_per_step": e["d2h"]}
+                            "h2d_bytes_per_step": 3 * cfg["n"] * 4, "d2h_bytes_per_step": 2 * cfg["n"] * 4}
 
     peaks = load_peaks()
     if args.workload == "bs":
-        n = configs.BLACK_SCHOLES["n"]
-        alg_bytes = 20 * n
-        kern_ms = statistics.mean(fused["kernel_ms"])
+        alg_bytes = 20 * cfg["n"]                          # read S, K, T; write call, put
     elif args.workload == "cg":
-        m = configs.CG["m"]
-        nn = m * m
-        nnz = 5 * nn - 4 * m
-        alg_bytes = 12 * nnz + 4 * (nn + 1) + 96 * nn
-        kern_ms = statistics.mean(fused["kernel_ms"])
+        m = cfg["m"]
+        nn, nnz = m * m, 5 * m * m - 4 * m
+        alg_bytes = 12 * nnz + 4 * (nn + 1) + 96 * nn     # one CG iteration (one launch)
     else:
-        N = configs.JACOBI["N"]
-        alg_bytes = 16 * N * N
-        kern_ms = statistics.mean(fused["kernel_ms"])
-    achieved = alg_bytes / (kern_ms / 1e3) / 1e9
+        alg_bytes = 16 * cfg["N"] * cfg["N"]               # one sweep (one launch)
+    kern_ms = fused["dominant_ms"]
+    achieved = alg_bytes / (kern_ms / 1e3) / 1e9 if kern_ms > 0 else 0.0
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                "peak_source": peaks["source"], "kernel_ms": kern_ms, "algorithmic_bytes": alg_bytes}
+                "peak_source": peaks["source"], "kernel": fused["dominant"], "kernel_ms": kern_ms,
+                "launches": fused["dominant_launches"], "algorithmic_bytes_per_launch": alg_bytes}
 
     cpu = None
     if rank == 0 and world == 1 and not args.quick:
@@ -402,17 +375,18 @@ def main():
 
     line = {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if args.workload != "cg" else "f64",
-            "data": "synthetic (seeded generators of synth/inputs.py)",
-            "config": {"workload": workload_name, "l2": "inputs larger than L2" if args.workload != "cg"
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic (seeded generators of synth/inputs.py)",
+            "config": {"workload": WORKLOAD[args.workload],
+                       "l2": "inputs larger than L2" if args.workload != "cg"
                        else "working set L2-resident (10 MB); no flush", "launch": "persistent fused",
                        "parallelism": f"replicas x{world}"},
-            "e2e": extra.get("e2e"), "gpu_launches": fused["launches"], "roofline": roofline,
+            "e2e": extra.pop("e2e", None), "gpu_launches": fused["launches"], "roofline": roofline,
             "cpu_baseline": cpu, "clocks": clk}
-    line.update({k: v for k, v in extra.items() if k != "e2e"})
-    line["runtime_stats"] = {k: fused["stats"].get(k) for k in ("compile_s", "kernels_compiled", "plan_hits",
-                                                                  "plan_misses", "kernel_disk_hits", "last_regs",
-                                                                  "last_occupancy", "last_grid", "last_block")}
+    line.update(extra)
+    st = fused["stats"]
+    line["runtime_stats"] = {k: st.get(k) for k in ("compile_s", "kernels_compiled", "plan_hits", "plan_misses",
+                                                     "kernel_disk_hits", "last_regs", "last_occupancy",
+                                                     "last_grid", "last_block", "analysis_s")}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

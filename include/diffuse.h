@@ -150,6 +150,9 @@ typedef struct {
    * barrier number k, so every CTA's wait runs out after barrier_timeout_s
    * and the launch ends with DFS_ERR_BARRIER_TIMEOUT at the next dfs_sync. */
   int32_t debug_skip_arrival;
+  /* 1: record CUDA events immediately around every kernel launch; the
+   * per-kernel device times appear in dfs_stats_json after dfs_sync. */
+  int32_t time_launches;
 } dfs_config;
 
 /* Fills *cfg with the defaults above (device 0, fusion on, persistent). */

@@ -12,11 +12,15 @@ over the launch domain (ceil(n/tile),); a 2-D array (or view) of shape (m, w)
 into bands of ``rows`` rows, launch domain (ceil(m/rows), 1).  Arrays of equal
 shape therefore share launch domain and tiling, which is what lets the fusion
 pass fuse their tasks.  0-d arrays are read through the None partition.
+
+The issue path is kept short (cached layouts, one packed argument buffer per
+runtime) because the host issues one task per array operation.
 """
 from __future__ import annotations
 
+import ctypes as C
 import math
-import weakref
+import struct
 
 import numpy as np
 
@@ -24,6 +28,11 @@ from . import binding as B
 
 _DT = {np.dtype(np.float32): B.DFS_F32, np.dtype(np.float64): B.DFS_F64,
        np.dtype(np.int32): B.DFS_I32, np.dtype(np.int64): B.DFS_I64}
+_ARG = struct.Struct("=qqiid")      # dfs_arg: store, partition, privilege, redop, imm (32 bytes)
+assert _ARG.size == C.sizeof(B.dfs_arg)
+_R, _W, _RD, _IMM = B.DFS_PRIV_R, B.DFS_PRIV_W, B.DFS_PRIV_RD, B.DFS_PRIV_IMM
+_SUM = B.DFS_REDOP_SUM
+_OP = B.OPS
 
 
 def _dfs_dtype(dt) -> int:
@@ -37,7 +46,7 @@ class Runtime:
                  window_size: int = 256, block: int = 256, unroll: int = 2, ctas_per_sm: int = 0,
                  stream: int | None = None, cache_dir: str | None = None, timeout_s: float = 2.0,
                  tile: int | None = None, rows: int | None = None, sms: int = 152,
-                 debug_skip_arrival: int = 0):
+                 debug_skip_arrival: int = 0, time_launches: bool = False):
         cfg = B.dfs_config_default()
         cfg.device = device
         cfg.fusion = 1 if fusion else 0
@@ -49,16 +58,27 @@ class Runtime:
         cfg.barrier_timeout_s = timeout_s
         cfg.stream = stream
         cfg.debug_skip_arrival = debug_skip_arrival
+        cfg.time_launches = 1 if time_launches else 0
         self._cache_dir = cache_dir.encode() if cache_dir else None
         cfg.cache_dir = self._cache_dir
         self.ctx = B.dfs_init(cfg)
         self.device = device
         self.none = B.dfs_partition_none(self.ctx)
         self._tilings = {}
+        self._layouts = {}
+        self._shapes = {}
         self.tile = tile
         self.rows = rows
         self.sms = sms
         self._alive = True
+        L = B.lib()
+        self._lib_submit = L.dfs_submit
+        self._lib_create = L.dfs_store_create
+        self._lib_release = L.dfs_store_release
+        self._argbuf = (B.dfs_arg * 8)()
+        self._argptr = C.cast(self._argbuf, C.POINTER(B.dfs_arg))
+        self._out = C.c_int64()
+        self._outref = C.byref(self._out)
 
     # ------------------------------------------------------------ lifetime
     def close(self):
@@ -96,21 +116,50 @@ class Runtime:
 
     def layout(self, shape):
         """(launch domain, partition handle) the library uses for this shape."""
-        if len(shape) == 0:
-            return (1,), self.none
-        if len(shape) == 1:
-            t = self.tile_1d(shape[0])
-            return (max(1, math.ceil(shape[0] / t)),), self.tiling((t,))
-        if len(shape) == 2:
-            r = self.rows_2d(shape[0], shape[1])
-            return (max(1, math.ceil(shape[0] / r)), 1), self.tiling((r, shape[1]))
-        raise ValueError("arrays of rank > 2 are not supported by the front end")
+        lay = self._layouts.get(shape)
+        if lay is None:
+            lay = self._make_layout(shape)
+        return lay[0], lay[1]
 
-    # -------------------------------------------------------------- arrays
+    def _make_layout(self, shape):
+        if len(shape) == 0:
+            dom, part = (1,), self.none
+        elif len(shape) == 1:
+            t = self.tile_1d(shape[0])
+            dom, part = (max(1, math.ceil(shape[0] / t)),), self.tiling((t,))
+        elif len(shape) == 2:
+            r = self.rows_2d(shape[0], shape[1])
+            dom, part = (max(1, math.ceil(shape[0] / r)), 1), self.tiling((r, shape[1]))
+        else:
+            raise ValueError("arrays of rank > 2 are not supported by the front end")
+        lay = (dom, part, (C.c_int64 * len(dom))(*dom), len(dom))
+        self._layouts[shape] = lay
+        return lay
+
+    # ------------------------------------------------------------- tasking
+    def _pack(self, i, x):
+        if x.__class__ is Array:
+            lay = self._layouts.get(x.shape) or self._make_layout(x.shape)
+            _ARG.pack_into(self._argbuf, i * 32, x.handle, lay[1], _R, 0, 0.0)
+        else:
+            _ARG.pack_into(self._argbuf, i * 32, 0, 0, _IMM, 0, float(x))
+
+    def _issue(self, opcode, lay, n):
+        rc = self._lib_submit(self.ctx, opcode, lay[3], lay[2], n, self._argptr)
+        if rc:
+            B._check(self.ctx, rc)
+
+    def _new(self, shape, dtype) -> "Array":
+        sc = self._shapes.get(shape)
+        if sc is None:
+            sc = self._shapes[shape] = (C.c_int64 * max(1, len(shape)))(*shape)
+        rc = self._lib_create(self.ctx, _DT[dtype], len(shape), sc, self._outref)
+        if rc:
+            B._check(self.ctx, rc)
+        return Array(self, self._out.value, shape, dtype)
+
     def empty(self, shape, dtype=np.float64) -> "Array":
-        shape = tuple(int(s) for s in shape)
-        h = B.dfs_store_create(self.ctx, _dfs_dtype(dtype), shape)
-        return Array(self, h, shape, np.dtype(dtype))
+        return self._new(tuple(int(s) for s in shape), np.dtype(dtype))
 
     def array(self, host: np.ndarray) -> "Array":
         host = np.ascontiguousarray(host)
@@ -128,7 +177,9 @@ class Runtime:
         dt = {torch.float32: np.float32, torch.float64: np.float64,
               torch.int32: np.int32, torch.int64: np.int64}[tensor.dtype]
         h = B.dfs_store_wrap(self.ctx, _dfs_dtype(dt), tuple(tensor.shape), tensor.data_ptr())
-        return Array(self, h, tuple(tensor.shape), np.dtype(dt), keep=tensor)
+        a = Array(self, h, tuple(tensor.shape), np.dtype(dt))
+        a._keep = tensor
+        return a
 
     def submit(self, op, domain, args):
         B.dfs_submit(self.ctx, op, domain, args)
@@ -149,27 +200,30 @@ class Runtime:
         return B.dfs_last_kernel_source(self.ctx)
 
 
-def _release(rt_ref, handle):
-    rt = rt_ref()
-    if rt is not None and rt._alive:
-        try:
-            B.dfs_store_release(rt.ctx, handle)
-        except B.DfsError:
-            pass
-
-
 class Array:
     """A store (or view) handle; operators submit one index task each."""
 
+    __slots__ = ("rt", "handle", "shape", "dtype", "_keep", "__weakref__")
     __array_priority__ = 100
 
-    def __init__(self, rt: Runtime, handle: int, shape, dtype, keep=None):
+    def __init__(self, rt: Runtime, handle: int, shape, dtype):
         self.rt = rt
         self.handle = handle
-        self.shape = tuple(shape)
-        self.dtype = np.dtype(dtype)
-        self._keep = keep
-        self._fin = weakref.finalize(self, _release, weakref.ref(rt), handle)
+        self.shape = shape
+        self.dtype = dtype
+        self._keep = None
+
+    def __del__(self):
+        rt = self.rt
+        if self.handle and rt._alive:
+            rt._lib_release(rt.ctx, self.handle)
+            self.handle = 0
+
+    def release(self):
+        rt = self.rt
+        if self.handle and rt._alive:
+            B.dfs_store_release(rt.ctx, self.handle)
+        self.handle = 0
 
     @property
     def ndim(self):
@@ -178,9 +232,6 @@ class Array:
     @property
     def size(self):
         return int(np.prod(self.shape)) if self.shape else 1
-
-    def release(self):
-        self._fin()
 
     # ------------------------------------------------------------ host I/O
     def write(self, host: np.ndarray):
@@ -216,98 +267,97 @@ class Array:
             off.append(lo)
             shp.append(max(0, hi - lo))
         h = B.dfs_store_view(self.rt.ctx, self.handle, off, shp)
-        return Array(self.rt, h, shp, self.dtype)
+        return Array(self.rt, h, tuple(shp), self.dtype)
 
     def __setitem__(self, idx, value):
         view = self[idx]
-        view._unary("COPY", value, out=view)
+        _unary(_OP["COPY"], value, view, view)
 
     # ------------------------------------------------------------ tasking
     def _arg(self, priv):
         _, part = self.rt.layout(self.shape)
         return (self.handle, part, priv)
 
-    def _operand(self, v):
-        if isinstance(v, Array):
-            return v._arg(B.DFS_PRIV_R)
-        return float(v)
+    def __add__(self, o): return _binary(32, self, o, self)
+    def __radd__(self, o): return _binary(32, o, self, self)
+    def __sub__(self, o): return _binary(33, self, o, self)
+    def __rsub__(self, o): return _binary(33, o, self, self)
+    def __mul__(self, o): return _binary(34, self, o, self)
+    def __rmul__(self, o): return _binary(34, o, self, self)
+    def __truediv__(self, o): return _binary(35, self, o, self)
+    def __rtruediv__(self, o): return _binary(35, o, self, self)
+    def __pow__(self, o): return _binary(36, self, o, self)
+    def __neg__(self): return _unary(2, self, self)
 
-    def _domain_of(self, *xs):
-        best = None
-        for x in xs:
-            if isinstance(x, Array) and x.ndim > 0:
-                best = x
-                break
-        return self.rt.layout(best.shape if best is not None else ())[0], best
+    def __iadd__(self, o): return _binary(32, self, o, self, out=self)
+    def __isub__(self, o): return _binary(33, self, o, self, out=self)
+    def __imul__(self, o): return _binary(34, self, o, self, out=self)
+    def __itruediv__(self, o): return _binary(35, self, o, self, out=self)
 
-    def _binary(self, op, a, b, out=None):
-        dom, big = self._domain_of(a, b)
-        shape = big.shape if big is not None else ()
-        if out is None:
-            out = self.rt.empty(shape, self.dtype)
-        self.rt.submit(op, dom, [self._operand(a), self._operand(b), out._arg(B.DFS_PRIV_W)])
-        return out
 
-    def _unary(self, op, a, out=None):
-        dom, big = self._domain_of(a if isinstance(a, Array) else self)
-        target = out if out is not None else self.rt.empty(self.shape, self.dtype)
-        dom = self.rt.layout(target.shape)[0]
-        self.rt.submit(op, dom, [self._operand(a), target._arg(B.DFS_PRIV_W)])
-        return target
+def _binary(opcode, a, b, like: Array, out: Array | None = None) -> Array:
+    rt = like.rt
+    big = a if (a.__class__ is Array and a.shape) else (b if (b.__class__ is Array and b.shape) else like)
+    shape = big.shape
+    if out is None:
+        out = rt._new(shape, like.dtype)
+    lay = rt._layouts.get(shape) or rt._make_layout(shape)
+    rt._pack(0, a)
+    rt._pack(1, b)
+    olay = rt._layouts.get(out.shape) or rt._make_layout(out.shape)
+    _ARG.pack_into(rt._argbuf, 64, out.handle, olay[1], _W, 0, 0.0)
+    rt._issue(opcode, lay, 3)
+    return out
 
-    def __add__(self, o): return self._binary("ADD", self, o)
-    def __radd__(self, o): return self._binary("ADD", o, self)
-    def __sub__(self, o): return self._binary("SUB", self, o)
-    def __rsub__(self, o): return self._binary("SUB", o, self)
-    def __mul__(self, o): return self._binary("MUL", self, o)
-    def __rmul__(self, o): return self._binary("MUL", o, self)
-    def __truediv__(self, o): return self._binary("DIV", self, o)
-    def __rtruediv__(self, o): return self._binary("DIV", o, self)
-    def __pow__(self, o): return self._binary("POW", self, o)
-    def __neg__(self): return self._unary("NEG", self)
 
-    def __iadd__(self, o): return self._binary("ADD", self, o, out=self)
-    def __isub__(self, o): return self._binary("SUB", self, o, out=self)
-    def __imul__(self, o): return self._binary("MUL", self, o, out=self)
-    def __itruediv__(self, o): return self._binary("DIV", self, o, out=self)
+def _unary(opcode, a, like: Array, out: Array | None = None) -> Array:
+    rt = like.rt
+    if out is None:
+        out = rt._new(like.shape, like.dtype)
+    lay = rt._layouts.get(out.shape) or rt._make_layout(out.shape)
+    rt._pack(0, a)
+    _ARG.pack_into(rt._argbuf, 32, out.handle, lay[1], _W, 0, 0.0)
+    rt._issue(opcode, lay, 2)
+    return out
 
 
 # ------------------------------------------------------------- functions
-def _map(op, x: Array) -> Array:
-    return x._unary(op, x)
-
-
-def exp(x): return _map("EXP", x)
-def log(x): return _map("LOG", x)
-def sqrt(x): return _map("SQRT", x)
-def erf(x): return _map("ERF", x)
-def absolute(x): return _map("ABS", x)
-def ncdf(x): return _map("NCDF", x)
-def copy(x): return _map("COPY", x)
-def maximum(a, b): return (a if isinstance(a, Array) else b)._binary("MAX", a, b)
-def minimum(a, b): return (a if isinstance(a, Array) else b)._binary("MIN", a, b)
+def exp(x): return _unary(4, x, x)
+def log(x): return _unary(5, x, x)
+def sqrt(x): return _unary(6, x, x)
+def erf(x): return _unary(7, x, x)
+def absolute(x): return _unary(3, x, x)
+def ncdf(x): return _unary(8, x, x)
+def copy(x): return _unary(1, x, x)
+def maximum(a, b): return _binary(37, a, b, a if isinstance(a, Array) else b)
+def minimum(a, b): return _binary(38, a, b, a if isinstance(a, Array) else b)
 
 
 def full(rt: Runtime, shape, value: float, dtype=np.float64) -> Array:
     out = rt.empty(shape, dtype)
-    dom = rt.layout(out.shape)[0]
-    rt.submit("COPY", dom, [float(value), out._arg(B.DFS_PRIV_W)])
+    return _unary(1, float(value), out, out)
+
+
+def _reduce(opcode, x: Array, y: Array | None) -> Array:
+    rt = x.rt
+    out = rt._new((), x.dtype)
+    lay = rt._layouts.get(x.shape) or rt._make_layout(x.shape)
+    rt._pack(0, x)
+    n = 1
+    if y is not None:
+        rt._pack(1, y)
+        n = 2
+    _ARG.pack_into(rt._argbuf, 32 * n, out.handle, rt.none, _RD, _SUM, 0.0)
+    rt._issue(opcode, lay, n + 1)
     return out
 
 
 def dot(x: Array, y: Array) -> Array:
-    out = x.rt.empty((), x.dtype)
-    dom = x.rt.layout(x.shape)[0]
-    x.rt.submit("DOT", dom, [x._arg(B.DFS_PRIV_R), y._arg(B.DFS_PRIV_R),
-                             (out.handle, x.rt.none, B.DFS_PRIV_RD, B.DFS_REDOP_SUM)])
-    return out
+    return _reduce(64, x, y)
 
 
 def asum(x: Array) -> Array:
-    out = x.rt.empty((), x.dtype)
-    dom = x.rt.layout(x.shape)[0]
-    x.rt.submit("SUM", dom, [x._arg(B.DFS_PRIV_R), (out.handle, x.rt.none, B.DFS_PRIV_RD, B.DFS_REDOP_SUM)])
-    return out
+    return _reduce(65, x, None)
 
 
 def norm(x: Array) -> Array:
@@ -328,14 +378,18 @@ class CSR:
         self.dtype = self.val.dtype
 
     def __matmul__(self, x: Array) -> Array:
-        y = self.rt.empty((self.nrows,), self.dtype)
+        y = self.rt._new((self.nrows,), self.dtype)
         self.spmv(x, y)
         return y
 
     def spmv(self, x: Array, y: Array):
-        dom, part = self.rt.layout(y.shape)
-        n = self.rt.none
-        self.rt.submit("SPMV", dom, [(self.rowptr.handle, n, B.DFS_PRIV_R), (self.col.handle, n, B.DFS_PRIV_R),
-                                     (self.val.handle, n, B.DFS_PRIV_R), (x.handle, n, B.DFS_PRIV_R),
-                                     (y.handle, part, B.DFS_PRIV_W)])
+        rt = self.rt
+        lay = rt._layouts.get(y.shape) or rt._make_layout(y.shape)
+        n = rt.none
+        _ARG.pack_into(rt._argbuf, 0, self.rowptr.handle, n, _R, 0, 0.0)
+        _ARG.pack_into(rt._argbuf, 32, self.col.handle, n, _R, 0, 0.0)
+        _ARG.pack_into(rt._argbuf, 64, self.val.handle, n, _R, 0, 0.0)
+        _ARG.pack_into(rt._argbuf, 96, x.handle, n, _R, 0, 0.0)
+        _ARG.pack_into(rt._argbuf, 128, y.handle, lay[1], _W, 0, 0.0)
+        rt._issue(96, lay, 5)
         return y

@@ -222,35 +222,55 @@ Plan analyse(const std::vector<Task>& w, const std::map<int64_t, RootInfo>& root
 }
 
 // ------------------------------------------------------------- Section 5.2
+// The key is a compact binary string (raw 64-bit words): task ops and
+// domains, and per argument the first-occurrence number of its root, the
+// privilege and the normalised partition; each root's dtype, shape and
+// liveness bits are recorded at its first occurrence.  Immediate values and
+// store identities are left out, so isomorphic windows share a key.
 std::string canonical_key(const std::vector<Task>& w, const std::map<int64_t, RootInfo>& roots) {
-  std::map<int64_t, int> ids;
-  std::ostringstream o;
+  std::map<int64_t, int64_t> ids;
+  std::string o;
+  o.reserve(w.size() * 256);
+  auto put = [&o](int64_t v) { o.append(reinterpret_cast<const char*>(&v), sizeof v); };
   for (const Task& t : w) {
-    o << "op" << t.op << "<";
-    for (int d = 0; d < t.dnd; ++d) o << t.dom[d] << (d + 1 < t.dnd ? "x" : "");
-    o << ">(";
+    put(-1 - t.op);
+    put(t.dnd);
+    for (int d = 0; d < t.dnd; ++d) put(t.dom[d]);
+    put((int64_t)t.args.size());
     for (const Arg& a : t.args) {
       if (a.imm) {
-        o << "imm,";
+        put(-7);
         continue;
       }
       auto it = ids.find(a.root);
-      int id;
       if (it == ids.end()) {
-        id = (int)ids.size();
+        const int64_t id = (int64_t)ids.size();
         ids[a.root] = id;
         const RootInfo& ri = roots.at(a.root);
-        o << "#" << id << "{t" << a.dtype << "s";
-        for (int d = 0; d < ri.ndim; ++d) o << ri.shape[d] << ".";
-        o << (ri.app_live ? "A" : "a") << (ri.wrapped ? "W" : "w") << (ri.valid ? "V" : "v") << "}";
+        put(-8);
+        put(a.dtype);
+        put(ri.ndim);
+        for (int d = 0; d < ri.ndim; ++d) put(ri.shape[d]);
+        put((ri.app_live ? 1 : 0) | (ri.wrapped ? 2 : 0) | (ri.valid ? 4 : 0));
+        put(id);
       } else {
-        id = it->second;
+        put(it->second);
       }
-      o << id << ":" << a.priv << ":" << a.redop << ":" << a.part.key() << ",";
+      put(a.priv * 16 + a.redop);
+      const NPart& p = a.part;
+      put(p.kind * 16 + p.nd);
+      for (int d = 0; d < p.nd; ++d) {
+        put(p.vlo[d]);
+        put(p.vhi[d]);
+        if (p.kind) {
+          put(p.tile[d]);
+          put(p.off[d]);
+          put(p.proj[d]);
+        }
+      }
     }
-    o << ")";
   }
-  return o.str();
+  return o;
 }
 
 }  // namespace dfs

@@ -76,6 +76,14 @@ struct dfs_ctx {
   std::unordered_map<std::string, std::unique_ptr<dfs::CachedWindow>> wcache;
   dfs::Stats st;
   std::string last_source;
+  // per-launch device timing (cfg.time_launches)
+  struct Timed {
+    cudaEvent_t a, b;
+    std::string name;
+  };
+  std::vector<Timed> timed;
+  std::vector<cudaEvent_t> event_pool;
+  std::map<std::string, std::pair<double, int64_t>> ktime;  // kernel -> (ms, launches)
 };
 
 namespace dfs {
@@ -252,17 +260,16 @@ WindowInfo window_info(dfs_ctx* c) {
       ri.valid = r.valid;
       wi.roots[a.root] = ri;
     }
-  std::ostringstream k;
-  k << "f" << c->cfg.fusion << "m" << c->cfg.launch_mode << "b" << c->cfg.block_threads << "u" << c->cfg.unroll
-    << "x" << c->cfg.debug_skip_arrival
-    << "c" << c->cfg.ctas_per_sm << "|";
+  // configuration, pointer alignment of every root, then the window's form
+  std::string& k = wi.key;
+  const int64_t head[] = {c->cfg.fusion, c->cfg.launch_mode, c->cfg.block_threads, c->cfg.unroll,
+                          c->cfg.debug_skip_arrival, c->cfg.ctas_per_sm};
+  k.append(reinterpret_cast<const char*>(head), sizeof head);
   for (int64_t r : wi.by_canon) {
     const StoreRec& s = c->stores.at(r);
-    const bool al = s.ptr ? ((uintptr_t)s.ptr % 16 == 0) : true;
-    k << (al ? "a" : "u");
+    k.push_back((s.ptr && (uintptr_t)s.ptr % 16 != 0) ? 'u' : 'a');
   }
-  k << "|" << canonical_key(c->window, wi.roots);
-  wi.key = k.str();
+  k += canonical_key(c->window, wi.roots);
   return wi;
 }
 
@@ -501,6 +508,18 @@ int run_window(dfs_ctx* c, const CachedWindow& cw, const WindowInfo& wi) {
     void* params[] = {bp};
     // the kernel takes one struct parameter: pass its bytes as the argument
     CUresult cr;
+    dfs_ctx::Timed tm{nullptr, nullptr, L.name};
+    if (c->cfg.time_launches) {
+      for (cudaEvent_t* e : {&tm.a, &tm.b}) {
+        if (!c->event_pool.empty()) {
+          *e = c->event_pool.back();
+          c->event_pool.pop_back();
+        } else {
+          CUDA_OK(cudaEventCreate(e));
+        }
+      }
+      CUDA_OK(cudaEventRecord(tm.a, c->stream));
+    }
     if (L.cooperative)
       cr = c->drv.LaunchCooperativeKernel(L.k->fn, L.grid, 1, 1, L.block, 1, 1, 0, (CUstream)c->stream, params);
     else
@@ -509,6 +528,10 @@ int run_window(dfs_ctx* c, const CachedWindow& cw, const WindowInfo& wi) {
       const char* s = nullptr;
       c->drv.GetErrorString(cr, &s);
       return fail(c, DFS_ERR_CUDA, std::string("launch of ") + L.name + ": " + (s ? s : "?"));
+    }
+    if (c->cfg.time_launches) {
+      CUDA_OK(cudaEventRecord(tm.b, c->stream));
+      c->timed.push_back(tm);
     }
     c->st.launches += 1;
     c->st.last_regs = L.k->regs;
@@ -667,6 +690,11 @@ int dfs_shutdown(dfs_ctx* c) {
       if (kv.second.owned && kv.second.ptr) cudaFreeAsync(kv.second.ptr, c->stream);
     if (c->partials) cudaFreeAsync(c->partials, c->stream);
     cudaStreamSynchronize(c->stream);
+    for (auto& t : c->timed) {
+      cudaEventDestroy(t.a);
+      cudaEventDestroy(t.b);
+    }
+    for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
     if (c->ctl) cudaFree(c->ctl);
     c->jit.reset();
     if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -930,6 +958,17 @@ int dfs_sync(dfs_ctx* c) {
   int rc = flush(c);
   if (rc) return rc;
   CUDA_OK(cudaStreamSynchronize(c->stream));
+  for (auto& t : c->timed) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+      auto& kt = c->ktime[t.name];
+      kt.first += ms;
+      kt.second += 1;
+    }
+    c->event_pool.push_back(t.a);
+    c->event_pool.push_back(t.b);
+  }
+  c->timed.clear();
   return check_device_error(c);
 }
 
@@ -958,6 +997,14 @@ int dfs_stats_json(dfs_ctx* c, char* buf, size_t len, size_t* needed) {
       << ", \"kernel_cache_hits\": " << c->jit->hits() << ", \"kernel_disk_hits\": " << c->jit->disk_hits();
   o << ", \"last_regs\": " << s.last_regs << ", \"last_occupancy\": " << s.last_occupancy
     << ", \"last_grid\": " << s.last_grid << ", \"last_block\": " << s.last_block;
+  o << ", \"kernel_times\": {";
+  bool first = true;
+  for (const auto& kv : c->ktime) {
+    o << (first ? "" : ", ") << "\"" << kv.first << "\": {\"ms\": " << kv.second.first
+      << ", \"launches\": " << kv.second.second << "}";
+    first = false;
+  }
+  o << "}";
   o << ", \"sms\": " << c->sms << "}";
   return write_json(o.str(), buf, len, needed);
 }

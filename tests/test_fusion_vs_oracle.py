@@ -38,6 +38,8 @@ class World:
             self.views.append(v)
             self.view_of[v.handle] = (self.full[k % 2].handle, lo, hi)
         self.scal = [rt.empty((), np.float64) for _ in range(2)]
+        self.full_h = [a.handle for a in self.full]
+        self.scal_h = [a.handle for a in self.scal]
         self.T4 = rt.tiling((4,))
         self.T2 = rt.tiling((2,))
 
@@ -49,7 +51,7 @@ class World:
             r, lo, hi = self.view_of[h]
             return ir.Tiling((2,), (lo,), ir.IDENTITY, ((lo,), (hi,)))
         if part == self.rt.none:
-            return ir.NonePart(((), ())) if h in [s.handle for s in self.scal] else ir.NonePart(((0,), (N,)))
+            return ir.NonePart(((), ())) if h in self.scal_h else ir.NonePart(((0,), (N,)))
         return ir.Tiling((4,), (0,), ir.IDENTITY, ((0,), (N,)))
 
 
@@ -116,19 +118,18 @@ def test_random_windows_match_oracle(seed):
             assert ir.non_interfering(t), (op, args)
             tasks.append(t)
         # drop some application references before planning
-        live = {}
-        for arr in w.full + w.scal:
-            live[arr.handle] = True
+        live = {h: True for h in w.full_h + w.scal_h}
         for arr in rng.sample(w.full + w.scal, rng.randint(0, 4)):
             live[arr.handle] = False
             arr.release()
         if any(not live[w.root(v.handle)] for v in w.views):
             pass
         for v in w.views:       # views keep their root alive while they live
+            root = w.root(v.handle)
             if rng.random() < 0.5:
                 v.release()
             else:
-                live[w.root(v.handle)] = True
+                live[root] = True
         plan = rt.plan()
         groups = [(g[0], g[-1] + 1) for g in plan["groups"]]
         assert groups == ir.partition_window(tasks), (trial, plan)
@@ -136,8 +137,8 @@ def test_random_windows_match_oracle(seed):
             assert ir.fusible_sequence(tasks[s:e])
         # temporaries: roots temporary in every group referencing them (Def. 4)
         roots = {a.store for t in tasks for a in t.args}
-        shapes = {h: ((0,), (N,)) for h in [a.handle for a in w.full]}
-        shapes.update({s.handle: ((), ()) for s in w.scal})
+        shapes = {h: ((0,), (N,)) for h in w.full_h}
+        shapes.update({h: ((), ()) for h in w.scal_h})
         want_exact, want_any = set(), set()
         for r in roots:
             refs, temp = 0, 0
