@@ -56,7 +56,8 @@ typedef enum {
   DFS_ERR_OOM = -5,             /* device allocation failed */
   DFS_ERR_BARRIER_TIMEOUT = -6, /* a grid barrier gave up waiting (deferred) */
   DFS_ERR_STATE = -7,           /* handle released / unknown, or wrong call order */
-  DFS_ERR_BUFFER = -8           /* caller's buffer too small (see *needed) */
+  DFS_ERR_BUFFER = -8,          /* caller's buffer too small (see *needed) */
+  DFS_ERR_TOO_LARGE = -9        /* input exceeds a fixed capacity (dfs_dot_noalloc) */
 } dfs_status;
 
 typedef enum { DFS_F32 = 0, DFS_F64 = 1, DFS_I32 = 2, DFS_I64 = 3 } dfs_dtype;
@@ -239,6 +240,39 @@ int dfs_last_kernel_source(dfs_ctx *ctx, char *buf, size_t len, size_t *needed);
 
 /* ABI version (major*100 + minor). */
 int dfs_version(void);
+
+/*
+ * dfs_dot_noalloc -- *out = sum_i x[i]*y[i] over n FP64 elements, computed on
+ * `stream` (a cudaStream_t; NULL = the legacy default stream) of the current
+ * device WITHOUT allocating any device memory.
+ *
+ * The paper has no counterpart: this entry point serves callers that cannot
+ * allocate when they need a reduction -- code running under CUDA stream
+ * capture (cudaMalloc is not allowed there and breaks the capture), serving
+ * loops that reserve all device memory at start-up, and plug-ins whose host
+ * framework owns every device allocation.
+ *
+ * x, y: device pointers to n doubles (8-byte aligned); out: device pointer to
+ * one double.  All three are owned by the caller.  The result is written
+ * asynchronously on `stream`.  Summation order is fixed (one partial per
+ * DFS_NOALLOC_TILE elements, a fixed tree inside each block, partials summed
+ * in order), so repeated calls give identical bits.
+ *
+ * Scratch: a file-scope __device__ array of DFS_NOALLOC_MAX_N /
+ * DFS_NOALLOC_TILE doubles plus a 32-byte counter, held by every GPU that
+ * loads the library until the process exits.  Every call on a device shares
+ * it, so calls whose kernels overlap on the GPU (different streams, no
+ * ordering between them) race and give wrong results; order them.
+ * The first call on each device resolves the scratch's device address with
+ * that device current; make that first call before any stream capture.
+ *
+ * Returns DFS_OK; DFS_ERR_INVALID for null pointers or n < 0;
+ * DFS_ERR_TOO_LARGE when n > DFS_NOALLOC_MAX_N (nothing is launched);
+ * DFS_ERR_CUDA when a CUDA call fails.  n == 0 writes 0.0.
+ */
+#define DFS_NOALLOC_TILE 4096
+#define DFS_NOALLOC_MAX_N (16384LL * DFS_NOALLOC_TILE) /* 2^26 elements; 128 KB of scratch */
+int dfs_dot_noalloc(const double *x, const double *y, int64_t n, double *out, void *stream);
 
 #ifdef __cplusplus
 }

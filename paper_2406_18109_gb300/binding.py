@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libdiffuse.so")
 DFS_OK = 0
 STATUS = {0: "DFS_OK", -1: "DFS_ERR_INVALID", -2: "DFS_ERR_NO_DEVICE", -3: "DFS_ERR_CUDA",
           -4: "DFS_ERR_COMPILE", -5: "DFS_ERR_OOM", -6: "DFS_ERR_BARRIER_TIMEOUT",
-          -7: "DFS_ERR_STATE", -8: "DFS_ERR_BUFFER"}
+          -7: "DFS_ERR_STATE", -8: "DFS_ERR_BUFFER", -9: "DFS_ERR_TOO_LARGE"}
 DFS_F32, DFS_F64, DFS_I32, DFS_I64 = 0, 1, 2, 3
 DFS_PRIV_R, DFS_PRIV_W, DFS_PRIV_RW, DFS_PRIV_RD, DFS_PRIV_IMM = 1, 2, 3, 4, 8
 DFS_REDOP_NONE, DFS_REDOP_SUM = 0, 1
@@ -34,7 +34,7 @@ EXPORTS = ("dfs_config_default", "dfs_init", "dfs_shutdown", "dfs_store_create",
            "dfs_store_view", "dfs_store_release", "dfs_store_write", "dfs_store_read",
            "dfs_store_device_ptr", "dfs_partition_none", "dfs_partition_tiling", "dfs_submit",
            "dfs_flush", "dfs_sync", "dfs_last_error", "dfs_plan_json", "dfs_stats_json",
-           "dfs_last_kernel_source", "dfs_version")
+           "dfs_last_kernel_source", "dfs_version", "dfs_dot_noalloc")
 
 
 class dfs_config(C.Structure):
@@ -88,6 +88,7 @@ def lib():
             "dfs_stats_json": (C.c_int, [P, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
             "dfs_last_kernel_source": (C.c_int, [P, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
             "dfs_version": (C.c_int, []),
+            "dfs_dot_noalloc": (C.c_int, [P, P, I64, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -233,3 +234,15 @@ def dfs_last_kernel_source(ctx) -> str:
 
 def dfs_version() -> int:
     return lib().dfs_version()
+
+
+NOALLOC_TILE = 4096
+NOALLOC_MAX_N = 16384 * NOALLOC_TILE
+
+
+def dfs_dot_noalloc(x_ptr: int, y_ptr: int, n: int, out_ptr: int, stream: int = 0) -> None:
+    """Dot product of two device vectors into a device double, allocating nothing."""
+    rc = lib().dfs_dot_noalloc(C.c_void_p(x_ptr), C.c_void_p(y_ptr), n, C.c_void_p(out_ptr),
+                               C.c_void_p(stream) if stream else None)
+    if rc != DFS_OK:
+        raise DfsError(rc, "dfs_dot_noalloc failed")
