@@ -160,7 +160,7 @@ def kernel_delta(before: dict, after: dict) -> dict:
 class Arm:
     """One timed configuration of a workload: build state, warm up, time K steps."""
 
-    def __init__(self, workload, rt_kwargs, torch, stream, e2e=False):
+    def __init__(self, workload, rt_kwargs, torch, stream, e2e=False, graph=False):
         from paper_2406_18109_gb300 import arrays as A
         from paper_2406_18109_gb300 import dist as D
         from paper_2406_18109_gb300 import workloads as W
@@ -190,6 +190,20 @@ class Arm:
             self.b = self.Am @ self.rt.array(xs)
             self.units = cfg["iters"]
             self.step = self._cg
+            if graph:
+                # the whole solve (reset + 50 in-place iterations) captured once
+                # after one normally issued iteration, then replayed per step
+                self.s = W.cg_start_inplace(self.b)
+                W.cg_iteration_inplace(self.Am, self.s)
+                self.rt.flush()
+                self.rt.capture_begin()
+                W.cg_reset_inplace(self.s, self.b)
+                self.rt.flush()
+                for _ in range(cfg["iters"]):
+                    W.cg_iteration_inplace(self.Am, self.s)
+                    self.rt.flush()
+                self.graph = self.rt.capture_end()
+                self.step = self._cg_graph
         else:
             cfg = self.cfg = configs.JACOBI
             grid = inputs.jacobi_grid(cfg["N"], seed=cfg["seed"])
@@ -220,6 +234,9 @@ class Arm:
             self.W.cg_iteration(self.Am, st)
             self.rt.flush()
         self.keep = st
+
+    def _cg_graph(self):
+        self.rt.graph_launch(self.graph)
 
     def _jacobi(self):
         per = self.cfg["sweeps_per_flush"]
@@ -270,9 +287,15 @@ def main():
     ap.add_argument("--workload", default="bs", choices=["bs", "cg", "jacobi"])
     ap.add_argument("--quick", action="store_true", help="skip the comparison arms (for profiling)")
     ap.add_argument("--bs-n", type=int, default=0, help="Black-Scholes batch size (profiling a smaller case)")
+    ap.add_argument("--jac-n", type=int, default=0, help="Jacobi interior size N (profiling a smaller case)")
+    ap.add_argument("--sweeps", type=int, default=0, help="Jacobi sweeps per step (profiling)")
     args = ap.parse_args()
     if args.bs_n:
         configs.BLACK_SCHOLES["n"] = args.bs_n
+    if args.jac_n:
+        configs.JACOBI["N"] = args.jac_n
+    if args.sweeps:
+        configs.JACOBI["sweeps"] = args.sweeps
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     metric, unit, dtype = METRIC[args.workload]
@@ -316,14 +339,18 @@ def main():
     if "rows" in cfg:
         base["rows"] = cfg["rows"]
 
-    def arm(kw, steps, warmup, e2e=False):
-        a = Arm(args.workload, kw, torch, stream, e2e=e2e)
+    # CG: the iteration windows are captured once (memoised windows + a CUDA
+    # graph) and replayed; the Python-issued runs are reported beside them
+    graph = args.workload == "cg"
+
+    def arm(kw, steps, warmup, e2e=False, graph=graph):
+        a = Arm(args.workload, kw, torch, stream, e2e=e2e, graph=graph)
         try:
             return a.run(steps, warmup)
         finally:
             a.close()
 
-    fused_arm = Arm(args.workload, dict(base, fusion=True, launch="persistent"), torch, stream)
+    fused_arm = Arm(args.workload, dict(base, fusion=True, launch="persistent"), torch, stream, graph=graph)
     clocks = Clocks(dev)
     if world > 1:
         torch.distributed.barrier()
@@ -347,6 +374,13 @@ def main():
                                    "kernel_ms_per_step": sum(v["ms"] for v in pt["kernels"].values()) / k2}
         extra["fused_vs_unfused"] = value / world / extra["unfused"]["value"]
         extra["fused_kernel_ms_per_step"] = sum(v["ms"] for v in fused["kernels"].values()) / args.steps
+        if graph:
+            nf = arm(dict(base, fusion=True, launch="persistent"), k2, 2, graph=False)
+            nu = arm(dict(base, fusion=False, launch="per_task"), k2, 2, graph=False)
+            extra["python_issued"] = {
+                "fused": {"value": nf["units"] / (nf["ms"] / 1e3), "ms_per_step": nf["ms"] / k2},
+                "unfused": {"value": nu["units"] / (nu["ms"] / 1e3), "ms_per_step": nu["ms"] / k2},
+                "note": "each iteration issued from Python (11 tasks + flush); host-bound"}
         if args.workload == "bs":
             e = arm(dict(base, fusion=True, launch="persistent"), k2, 2, e2e=True)
             extra["e2e"] = {"value": e["units"] / (e["ms"] / 1e3), "unit": unit,
@@ -367,6 +401,20 @@ def main():
                 "frac": achieved / peaks["hbm_gbs"], "traffic": None,
                 "peak_source": peaks["source"], "kernel": fused["dominant"], "kernel_ms": kern_ms,
                 "launches": fused["dominant_launches"], "algorithmic_bytes_per_launch": alg_bytes}
+    if args.workload == "bs":
+        # issue-bound: instructions per option (ncu) x options / kernel time,
+        # against SMs x 4 sub-partitions x 32 lanes x maximum SM clock
+        sm_max = clk.get("sm_max_mhz") or 2070.0
+        peak_ti = sms * 4 * 32 * sm_max * 1e6 / 1e12
+        ach_ti = cfg["inst_per_option"] * cfg["n"] / (kern_ms / 1e3) / 1e12 if kern_ms > 0 else 0.0
+        roofline = {"bound": "alu", "achieved": ach_ti, "peak": peak_ti, "unit": "T thread-inst/s",
+                    "frac": ach_ti / peak_ti, "traffic": None,
+                    "peak_source": f"derived: {sms} SMs x 4 SMSPs x 32 lanes x {sm_max:.0f} MHz",
+                    "inst_per_option": cfg["inst_per_option"], "kernel": fused["dominant"],
+                    "kernel_ms": kern_ms, "launches": fused["dominant_launches"],
+                    "hbm": {"achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                            "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"],
+                            "algorithmic_bytes_per_launch": alg_bytes}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.quick:
@@ -378,7 +426,9 @@ def main():
             "vs_baseline": None, "dtype": dtype, "data": "synthetic (seeded generators of synth/inputs.py)",
             "config": {"workload": WORKLOAD[args.workload],
                        "l2": "inputs larger than L2" if args.workload != "cg"
-                       else "working set L2-resident (10 MB); no flush", "launch": "persistent fused",
+                       else "working set L2-resident (10 MB); no flush",
+                       "launch": "persistent fused" + (", each solve replayed from a CUDA graph of the memoised "
+                                                        "iteration windows" if graph else ""),
                        "parallelism": f"replicas x{world}"},
             "e2e": extra.pop("e2e", None), "gpu_launches": fused["launches"], "roofline": roofline,
             "cpu_baseline": cpu, "clocks": clk}

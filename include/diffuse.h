@@ -235,6 +235,33 @@ int dfs_plan_json(dfs_ctx *ctx, char *buf, size_t len, size_t *needed);
  * kernel cache hits/misses, NVRTC compile seconds, bytes allocated. */
 int dfs_stats_json(dfs_ctx *ctx, char *buf, size_t len, size_t *needed);
 
+/*
+ * CUDA-graph capture of flushed windows.  The paper memoises the analysis and
+ * code generation of isomorphic windows (Section 5.2); capture goes one step
+ * further and records the launches themselves, so a steady-state loop body
+ * (e.g. one iteration of an iterative solver whose state lives in stores the
+ * application holds and updates in place) can be replayed with no host-side
+ * issue cost.
+ *
+ * dfs_capture_begin flushes, then records instead of executing: every launch
+ * of the following flushes, and the stream-ordered allocations and frees of
+ * stores created and released inside the captured region, go into a graph.
+ * Bookkeeping (which stores hold values) advances as if the work ran once.
+ * dfs_capture_end flushes, ends the capture and instantiates the graph into
+ * *out.  The captured work has NOT run; dfs_graph_launch runs it (any number
+ * of times) on the context stream, on the same device addresses and with the
+ * same immediate values.
+ * Restrictions (DFS_ERR_STATE otherwise): no dfs_store_read / dfs_sync while
+ * capturing; a store created inside the captured region must be released
+ * before dfs_capture_end; stores the graph uses stay allocated until
+ * dfs_graph_destroy even if released (replays may read them).
+ */
+typedef int64_t dfs_graph;
+int dfs_capture_begin(dfs_ctx *ctx);
+int dfs_capture_end(dfs_ctx *ctx, dfs_graph *out);
+int dfs_graph_launch(dfs_ctx *ctx, dfs_graph g);
+int dfs_graph_destroy(dfs_ctx *ctx, dfs_graph g);
+
 /* Source of the generated CUDA for the most recent launch (debugging). */
 int dfs_last_kernel_source(dfs_ctx *ctx, char *buf, size_t len, size_t *needed);
 

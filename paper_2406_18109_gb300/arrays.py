@@ -199,6 +199,19 @@ class Runtime:
     def kernel_source(self) -> str:
         return B.dfs_last_kernel_source(self.ctx)
 
+    # ------------------------------------------------------- graph capture
+    def capture_begin(self):
+        B.dfs_capture_begin(self.ctx)
+
+    def capture_end(self) -> int:
+        return B.dfs_capture_end(self.ctx)
+
+    def graph_launch(self, graph: int):
+        B.dfs_graph_launch(self.ctx, graph)
+
+    def graph_destroy(self, graph: int):
+        B.dfs_graph_destroy(self.ctx, graph)
+
 
 class Array:
     """A store (or view) handle; operators submit one index task each."""
@@ -254,6 +267,8 @@ class Array:
 
     # --------------------------------------------------------------- views
     def __getitem__(self, idx) -> "Array":
+        if idx is Ellipsis:
+            idx = ()
         if not isinstance(idx, tuple):
             idx = (idx,)
         if len(idx) > self.ndim:

@@ -34,7 +34,8 @@ EXPORTS = ("dfs_config_default", "dfs_init", "dfs_shutdown", "dfs_store_create",
            "dfs_store_view", "dfs_store_release", "dfs_store_write", "dfs_store_read",
            "dfs_store_device_ptr", "dfs_partition_none", "dfs_partition_tiling", "dfs_submit",
            "dfs_flush", "dfs_sync", "dfs_last_error", "dfs_plan_json", "dfs_stats_json",
-           "dfs_last_kernel_source", "dfs_version", "dfs_dot_noalloc")
+           "dfs_last_kernel_source", "dfs_version", "dfs_dot_noalloc", "dfs_capture_begin",
+           "dfs_capture_end", "dfs_graph_launch", "dfs_graph_destroy")
 
 
 class dfs_config(C.Structure):
@@ -89,6 +90,10 @@ def lib():
             "dfs_last_kernel_source": (C.c_int, [P, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
             "dfs_version": (C.c_int, []),
             "dfs_dot_noalloc": (C.c_int, [P, P, I64, P, P]),
+            "dfs_capture_begin": (C.c_int, [P]),
+            "dfs_capture_end": (C.c_int, [P, pI64]),
+            "dfs_graph_launch": (C.c_int, [P, I64]),
+            "dfs_graph_destroy": (C.c_int, [P, I64]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -230,6 +235,24 @@ def dfs_stats_json(ctx) -> dict:
 
 def dfs_last_kernel_source(ctx) -> str:
     return _json_call(lib().dfs_last_kernel_source, ctx)
+
+
+def dfs_capture_begin(ctx) -> None:
+    _check(ctx, lib().dfs_capture_begin(ctx))
+
+
+def dfs_capture_end(ctx) -> int:
+    out = C.c_int64()
+    _check(ctx, lib().dfs_capture_end(ctx, C.byref(out)))
+    return out.value
+
+
+def dfs_graph_launch(ctx, graph: int) -> None:
+    _check(ctx, lib().dfs_graph_launch(ctx, graph))
+
+
+def dfs_graph_destroy(ctx, graph: int) -> None:
+    _check(ctx, lib().dfs_graph_destroy(ctx, graph))
 
 
 def dfs_version() -> int:

@@ -4,7 +4,11 @@ check exactly the launch configuration the benchmark times."""
 
 # Black-Scholes: 2^26 FP32 options (spot U[5,30], strike U[1,100], expiry
 # U[0.25,10], r = 0.02, sigma = 0.3, seed 1)
-BLACK_SCHOLES = dict(n=1 << 26, seed=1, r=0.02, sigma=0.3, tile=16384, block=256, unroll=1)
+BLACK_SCHOLES = dict(n=1 << 26, seed=1, r=0.02, sigma=0.3, tile=16384, block=256, unroll=1,
+                     # thread instructions per option of the fused kernel (ncu
+                     # smsp__inst_executed x 32 / options); the kernel is bound
+                     # by instruction issue, see profiles/
+                     inst_per_option=190.0)
 
 # CG: 2-D 5-point Poisson on a 256x256 grid, 50 iterations, FP64 values,
 # int32 indices, x* ~ U[-1,1] (seed 0), b = A x*, x0 = 0

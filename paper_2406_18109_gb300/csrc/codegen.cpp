@@ -116,7 +116,7 @@ class Gen {
   void emit_group(int g);
   void emit_scalar_group(int g);
   void emit_vector_group(int g);
-  void emit_nest(int g, const Nest& n, const std::string& red_pt);
+  void emit_nest(int g, const Nest& n, const std::string& red_pt, bool flat);
   void emit_finalise(const char* indent);
   std::vector<Nest> nests_of(int g);
   std::string imm_expr(int task, int arg, int dt);
@@ -277,6 +277,23 @@ void Gen::emit_vector_group(int g) {
   const int64_t npts = t0.npoints();
   kc.max_points = std::max(kc.max_points, npts);
   std::vector<Nest> nests = nests_of(g);
+  // A group with one loop nest and no reduction needs no per-point
+  // structure: the union of the points' sub-stores is one rectangle of
+  // contiguous tiles (every operand has the same tile shape and offsets
+  // relative to its view), so it is swept as one range with a grid stride,
+  // which balances the work across CTAs at element granularity.
+  bool flat = nests.size() == 1;
+  for (int i = G.begin; i < G.end && flat; ++i)
+    if (is_reduction(S.tasks[i].op)) flat = false;
+  if (flat && space_arg(t0).nd > 2) flat = false;
+  if (flat) {
+    kc.has_flat = true;
+    o << "    { // group " << g << ": tasks " << G.begin << ".." << G.end - 1 << ", one flat nest over "
+      << npts << " points\n";
+    emit_nest(g, nests[0], "", true);
+    o << "    }\n";
+    return;
+  }
   o << "    { // group " << g << ": tasks " << G.begin << ".." << G.end - 1 << ", " << nests.size()
     << " loop nest(s), " << npts << " points\n";
   o << "      for (i64 pt = blockIdx.x; pt < " << npts << "LL; pt += gridDim.x) {\n";
@@ -290,13 +307,13 @@ void Gen::emit_vector_group(int g) {
   }
   for (size_t k = 0; k < nests.size(); ++k) {
     if (k) o << "        __syncthreads();\n";
-    emit_nest(g, nests[k], "pt");
+    emit_nest(g, nests[k], "pt", false);
   }
   o << "      }\n";
   o << "    }\n";
 }
 
-void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar) {
+void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
   const int BD = S.block;
   const int U = std::max(1, S.unroll);
   const int V = n.vec;
@@ -313,6 +330,8 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar) {
     std::ostringstream s;
     if (a.part.kind == 0) {
       s << a.part.vlo[d] << "LL";
+    } else if (flat) {
+      s << std::max(a.part.off[d], a.part.vlo[d]) << "LL";
     } else {
       s << "max(q" << a.part.proj[d] << " * " << a.part.tile[d] << "LL + (" << a.part.off[d] << "LL), "
         << a.part.vlo[d] << "LL)";
@@ -332,9 +351,16 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar) {
     return nm;
   };
   // ---- extents of the iteration space
+  int64_t flat_cells = 1;  // elements of a flat range (constant)
   for (int d = 0; d < nd; ++d) {
     if (sa.part.kind == 0) {
       o << ind << "  const i64 ext" << d << " = " << (sa.part.vhi[d] - sa.part.vlo[d]) << "LL;\n";
+    } else if (flat) {
+      const int64_t cnt = first.dom[sa.part.proj[d]];
+      const int64_t lo = std::max(sa.part.off[d], sa.part.vlo[d]);
+      const int64_t hi = std::min(cnt * sa.part.tile[d] + sa.part.off[d], sa.part.vhi[d]);
+      flat_cells *= std::max<int64_t>(0, hi - lo);
+      o << ind << "  const i64 ext" << d << " = " << std::max<int64_t>(0, hi - lo) << "LL;\n";
     } else {
       o << ind << "  const i64 ext" << d << " = min(q" << sa.part.proj[d] << " * " << sa.part.tile[d]
         << "LL + (" << sa.part.off[d] << "LL) + " << sa.part.tile[d] << "LL, " << sa.part.vhi[d]
@@ -512,51 +538,75 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar) {
     }
   };
 
+  // block-stride loops inside a point, grid-stride loops over a flat range
+  const std::string st0 = flat ? "((i64)blockIdx.x * " + std::to_string(BD) + " + threadIdx.x)" : "(i64)threadIdx.x";
+  const std::string stp = flat ? "gs" : std::to_string(BD);
+  if (flat) o << ind << "  const i64 gs = (i64)gridDim.x * " << BD << ";\n";
+  auto slot_off = [&](int u) { return flat ? std::to_string(u) + " * gs" : std::to_string(u * BD); };
   if (n.dims == 1) {
-    // flat: n elements; vectors of V; main loop unrolled U
+    // n elements in one contiguous range; vectors of V; main loop unrolled U
     o << ind << "  const i64 n = ";
     for (int d = 0; d < nd; ++d) o << (d ? " * " : "") << "ext" << d;
     o << ";\n";
     o << ind << "  if (n > 0) {\n";
+    const std::string it = V > 1 ? "v" : "e";
+    const std::string lim = V > 1 ? "nv" : "n";
+    if (V > 1) o << ind << "    const i64 nv = n / " << V << ";\n";
+    o << ind << "    i64 " << it << " = " << st0 << ";\n";
+    auto flat_e = [&](const std::string& x) { return V > 1 ? "(" + x + ") * " + std::to_string(V) : "(" + x + ")"; };
+    if (U > 1) {
+      o << ind << "    for (; " << it << " + " << slot_off(U - 1) << " < " << lim << "; " << it << " += " << U
+        << " * " << stp << ") {\n";
+      std::vector<std::string> sl, ef, er, ec;
+      for (int u = 0; u < U; ++u) {
+        sl.push_back("u" + std::to_string(u));
+        ef.push_back(flat_e(it + " + " + slot_off(u)));
+        er.push_back("");
+        ec.push_back("");
+      }
+      body(V, sl, ef, er, ec, ind + "      ");
+      o << ind << "    }\n";
+    }
+    o << ind << "    for (; " << it << " < " << lim << "; " << it << " += " << stp << ") {\n";
+    body(V, {"r"}, {flat_e(it)}, {""}, {""}, ind + "      ");
+    o << ind << "    }\n";
     if (V > 1) {
-      o << ind << "    const i64 nv = n / " << V << ";\n";
-      o << ind << "    i64 v = threadIdx.x;\n";
-      if (U > 1) {
-        o << ind << "    for (; v + " << (U - 1) * BD << " < nv; v += " << U * BD << ") {\n";
-        std::vector<std::string> sl, ef, er, ec;
-        for (int u = 0; u < U; ++u) {
-          sl.push_back("u" + std::to_string(u));
-          ef.push_back("(v + " + std::to_string(u * BD) + ") * " + std::to_string(V));
-          er.push_back("");
-          ec.push_back("");
-        }
-        body(V, sl, ef, er, ec, ind + "      ");
-        o << ind << "    }\n";
-      }
-      o << ind << "    for (; v < nv; v += " << BD << ") {\n";
-      body(V, {"r"}, {"v * " + std::to_string(V)}, {""}, {""}, ind + "      ");
-      o << ind << "    }\n";
-      o << ind << "    for (i64 e = nv * " << V << " + threadIdx.x; e < n; e += " << BD << ") {\n";
-      body(1, {"t"}, {"e"}, {""}, {""}, ind + "      ");
-      o << ind << "    }\n";
-    } else {
-      o << ind << "    i64 e = threadIdx.x;\n";
-      if (U > 1) {
-        o << ind << "    for (; e + " << (U - 1) * BD << " < n; e += " << U * BD << ") {\n";
-        std::vector<std::string> sl, ef, er, ec;
-        for (int u = 0; u < U; ++u) {
-          sl.push_back("u" + std::to_string(u));
-          ef.push_back("(e + " + std::to_string(u * BD) + ")");
-          er.push_back("");
-          ec.push_back("");
-        }
-        body(1, sl, ef, er, ec, ind + "      ");
-        o << ind << "    }\n";
-      }
-      o << ind << "    for (; e < n; e += " << BD << ") {\n";
+      o << ind << "    for (i64 e = nv * " << V << " + " << st0 << "; e < n; e += " << stp << ") {\n";
       body(1, {"t"}, {"e"}, {""}, {""}, ind + "      ");
       o << ind << "    }\n";
     }
+    o << ind << "  }\n";
+  } else if (flat) {
+    // a rectangle of ext0 rows x ext1 columns swept as one range of
+    // (row, vector) cells with a grid stride
+    o << ind << "  const i64 nvr = ext1 / " << V << ";\n";
+    o << ind << "  const i64 ncell = ext0 * nvr;\n";
+    o << ind << "  i64 c = " << st0 << ";\n";
+    // 32-bit division by the constant row length when the range allows it
+    const bool narrow = flat_cells < (int64_t(1) << 31);
+    auto cell = [&](const std::string& cv, const std::string& sfx) {
+      if (narrow)
+        o << ind << "      const i64 i" << sfx << " = (i64)((u32)(" << cv << ") / (u32)nvr);\n";
+      else
+        o << ind << "      const i64 i" << sfx << " = (" << cv << ") / nvr;\n";
+      o << ind << "      const i64 j" << sfx << " = ((" << cv << ") - i" << sfx << " * nvr) * " << V << ";\n";
+    };
+    if (U > 1) {
+      o << ind << "  for (; c + " << slot_off(U - 1) << " < ncell; c += " << U << " * gs) {\n";
+      std::vector<std::string> sl, ef, er, ec;
+      for (int u = 0; u < U; ++u) {
+        cell("c + " + slot_off(u), std::to_string(u));
+        sl.push_back("u" + std::to_string(u));
+        ef.push_back("");
+        er.push_back("i" + std::to_string(u));
+        ec.push_back("j" + std::to_string(u));
+      }
+      body(V, sl, ef, er, ec, ind + "      ");
+      o << ind << "  }\n";
+    }
+    o << ind << "  for (; c < ncell; c += gs) {\n";
+    cell("c", "r");
+    body(V, {"r"}, {""}, {"ir"}, {"jr"}, ind + "      ");
     o << ind << "  }\n";
   } else {
     // rows: each row of ext1 elements is swept by the whole block

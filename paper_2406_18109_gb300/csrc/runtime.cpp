@@ -84,6 +84,18 @@ struct dfs_ctx {
   std::vector<Timed> timed;
   std::vector<cudaEvent_t> event_pool;
   std::map<std::string, std::pair<double, int64_t>> ktime;  // kernel -> (ms, launches)
+  // CUDA-graph capture
+  bool capturing = false;
+  std::set<int64_t> captured_allocs;    // roots allocated inside the capture
+  std::vector<void*> capture_deferred;  // pre-capture memory released while capturing
+  int64_t capture_launches = 0;
+  struct GraphRec {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<void*> owned;           // memory freed when the graph is destroyed
+    int64_t launches = 0;
+  };
+  std::map<int64_t, GraphRec> graphs;
 };
 
 namespace dfs {
@@ -112,7 +124,15 @@ void maybe_free(dfs_ctx* c, int64_t root) {
   if (it == c->stores.end()) return;
   StoreRec& r = it->second;
   if (r.app_refs > 0 || r.pending > 0) return;
-  if (r.owned && r.ptr && c->device) cudaFreeAsync(r.ptr, c->stream);
+  if (r.owned && r.ptr && c->device) {
+    if (c->capturing && !c->captured_allocs.count(root)) {
+      // allocated before the capture: replays of the graph may still read it
+      c->capture_deferred.push_back(r.ptr);
+    } else {
+      cudaFreeAsync(r.ptr, c->stream);  // recorded as a free node while capturing
+    }
+  }
+  c->captured_allocs.erase(root);
   c->stores.erase(it);
 }
 
@@ -126,6 +146,7 @@ int materialise(dfs_ctx* c, StoreRec& r) {
     return fail(c, DFS_ERR_OOM, std::string("cudaMallocAsync(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
   }
   r.owned = true;
+  if (c->capturing) c->captured_allocs.insert(r.handle);
   c->st.bytes_allocated += (int64_t)bytes;
   c->st.allocations += 1;
   return DFS_OK;
@@ -442,7 +463,7 @@ int build_window(dfs_ctx* c, const WindowInfo& wi, std::unique_ptr<CachedWindow>
     L.cooperative = kc.nbarriers > 0;
     bool all_scalar = true;
     for (const Group& G : spec.groups) all_scalar &= G.scalar;
-    int64_t want = all_scalar ? 1 : kc.max_points;
+    int64_t want = all_scalar ? 1 : (kc.has_flat ? INT64_MAX : kc.max_points);
     int per_sm = comp->occupancy > 0 ? comp->occupancy : 1;
     if (c->cfg.ctas_per_sm > 0) per_sm = std::min(per_sm, c->cfg.ctas_per_sm);
     const int64_t cap = (int64_t)per_sm * c->sms;
@@ -478,6 +499,8 @@ int run_window(dfs_ctx* c, const CachedWindow& cw, const WindowInfo& wi) {
   }
   for (const CachedLaunch& L : cw.launches) {
     if (L.partial_bytes > c->partials_cap) {
+      if (c->capturing)
+        return fail(c, DFS_ERR_STATE, "reduction scratch would grow inside a capture: run the window once first");
       if (c->partials) cudaFreeAsync(c->partials, c->stream);
       c->partials = nullptr;
       size_t cap = std::max<size_t>(L.partial_bytes, 4096);
@@ -509,7 +532,8 @@ int run_window(dfs_ctx* c, const CachedWindow& cw, const WindowInfo& wi) {
     // the kernel takes one struct parameter: pass its bytes as the argument
     CUresult cr;
     dfs_ctx::Timed tm{nullptr, nullptr, L.name};
-    if (c->cfg.time_launches) {
+    const bool timing = c->cfg.time_launches && !c->capturing;
+    if (timing) {
       for (cudaEvent_t* e : {&tm.a, &tm.b}) {
         if (!c->event_pool.empty()) {
           *e = c->event_pool.back();
@@ -529,11 +553,14 @@ int run_window(dfs_ctx* c, const CachedWindow& cw, const WindowInfo& wi) {
       c->drv.GetErrorString(cr, &s);
       return fail(c, DFS_ERR_CUDA, std::string("launch of ") + L.name + ": " + (s ? s : "?"));
     }
-    if (c->cfg.time_launches) {
+    if (timing) {
       CUDA_OK(cudaEventRecord(tm.b, c->stream));
       c->timed.push_back(tm);
     }
-    c->st.launches += 1;
+    if (c->capturing)
+      c->capture_launches += 1;
+    else
+      c->st.launches += 1;
     c->st.last_regs = L.k->regs;
     c->st.last_occupancy = L.k->occupancy;
     c->st.last_grid = L.grid;
@@ -684,8 +711,21 @@ int dfs_shutdown(dfs_ctx* c) {
   if (!c) return DFS_OK;
   int rc = DFS_OK;
   if (c->device) {
+    if (c->capturing) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(c->stream, &g);
+      if (g) cudaGraphDestroy(g);
+      c->capturing = false;
+      for (void* p : c->capture_deferred) cudaFreeAsync(p, c->stream);
+    }
     rc = flush(c);
     cudaStreamSynchronize(c->stream);
+    for (auto& kv : c->graphs) {
+      cudaGraphExecDestroy(kv.second.exec);
+      cudaGraphDestroy(kv.second.graph);
+      for (void* p : kv.second.owned) cudaFreeAsync(p, c->stream);
+    }
+    c->graphs.clear();
     for (auto& kv : c->stores)
       if (kv.second.owned && kv.second.ptr) cudaFreeAsync(kv.second.ptr, c->stream);
     if (c->partials) cudaFreeAsync(c->partials, c->stream);
@@ -812,6 +852,7 @@ int dfs_store_read(dfs_ctx* c, dfs_store s, void* host_dst, size_t bytes) {
   StoreRec* r = find_store(c, s);
   if (!r) return fail(c, DFS_ERR_STATE, "unknown or released store");
   if (!c->device) return fail(c, DFS_ERR_NO_DEVICE, "analysis-only context");
+  if (c->capturing) return fail(c, DFS_ERR_STATE, "dfs_store_read while capturing");
   const size_t es = dtype_size(r->dtype);
   if (bytes != (size_t)r->nelem() * es) return fail(c, DFS_ERR_INVALID, "byte count does not match the store");
   int rc = flush(c);
@@ -955,6 +996,7 @@ int dfs_flush(dfs_ctx* c) {
 int dfs_sync(dfs_ctx* c) {
   if (!c) return DFS_ERR_INVALID;
   if (!c->device) return DFS_OK;
+  if (c->capturing) return fail(c, DFS_ERR_STATE, "dfs_sync while capturing");
   int rc = flush(c);
   if (rc) return rc;
   CUDA_OK(cudaStreamSynchronize(c->stream));
@@ -970,6 +1012,103 @@ int dfs_sync(dfs_ctx* c) {
   }
   c->timed.clear();
   return check_device_error(c);
+}
+
+int dfs_capture_begin(dfs_ctx* c) {
+  if (!c) return DFS_ERR_INVALID;
+  if (!c->device) return fail(c, DFS_ERR_NO_DEVICE, "analysis-only context");
+  if (c->capturing) return fail(c, DFS_ERR_STATE, "already capturing");
+  int rc = flush(c);
+  if (rc) return rc;
+  // reduction scratch cannot be reallocated inside a capture: reserve 1 MB
+  const size_t want = 1 << 20;
+  if (c->partials_cap < want) {
+    if (c->partials) cudaFreeAsync(c->partials, c->stream);
+    c->partials = nullptr;
+    CUDA_OK(cudaMallocAsync(&c->partials, want, c->stream));
+    c->partials_cap = want;
+  }
+  CUDA_OK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  c->capturing = true;
+  c->captured_allocs.clear();
+  c->capture_deferred.clear();
+  c->capture_launches = 0;
+  return DFS_OK;
+}
+
+int dfs_capture_end(dfs_ctx* c, dfs_graph* out) {
+  if (!c || !out) return DFS_ERR_INVALID;
+  if (!c->capturing) return fail(c, DFS_ERR_STATE, "not capturing");
+  int rc = flush(c);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+  c->capturing = false;
+  std::vector<void*> deferred;
+  deferred.swap(c->capture_deferred);
+  auto give_back = [&]() {
+    for (void* p : deferred) cudaFreeAsync(p, c->stream);
+    // addresses handed out inside an abandoned capture belong to no live
+    // allocation: those stores lose their memory (and value)
+    for (int64_t r : c->captured_allocs) {
+      auto it = c->stores.find(r);
+      if (it == c->stores.end()) continue;
+      it->second.ptr = nullptr;
+      it->second.owned = false;
+      it->second.valid = false;
+    }
+    c->captured_allocs.clear();
+  };
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    give_back();
+    return rc;
+  }
+  if (e != cudaSuccess || !graph) {
+    give_back();
+    return fail(c, DFS_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+  }
+  if (!c->captured_allocs.empty()) {
+    cudaGraphDestroy(graph);
+    give_back();
+    return fail(c, DFS_ERR_STATE, "a store created inside the captured region is still referenced");
+  }
+  dfs_ctx::GraphRec g;
+  g.graph = graph;
+  const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+  if (ie != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    give_back();
+    return fail(c, DFS_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+  }
+  g.owned.swap(deferred);
+  g.launches = c->capture_launches;
+  const int64_t h = c->next_handle++;
+  c->graphs[h] = std::move(g);
+  *out = h;
+  return DFS_OK;
+}
+
+int dfs_graph_launch(dfs_ctx* c, dfs_graph h) {
+  if (!c) return DFS_ERR_INVALID;
+  auto it = c->graphs.find(h);
+  if (it == c->graphs.end()) return fail(c, DFS_ERR_STATE, "unknown graph");
+  if (c->capturing) return fail(c, DFS_ERR_STATE, "cannot launch a graph while capturing");
+  int rc = flush(c);
+  if (rc) return rc;
+  CUDA_OK(cudaGraphLaunch(it->second.exec, c->stream));
+  c->st.launches += it->second.launches;
+  return DFS_OK;
+}
+
+int dfs_graph_destroy(dfs_ctx* c, dfs_graph h) {
+  if (!c) return DFS_ERR_INVALID;
+  auto it = c->graphs.find(h);
+  if (it == c->graphs.end()) return fail(c, DFS_ERR_STATE, "unknown graph");
+  cudaGraphExecDestroy(it->second.exec);
+  cudaGraphDestroy(it->second.graph);
+  for (void* p : it->second.owned) cudaFreeAsync(p, c->stream);
+  c->graphs.erase(it);
+  return DFS_OK;
 }
 
 const char* dfs_last_error(dfs_ctx* c) { return c ? c->err.c_str() : "null context"; }

@@ -82,6 +82,45 @@ def cg_iteration(Amat: CSR, s: CGState) -> None:
     s.p = s.r + beta * s.p
 
 
+@dataclass
+class CGInPlace:
+    """CG state held in fixed stores, updated in place (q, x, r, p, rho), so
+    that one iteration is a steady-state window sequence that can be captured
+    once and replayed (no store is created that outlives the iteration)."""
+    x: Array
+    r: Array
+    p: Array
+    q: Array
+    rho: Array
+
+
+def cg_start_inplace(b: Array) -> CGInPlace:
+    st = cg_start(b)
+    q = b.rt.empty(b.shape, b.dtype)
+    return CGInPlace(st.x, st.r, st.p, q, st.rho)
+
+
+def cg_reset_inplace(s: CGInPlace, b: Array) -> None:
+    """x = 0, r = b, p = b, rho = r.r, written into the existing state stores."""
+    s.x[...] = 0.0
+    s.r[...] = b
+    s.p[...] = b
+    s.rho[...] = A.dot(s.r, s.r)
+
+
+def cg_iteration_inplace(Amat: CSR, s: CGInPlace) -> None:
+    """One CG iteration writing only into the state stores (12 tasks)."""
+    Amat.spmv(s.p, s.q)
+    alpha = s.rho / A.dot(s.p, s.q)
+    s.x += alpha * s.p
+    s.r -= alpha * s.q
+    rho_new = A.dot(s.r, s.r)
+    beta = rho_new / s.rho
+    s.rho[...] = rho_new
+    s.p *= beta
+    s.p += s.r
+
+
 def jacobi_views(grid: Array):
     """center, north, east, west, south views of an (N+2)x(N+2) grid (Fig. 1a)."""
     return (grid[1:-1, 1:-1], grid[0:-2, 1:-1], grid[1:-1, 2:], grid[1:-1, 0:-2], grid[2:, 1:-1])

@@ -167,6 +167,19 @@ def test_cg_plan_two_iterations_memo_key():
     assert k1 == k2
 
 
+def test_capture_api_needs_a_device_and_checks_state():
+    rt = rt0()
+    with pytest.raises(B.DfsError) as e:
+        rt.capture_begin()
+    assert e.value.code == -2
+    with pytest.raises(B.DfsError) as e:
+        rt.capture_end()
+    assert e.value.code == -7
+    with pytest.raises(B.DfsError) as e:
+        rt.graph_launch(12345)
+    assert e.value.code == -7
+
+
 def test_window_size_triggers_analysis():
     rt = rt0(tile=4, window_size=3)
     a = rt.empty((8,), np.float32)
