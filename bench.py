@@ -278,6 +278,46 @@ class Arm:
         self.rt.close()
 
 
+def compile_report(torch, stream, sms) -> dict:
+    """Warm-up cost of compilation (Section 7.2, Fig. 13): first step (which
+    compiles every kernel with NVRTC, no on-disk cache) and steady-state step,
+    unfused vs fused, and the steps needed for fusion to pay for compiling."""
+    from paper_2406_18109_gb300 import arrays as A
+    # NVRTC's one-time start-up (loading its builtins) is paid here, by a
+    # kernel none of the measured windows uses
+    with A.Runtime(device=torch.cuda.current_device(), stream=stream.cuda_stream) as rt:
+        (A.full(rt, (1000,), 1.0) * 3.0).numpy()
+    out = {}
+    for wl in ("bs", "cg", "jacobi"):
+        cfg = {"bs": configs.BLACK_SCHOLES, "cg": configs.CG, "jacobi": configs.JACOBI}[wl]
+        base = dict(block=cfg["block"], unroll=cfg["unroll"], sms=sms)
+        for k in ("tile", "rows"):
+            if k in cfg:
+                base[k] = cfg[k]
+        row = {}
+        for name, kw in (("standard", dict(fusion=False, launch="per_task")),
+                         ("compiled", dict(fusion=True, launch="persistent"))):
+            a = Arm(wl, dict(base, **kw), torch, stream)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            a.step()
+            a.rt.sync()
+            first = time.perf_counter() - t0
+            r = a.run(3, 1)
+            st = a.rt.stats()
+            a.close()
+            row[name] = {"first_step_s": first, "steady_step_s": r["ms"] / 3 / 1e3,
+                         "compile_s": st.get("compile_s"), "kernels": st.get("kernels_compiled")}
+        s, c = row["standard"], row["compiled"]
+        gain = s["steady_step_s"] - c["steady_step_s"]
+        extra = c["first_step_s"] - s["first_step_s"]
+        row["breakeven_steps"] = (extra / gain) if (extra > 0 and gain > 0) else None
+        row["step"] = {"bs": "one 2^26-option batch", "cg": "one 50-iteration solve",
+                       "jacobi": "200 sweeps"}[wl]
+        out[wl] = row
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -289,6 +329,10 @@ def main():
     ap.add_argument("--bs-n", type=int, default=0, help="Black-Scholes batch size (profiling a smaller case)")
     ap.add_argument("--jac-n", type=int, default=0, help="Jacobi interior size N (profiling a smaller case)")
     ap.add_argument("--sweeps", type=int, default=0, help="Jacobi sweeps per step (profiling)")
+    for k in ("block", "unroll", "tile", "rows"):
+        ap.add_argument(f"--{k}", type=int, default=0, help=f"override the workload's {k} (tuning)")
+    ap.add_argument("--compile-report", action="store_true",
+                    help="print the warm-up/compilation cost table instead of the bench line")
     args = ap.parse_args()
     if args.bs_n:
         configs.BLACK_SCHOLES["n"] = args.bs_n
@@ -331,6 +375,9 @@ def main():
     from paper_2406_18109_gb300 import _build
     from paper_2406_18109_gb300 import dist as D
     _build.build()
+    if args.compile_report:
+        print(json.dumps({"compile_report": compile_report(torch, stream, sms)}))
+        return
 
     cfg = {"bs": configs.BLACK_SCHOLES, "cg": configs.CG, "jacobi": configs.JACOBI}[args.workload]
     base = dict(block=cfg["block"], unroll=cfg["unroll"], sms=sms, cache_dir=cache)
@@ -338,6 +385,9 @@ def main():
         base["tile"] = cfg["tile"]
     if "rows" in cfg:
         base["rows"] = cfg["rows"]
+    for k in ("block", "unroll", "tile", "rows"):       # command-line overrides (tuning)
+        if getattr(args, k):
+            base[k] = getattr(args, k)
 
     # CG: the iteration windows are captured once (memoised windows + a CUDA
     # graph) and replayed; the Python-issued runs are reported beside them
@@ -396,6 +446,12 @@ def main():
     else:
         alg_bytes = 16 * cfg["N"] * cfg["N"]               # one sweep (one launch)
     kern_ms = fused["dominant_ms"]
+    if graph:
+        # launches replayed from a graph are not timed one by one: use the
+        # replayed time per iteration (kernel plus the gap to the next node)
+        kern_ms = fused["ms"] / (args.steps * cfg["iters"])
+        fused["dominant"] = "CG iteration kernel, graph replay (time per iteration incl. launch gap)"
+        fused["dominant_launches"] = args.steps * cfg["iters"]
     achieved = alg_bytes / (kern_ms / 1e3) / 1e9 if kern_ms > 0 else 0.0
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": None,

@@ -162,7 +162,9 @@ class Runtime:
         return self._new(tuple(int(s) for s in shape), np.dtype(dtype))
 
     def array(self, host: np.ndarray) -> "Array":
-        host = np.ascontiguousarray(host)
+        host = np.asarray(host)
+        if not host.flags.c_contiguous:       # (ascontiguousarray would make 0-d arrays 1-d)
+            host = np.ascontiguousarray(host)
         a = self.empty(host.shape, host.dtype)
         a.write(host)
         return a

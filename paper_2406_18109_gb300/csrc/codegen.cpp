@@ -275,7 +275,6 @@ void Gen::emit_vector_group(int g) {
   const Group& G = S.groups[g];
   const Task& t0 = S.tasks[G.begin];
   const int64_t npts = t0.npoints();
-  kc.max_points = std::max(kc.max_points, npts);
   std::vector<Nest> nests = nests_of(g);
   // A group with one loop nest and no reduction needs no per-point
   // structure: the union of the points' sub-stores is one rectangle of
@@ -294,6 +293,8 @@ void Gen::emit_vector_group(int g) {
     o << "    }\n";
     return;
   }
+  kc.has_points = true;
+  kc.max_points = std::max(kc.max_points, npts);
   o << "    { // group " << g << ": tasks " << G.begin << ".." << G.end - 1 << ", " << nests.size()
     << " loop nest(s), " << npts << " points\n";
   o << "      for (i64 pt = blockIdx.x; pt < " << npts << "LL; pt += gridDim.x) {\n";

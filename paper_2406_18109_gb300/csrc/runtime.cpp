@@ -463,7 +463,10 @@ int build_window(dfs_ctx* c, const WindowInfo& wi, std::unique_ptr<CachedWindow>
     L.cooperative = kc.nbarriers > 0;
     bool all_scalar = true;
     for (const Group& G : spec.groups) all_scalar &= G.scalar;
-    int64_t want = all_scalar ? 1 : (kc.has_flat ? INT64_MAX : kc.max_points);
+    // per-point groups want one CTA per point (more CTAs would only wait at
+    // the barriers); kernels made only of flat sweeps use every resident CTA
+    int64_t want = 1;
+    if (!all_scalar) want = kc.has_points ? kc.max_points : (kc.has_flat ? INT64_MAX : 1);
     int per_sm = comp->occupancy > 0 ? comp->occupancy : 1;
     if (c->cfg.ctas_per_sm > 0) per_sm = std::min(per_sm, c->cfg.ctas_per_sm);
     const int64_t cap = (int64_t)per_sm * c->sms;

@@ -179,7 +179,8 @@ struct KernelCode {
   int nimm = 0;
   int nred = 0;         // reduction slots
   int64_t max_points = 1;
-  bool has_flat = false;  // some group sweeps a flat range: use every resident CTA
+  bool has_flat = false;    // some group sweeps a flat range
+  bool has_points = false;  // some group deals points to CTAs (max_points of them)
   int nbarriers = 0;
   std::vector<int64_t> red_points;  // points of each reduction slot
   std::vector<double> imms;         // immediate values in parameter order
