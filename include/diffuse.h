@@ -262,6 +262,37 @@ int dfs_capture_end(dfs_ctx *ctx, dfs_graph *out);
 int dfs_graph_launch(dfs_ctx *ctx, dfs_graph g);
 int dfs_graph_destroy(dfs_ctx *ctx, dfs_graph g);
 
+/*
+ * Batched execution of isomorphic windows (GB300 extension of the
+ * memoisation of Section 5.2 to many problems at once).
+ *
+ * Between dfs_batch_begin and dfs_batch_end the application submits K
+ * instances of one task sequence -- e.g. one iteration of each of K
+ * independent solves of different sizes -- calling dfs_batch_next after each
+ * instance.  The instances must be isomorphic: the same operations and
+ * privileges, the same pattern of store, partition and launch-domain
+ * identities, and the same liveness of their stores; sizes, tiles, store
+ * addresses and immediate values may differ.  dfs_batch_end runs the fusion
+ * pass once, generates one size-generic kernel whose sizes, pointers and
+ * immediates come from per-instance descriptors in device memory, and
+ * launches it once: each phase processes the points of all K instances
+ * through a work list, so the uneven problems share one persistent launch
+ * and its grid barriers.  Reductions keep one partial per point and each
+ * instance's scalars are finished in a fixed order, so every instance's
+ * results are bit-identical to running it alone with the same tiles.
+ *
+ * Batches whose instances are not isomorphic, or that use stores of rank
+ * other than 0 and 1, are executed as an ordinary flush of all their tasks
+ * (same results, no batching); dfs_stats_json counts both cases.
+ * Descriptor tables are cached by content, so a batch that repeats the same
+ * stores (in-place iterations) uploads nothing and can be captured in a
+ * CUDA graph after it has run once.
+ * Returns DFS_ERR_STATE for calls out of order.
+ */
+int dfs_batch_begin(dfs_ctx *ctx);
+int dfs_batch_next(dfs_ctx *ctx);
+int dfs_batch_end(dfs_ctx *ctx);
+
 /* Source of the generated CUDA for the most recent launch (debugging). */
 int dfs_last_kernel_source(dfs_ctx *ctx, char *buf, size_t len, size_t *needed);
 

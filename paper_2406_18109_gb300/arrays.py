@@ -201,6 +201,19 @@ class Runtime:
     def kernel_source(self) -> str:
         return B.dfs_last_kernel_source(self.ctx)
 
+    # ------------------------------------------------------------ batching
+    def batch_begin(self):
+        """Start a batch of isomorphic instances (see dfs_batch_begin)."""
+        B.dfs_batch_begin(self.ctx)
+
+    def batch_next(self):
+        """End the current instance of the batch."""
+        B.dfs_batch_next(self.ctx)
+
+    def batch_end(self):
+        """Run the batch: one launch over every instance."""
+        B.dfs_batch_end(self.ctx)
+
     # ------------------------------------------------------- graph capture
     def capture_begin(self):
         B.dfs_capture_begin(self.ctx)

@@ -35,7 +35,8 @@ EXPORTS = ("dfs_config_default", "dfs_init", "dfs_shutdown", "dfs_store_create",
            "dfs_store_device_ptr", "dfs_partition_none", "dfs_partition_tiling", "dfs_submit",
            "dfs_flush", "dfs_sync", "dfs_last_error", "dfs_plan_json", "dfs_stats_json",
            "dfs_last_kernel_source", "dfs_version", "dfs_dot_noalloc", "dfs_capture_begin",
-           "dfs_capture_end", "dfs_graph_launch", "dfs_graph_destroy")
+           "dfs_capture_end", "dfs_graph_launch", "dfs_graph_destroy", "dfs_batch_begin",
+           "dfs_batch_next", "dfs_batch_end")
 
 
 class dfs_config(C.Structure):
@@ -94,6 +95,9 @@ def lib():
             "dfs_capture_end": (C.c_int, [P, pI64]),
             "dfs_graph_launch": (C.c_int, [P, I64]),
             "dfs_graph_destroy": (C.c_int, [P, I64]),
+            "dfs_batch_begin": (C.c_int, [P]),
+            "dfs_batch_next": (C.c_int, [P]),
+            "dfs_batch_end": (C.c_int, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -253,6 +257,18 @@ def dfs_graph_launch(ctx, graph: int) -> None:
 
 def dfs_graph_destroy(ctx, graph: int) -> None:
     _check(ctx, lib().dfs_graph_destroy(ctx, graph))
+
+
+def dfs_batch_begin(ctx) -> None:
+    _check(ctx, lib().dfs_batch_begin(ctx))
+
+
+def dfs_batch_next(ctx) -> None:
+    _check(ctx, lib().dfs_batch_next(ctx))
+
+
+def dfs_batch_end(ctx) -> None:
+    _check(ctx, lib().dfs_batch_end(ctx))
 
 
 def dfs_version() -> int:

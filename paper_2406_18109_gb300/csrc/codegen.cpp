@@ -173,10 +173,11 @@ std::vector<Nest> Gen::nests_of(int g) {
   const Group& G = S.groups[g];
   std::vector<Nest> v;
   int i = G.begin;
+  while (i < G.end && S.tasks[i].scalar()) ++i;  // scalar tasks are hoisted
   while (i < G.end) {
     const std::string key = iteration_space_key(S.tasks[i]);
     int j = i + 1;
-    while (j < G.end && iteration_space_key(S.tasks[j]) == key) ++j;
+    while (j < G.end && (S.tasks[j].scalar() || iteration_space_key(S.tasks[j]) == key)) ++j;
     Nest n;
     n.first = i;
     n.last = j;
@@ -237,6 +238,7 @@ std::vector<Nest> Gen::nests_of(int g) {
     n.vec = aligned ? vec : 1;
     v.push_back(n);
     i = j;
+    while (i < G.end && S.tasks[i].scalar()) ++i;
   }
   return v;
 }
@@ -275,6 +277,31 @@ void Gen::emit_vector_group(int g) {
   const Group& G = S.groups[g];
   const Task& t0 = S.tasks[G.begin];
   const int64_t npts = t0.npoints();
+  // Scalar tasks can share a group with vector tasks when the launch domain
+  // has a single point.  They read and write 0-d values only, so every CTA
+  // evaluates them first, in program order (the one point may run anywhere);
+  // this is exact unless a vector task earlier in the group reads a value a
+  // later scalar task overwrites.
+  for (int i = G.begin; i < G.end; ++i) {
+    if (!S.tasks[i].scalar()) continue;
+    const int64_t out = S.tasks[i].args.back().root;
+    for (int j = G.begin; j < i; ++j)
+      if (!S.tasks[j].scalar())
+        for (const Arg& a : S.tasks[j].args)
+          if (!a.imm && a.root == out)
+            throw std::runtime_error("a scalar task overwrites a value read earlier in its group");
+    const Task& t = S.tasks[i];
+    const int dt = t.args.back().dtype;
+    std::vector<std::string> ins;
+    for (size_t k = 0; k + 1 < t.args.size(); ++k) {
+      const Arg& a = t.args[k];
+      ins.push_back(a.imm ? imm_expr(i, (int)k, dt) : "(" + T(dt) + ")" + sreg.at(a.root));
+    }
+    o << "    " << sreg.at(t.args.back().root) << " = " << op_fn(t.op) << "(";
+    for (size_t k = 0; k < ins.size(); ++k) o << (k ? ", " : "") << ins[k];
+    o << ");\n";
+    have[t.args.back().root] = true;
+  }
   std::vector<Nest> nests = nests_of(g);
   // A group with one loop nest and no reduction needs no per-point
   // structure: the union of the points' sub-stores is one rectangle of
@@ -380,6 +407,7 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
   std::vector<Acc> accs;
   for (int i = n.first; i < n.last; ++i) {
     const Task& t = S.tasks[i];
+    if (t.scalar()) continue;
     for (size_t ai = 0; ai < t.args.size(); ++ai) {
       const Arg& a = t.args[ai];
       if (a.imm || a.nd == 0) continue;
@@ -415,6 +443,7 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
   // SpMV gathered operands: bases of rowptr/col/val/x (None partitions)
   for (int i = n.first; i < n.last; ++i) {
     const Task& t = S.tasks[i];
+    if (t.scalar()) continue;
     if (t.op != DFS_OP_SPMV) continue;
     for (int ai = 0; ai < 4; ++ai) need_base(t.args[ai]);
   }
@@ -422,6 +451,7 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
   std::map<std::pair<int, int>, std::string> immv;
   for (int i = n.first; i < n.last; ++i) {
     const Task& t = S.tasks[i];
+    if (t.scalar()) continue;
     const int dt = t.args.back().dtype;
     for (size_t ai = 0; ai < t.args.size(); ++ai) {
       const Arg& a = t.args[ai];
@@ -471,6 +501,7 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
         }
         for (int i = n.first; i < n.last; ++i) {
           const Task& t = S.tasks[i];
+          if (t.scalar()) continue;
           const int dt = t.args.back().dtype;
           auto val = [&](size_t ai) -> std::string {
             const Arg& a = t.args[ai];
@@ -506,6 +537,7 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
         // collect outputs to store
         for (int i = n.first; i < n.last; ++i) {
           const Task& t = S.tasks[i];
+          if (t.scalar()) continue;
           const Arg* out = nullptr;
           if (is_elementwise(t.op)) out = &t.args.back();
           if (t.op == DFS_OP_SPMV) out = &t.args[4];
@@ -522,6 +554,7 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
       const Arg* a = nullptr;
       for (int i = n.first; i < n.last && !a; ++i) {
         const Task& t = S.tasks[i];
+        if (t.scalar()) continue;
         for (size_t ai = 0; ai < t.args.size(); ++ai)
           if (!t.args[ai].imm && akey(t.args[ai]) == kv.first) a = &t.args[ai];
       }
@@ -718,6 +751,8 @@ KernelCode Gen::run() {
 }
 
 }  // namespace
+
+const char* op_device_fn(int op) { return op_fn(op); }
 
 KernelCode generate(const LaunchSpec& spec) {
   Gen g(spec);

@@ -96,6 +96,24 @@ struct dfs_ctx {
     int64_t launches = 0;
   };
   std::map<int64_t, GraphRec> graphs;
+  // batched execution
+  bool batching = false;
+  std::vector<size_t> batch_marks;      // window positions where instances end
+  struct BatchEntry {
+    dfs::BatchCode code;
+    const dfs::Compiled* k = nullptr;
+    dfs::Plan plan;
+  };
+  std::unordered_map<std::string, std::unique_ptr<BatchEntry>> bcache;
+  struct Table {
+    void* dev = nullptr;
+    size_t bytes = 0;
+  };
+  std::unordered_map<std::string, Table> tables;  // descriptor bytes -> device copy
+  double* sval = nullptr;
+  size_t sval_cap = 0;
+  int64_t batches = 0, batched_instances = 0, batch_fallbacks = 0;
+  std::string batch_fallback_reason;
 };
 
 namespace dfs {
@@ -345,6 +363,96 @@ std::string plan_json(const Plan& p, const std::vector<Task>& w, const WindowInf
 }
 
 // Builds the cached form of a window: plan, generated and compiled kernels.
+// The launch of fused groups [g0, g1) of window w: its tasks, groups and the
+// role of every root (pointer parameter, temporary, 0-d value loaded before
+// or published after the launch).  `valid` is the value state before it.
+LaunchSpec make_spec(dfs_ctx* c, const std::vector<Task>& w, const std::map<int64_t, RootInfo>& roots,
+                     const Plan& P, int g0, int g1, std::map<int64_t, bool>& valid) {
+  const int t0 = P.groups[g0].begin, t1 = P.groups[g1 - 1].end;
+  LaunchSpec spec;
+  spec.block = c->cfg.block_threads;
+  spec.unroll = c->cfg.unroll;
+  spec.persistent = (g1 - g0) > 1;
+  spec.debug_skip = c->cfg.debug_skip_arrival;
+  for (int i = t0; i < t1; ++i) spec.tasks.push_back(w[i]);
+  for (int g = g0; g < g1; ++g) {
+    Group G = P.groups[g];
+    G.begin -= t0;
+    G.end -= t0;
+    spec.groups.push_back(G);
+  }
+  std::map<int64_t, std::pair<int, int>> tcount;  // groups referencing / temp in
+  for (int g = g0; g < g1; ++g) {
+    std::set<int64_t> seen;
+    for (int i = P.groups[g].begin; i < P.groups[g].end; ++i)
+      for (const Arg& a : w[i].args)
+        if (!a.imm) seen.insert(a.root);
+    for (int64_t r : seen) {
+      tcount[r].first++;
+      if (P.temps.count({g, r})) tcount[r].second++;
+    }
+  }
+  int nparam = 0;
+  for (int i = t0; i < t1; ++i)
+    for (const Arg& a : w[i].args) {
+      if (a.imm || spec.root_index.count(a.root)) continue;
+      const StoreRec& s = c->stores.at(a.root);
+      LaunchRoot lr{};
+      lr.root = a.root;
+      lr.dtype = s.dtype;
+      lr.ndim = s.ndim;
+      for (int d = 0; d < MAXD; ++d) {
+        lr.shape[d] = d < s.ndim ? s.shape[d] : 1;
+        lr.stride[d] = d < s.ndim ? s.stride[d] : 1;
+      }
+      lr.zero_d = s.ndim == 0;
+      lr.valid_before = valid[a.root];
+      lr.aligned16 = s.ptr ? ((uintptr_t)s.ptr % 16 == 0) : true;
+      lr.param = -1;
+      spec.root_index[a.root] = (int)spec.roots.size();
+      spec.roots.push_back(lr);
+    }
+  for (LaunchRoot& lr : spec.roots) {
+    for (int i = t0; i < t1; ++i)
+      for (const Arg& a : w[i].args) {
+        if (a.imm || a.root != lr.root) continue;
+        lr.written |= a.is_w() || a.is_rd();
+        lr.read |= a.is_r();
+      }
+    const auto& tc = tcount[lr.root];
+    const RootInfo& ri = roots.at(lr.root);
+    if (lr.zero_d) {
+      // 0-d values live in registers; memory is needed to load a prior value
+      // or to publish the result beyond this launch
+      bool used_later = false;
+      for (int i = t1; i < (int)w.size(); ++i)
+        for (const Arg& a : w[i].args)
+          if (!a.imm && a.root == lr.root && (a.is_r() || a.is_rd())) used_later = true;
+      lr.live_out = lr.written && (ri.app_live || ri.wrapped || used_later);
+      lr.temp = !lr.live_out;
+      bool load = false;
+      if (lr.valid_before) {
+        // first access in program order decides whether the old value is used
+        for (int i = t0; i < t1 && !load; ++i) {
+          bool touched = false;
+          for (const Arg& a : w[i].args) {
+            if (a.imm || a.root != lr.root) continue;
+            touched = true;
+            if (a.is_r() || a.is_rd()) load = true;
+          }
+          if (touched) break;
+        }
+      }
+      lr.valid_before = lr.valid_before && load;
+      if (load || lr.live_out) lr.param = nparam++;
+    } else {
+      lr.temp = c->cfg.fusion && tc.first > 0 && tc.first == tc.second;
+      if (!lr.temp) lr.param = nparam++;
+    }
+  }
+  return spec;
+}
+
 int build_window(dfs_ctx* c, const WindowInfo& wi, std::unique_ptr<CachedWindow>& out) {
   const auto& w = c->window;
   auto cw = std::make_unique<CachedWindow>();
@@ -357,89 +465,9 @@ int build_window(dfs_ctx* c, const WindowInfo& wi, std::unique_ptr<CachedWindow>
   for (size_t li = 0; li < P.launches.size(); ++li) {
     const int g0 = P.launches[li].first, g1 = P.launches[li].second;
     const int t0 = P.groups[g0].begin, t1 = P.groups[g1 - 1].end;
-    LaunchSpec spec;
-    spec.block = c->cfg.block_threads;
-    spec.unroll = c->cfg.unroll;
-    spec.persistent = (g1 - g0) > 1;
-    spec.debug_skip = c->cfg.debug_skip_arrival;
-    for (int i = t0; i < t1; ++i) spec.tasks.push_back(w[i]);
-    for (int g = g0; g < g1; ++g) {
-      Group G = P.groups[g];
-      G.begin -= t0;
-      G.end -= t0;
-      spec.groups.push_back(G);
-    }
-    // roots of the launch
-    std::map<int64_t, std::pair<int, int>> tcount;  // groups referencing / temp in
-    for (int g = g0; g < g1; ++g) {
-      std::set<int64_t> seen;
-      for (int i = P.groups[g].begin; i < P.groups[g].end; ++i)
-        for (const Arg& a : w[i].args)
-          if (!a.imm) seen.insert(a.root);
-      for (int64_t r : seen) {
-        tcount[r].first++;
-        if (P.temps.count({g, r})) tcount[r].second++;
-      }
-    }
-    int nparam = 0;
-    for (int i = t0; i < t1; ++i)
-      for (const Arg& a : w[i].args) {
-        if (a.imm || spec.root_index.count(a.root)) continue;
-        const StoreRec& s = c->stores.at(a.root);
-        LaunchRoot lr{};
-        lr.root = a.root;
-        lr.dtype = s.dtype;
-        lr.ndim = s.ndim;
-        for (int d = 0; d < MAXD; ++d) {
-          lr.shape[d] = d < s.ndim ? s.shape[d] : 1;
-          lr.stride[d] = d < s.ndim ? s.stride[d] : 1;
-        }
-        lr.zero_d = s.ndim == 0;
-        lr.valid_before = valid[a.root];
-        lr.aligned16 = s.ptr ? ((uintptr_t)s.ptr % 16 == 0) : true;
-        lr.param = -1;
-        spec.root_index[a.root] = (int)spec.roots.size();
-        spec.roots.push_back(lr);
-      }
-    for (LaunchRoot& lr : spec.roots) {
-      for (int i = t0; i < t1; ++i)
-        for (const Arg& a : w[i].args) {
-          if (a.imm || a.root != lr.root) continue;
-          lr.written |= a.is_w() || a.is_rd();
-          lr.read |= a.is_r();
-        }
-      const auto& tc = tcount[lr.root];
-      const RootInfo& ri = wi.roots.at(lr.root);
-      if (lr.zero_d) {
-        // 0-d values live in registers; memory is needed to load a prior value
-        // or to publish the result beyond this launch
-        bool used_later = false;
-        for (int i = t1; i < (int)w.size(); ++i)
-          for (const Arg& a : w[i].args)
-            if (!a.imm && a.root == lr.root && (a.is_r() || a.is_rd())) used_later = true;
-        lr.live_out = lr.written && (ri.app_live || ri.wrapped || used_later);
-        lr.temp = !lr.live_out;
-        bool load = false;
-        if (lr.valid_before) {
-          // first access in program order decides whether the old value is used
-          for (int i = t0; i < t1 && !load; ++i) {
-            bool touched = false;
-            for (const Arg& a : w[i].args) {
-              if (a.imm || a.root != lr.root) continue;
-              touched = true;
-              if (a.is_r() || a.is_rd()) load = true;
-            }
-            if (touched) break;
-          }
-        }
-        lr.valid_before = lr.valid_before && load;
-        if (load || lr.live_out) lr.param = nparam++;
-      } else {
-        lr.temp = c->cfg.fusion && tc.first > 0 && tc.first == tc.second;
-        if (!lr.temp) lr.param = nparam++;
-      }
+    LaunchSpec spec = make_spec(c, w, wi.roots, P, g0, g1, valid);
+    for (const LaunchRoot& lr : spec.roots)
       if (lr.param >= 0) need_mem.insert(lr.root);
-    }
     KernelCode kc;
     try {
       kc = generate(spec);
@@ -624,6 +652,347 @@ int flush(dfs_ctx* c) {
   return rc;
 }
 
+// ------------------------------------------------------------- batching
+// Root descriptions of one instance window, roots numbered by first use.
+std::map<int64_t, RootInfo> root_infos(dfs_ctx* c, const std::vector<Task>& w, std::vector<int64_t>& order) {
+  std::map<int64_t, RootInfo> m;
+  for (const Task& t : w)
+    for (const Arg& a : t.args) {
+      if (a.imm || m.count(a.root)) continue;
+      order.push_back(a.root);
+      const StoreRec& r = c->stores.at(a.root);
+      RootInfo ri;
+      ri.root = a.root;
+      ri.ndim = r.ndim;
+      for (int d = 0; d < MAXD; ++d) ri.shape[d] = d < r.ndim ? r.shape[d] : 0;
+      ri.app_live = r.app_refs > 0;
+      ri.wrapped = r.wrapped;
+      ri.valid = r.valid;
+      m[a.root] = ri;
+    }
+  return m;
+}
+
+// Structure of one instance without its sizes: operations, privileges,
+// dtypes, ranks, store liveness and the patterns of root, partition and
+// launch-domain identity.  Equal keys mean the fusion pass treats the
+// instances alike.
+std::string batch_key(const std::vector<Task>& w, const std::map<int64_t, RootInfo>& roots) {
+  std::map<int64_t, int64_t> rid;
+  std::vector<NPart> parts;
+  std::vector<const Task*> doms;
+  std::string k;
+  auto put = [&k](int64_t v) { k.append(reinterpret_cast<const char*>(&v), sizeof v); };
+  for (const Task& t : w) {
+    put(-1 - t.op);
+    int64_t dc = -1;
+    for (size_t i = 0; i < doms.size() && dc < 0; ++i)
+      if (doms[i]->same_domain(t)) dc = (int64_t)i;
+    if (dc < 0) {
+      dc = (int64_t)doms.size();
+      doms.push_back(&t);
+    }
+    put(dc);
+    put(t.dnd);
+    for (const Arg& a : t.args) {
+      if (a.imm) {
+        put(-7);
+        continue;
+      }
+      auto it = rid.find(a.root);
+      if (it == rid.end()) {
+        const int64_t id = (int64_t)rid.size();
+        rid[a.root] = id;
+        const RootInfo& ri = roots.at(a.root);
+        put(-8);
+        put(a.dtype);
+        put(ri.ndim);
+        put((ri.app_live ? 1 : 0) | (ri.wrapped ? 2 : 0) | (ri.valid ? 4 : 0));
+        put(id);
+      } else {
+        put(it->second);
+      }
+      put(a.priv * 16 + a.redop);
+      int64_t pc = -1;
+      for (size_t i = 0; i < parts.size() && pc < 0; ++i)
+        if (parts[i] == a.part) pc = (int64_t)i;
+      if (pc < 0) {
+        pc = (int64_t)parts.size();
+        parts.push_back(a.part);
+      }
+      put(pc);
+      put(a.part.kind * 16 + a.part.nd);
+    }
+  }
+  return k;
+}
+
+int flush_batch(dfs_ctx* c) {
+  const std::vector<Task>& w = c->window;
+  std::vector<size_t> marks = c->batch_marks;
+  if (marks.empty() || marks.back() != w.size()) marks.push_back(w.size());
+  std::vector<std::pair<size_t, size_t>> inst;
+  size_t s0 = 0;
+  for (size_t m : marks) {
+    if (m > s0) inst.push_back({s0, m});
+    s0 = m;
+  }
+  auto fallback = [&](const std::string& why) {
+    c->batch_fallbacks += 1;
+    c->batch_fallback_reason = why;
+    return flush(c);
+  };
+  if (inst.size() < 2) return flush(c);
+  if (c->cfg.launch_mode != DFS_LAUNCH_PERSISTENT || !c->cfg.fusion) return fallback("batching runs fused, persistent launches");
+  const int K = (int)inst.size();
+  std::vector<std::vector<Task>> iw(K);
+  std::vector<std::map<int64_t, RootInfo>> iroots(K);
+  std::vector<std::vector<int64_t>> canon(K);
+  for (int i = 0; i < K; ++i) {
+    iw[i].assign(w.begin() + (long)inst[i].first, w.begin() + (long)inst[i].second);
+    iroots[i] = root_infos(c, iw[i], canon[i]);
+  }
+  const std::string key0 = batch_key(iw[0], iroots[0]);
+  for (int i = 1; i < K; ++i)
+    if (batch_key(iw[i], iroots[i]) != key0) return fallback("instances are not isomorphic");
+  // instances must be independent: a written root belongs to one instance
+  {
+    std::map<int64_t, int> writer, user;
+    for (int i = 0; i < K; ++i)
+      for (const Task& t : iw[i])
+        for (const Arg& a : t.args) {
+          if (a.imm) continue;
+          auto u = user.find(a.root);
+          if (u == user.end()) user[a.root] = i;
+          if (a.is_w() || a.is_rd()) {
+            auto wr = writer.find(a.root);
+            if (wr != writer.end() && wr->second != i) return fallback("instances write a shared store");
+            writer[a.root] = i;
+          }
+        }
+    for (const auto& kv : writer)
+      for (int i = 0; i < K; ++i)
+        if (i != kv.second)
+          for (const Task& t : iw[i])
+            for (const Arg& a : t.args)
+              if (!a.imm && a.root == kv.first) return fallback("an instance reads a store another writes");
+  }
+  // one plan for all: it must be the same for every instance
+  const Plan p0 = analyse(iw[0], iroots[0], true, DFS_LAUNCH_PERSISTENT);
+  if (p0.launches.size() != 1) return fallback("instance window longer than one launch");
+  auto temps_canon = [&](const Plan& p, int i) {
+    std::set<std::pair<int, int>> s;
+    std::map<int64_t, int> ci;
+    for (size_t k = 0; k < canon[i].size(); ++k) ci[canon[i][k]] = (int)k;
+    for (const auto& tr : p.temps) s.insert({tr.first, ci.at(tr.second)});
+    return s;
+  };
+  const auto t0c = temps_canon(p0, 0);
+  for (int i = 1; i < K; ++i) {
+    const Plan pi = analyse(iw[i], iroots[i], true, DFS_LAUNCH_PERSISTENT);
+    bool same = pi.groups.size() == p0.groups.size();
+    for (size_t g = 0; same && g < pi.groups.size(); ++g)
+      same = pi.groups[g].begin == p0.groups[g].begin && pi.groups[g].end == p0.groups[g].end &&
+             pi.groups[g].scalar == p0.groups[g].scalar;
+    if (!same || temps_canon(pi, i) != t0c) return fallback("instance plans differ");
+  }
+  std::map<int64_t, bool> valid;
+  for (const auto& kv : iroots[0]) valid[kv.first] = kv.second.valid;
+  const LaunchSpec spec = make_spec(c, iw[0], iroots[0], p0, 0, (int)p0.groups.size(), valid);
+  // vector width: every instance's streamed arrays must be 16-byte aligned
+  size_t esz = 0;
+  bool mixed = false;
+  for (const Task& t : iw[0])
+    for (size_t ai = 0; ai < t.args.size(); ++ai) {
+      const Arg& a = t.args[ai];
+      if (a.imm || a.nd == 0 || (t.op == DFS_OP_SPMV && ai != 4)) continue;
+      if (esz && esz != dtype_size(a.dtype)) mixed = true;
+      esz = dtype_size(a.dtype);
+    }
+  int vec = (esz && !mixed) ? (int)(16 / esz) : 1;
+  for (int i = 0; i < K && vec > 1; ++i)
+    for (const Task& t : iw[i])
+      for (size_t ai = 0; ai < t.args.size(); ++ai) {
+        const Arg& a = t.args[ai];
+        if (a.imm || a.nd == 0 || (t.op == DFS_OP_SPMV && ai != 4)) continue;
+        const StoreRec& r = c->stores.at(a.root);
+        if ((r.ptr && (uintptr_t)r.ptr % 16) || a.part.tile[0] % vec || a.part.off[0] % vec || a.part.vlo[0] % vec)
+          vec = 1;
+      }
+  // memoised kernel of this structure
+  std::string ckey = key0;
+  const int64_t cfgk[] = {vec, c->cfg.block_threads, c->cfg.unroll, c->cfg.debug_skip_arrival};
+  ckey.append(reinterpret_cast<const char*>(cfgk), sizeof cfgk);
+  auto bit = c->bcache.find(ckey);
+  dfs_ctx::BatchEntry* be = nullptr;
+  if (bit != c->bcache.end()) {
+    be = bit->second.get();
+    c->st.plan_hits += 1;
+  } else {
+    c->st.plan_misses += 1;
+    auto ne = std::make_unique<dfs_ctx::BatchEntry>();
+    std::string why;
+    if (!generate_batch(spec, vec, ne->code, why)) return fallback(why);
+    std::string err;
+    c->last_source = ne->code.source;
+    if (!c->device) {
+      // analysis-only: check that the batched kernel compiles, launch nothing
+      const size_t ok = c->jit->compile_only(ne->code.source, ne->code.name, err);
+      release_window(c);
+      if (!ok) return fail(c, DFS_ERR_COMPILE, err);
+      return fail(c, DFS_ERR_NO_DEVICE, "analysis-only context: batched kernel compiled, not launched");
+    }
+    ne->k = c->jit->get(ne->code.source, ne->code.name, spec.block, err);
+    if (!ne->k) {
+      release_window(c);
+      return fail(c, DFS_ERR_COMPILE, err);
+    }
+    ne->plan = p0;
+    be = ne.get();
+    c->bcache[ckey] = std::move(ne);
+  }
+  const BatchCode& bc = be->code;
+  std::map<int64_t, int> ci0;
+  for (size_t k = 0; k < canon[0].size(); ++k) ci0[canon[0][k]] = (int)k;
+  std::vector<int> ptr_canon;
+  for (int64_t r : bc.ptr_roots) ptr_canon.push_back(ci0.at(r));
+  // descriptors and work lists
+  const size_t NP = (size_t)std::max(1, bc.nptr), NIm = (size_t)std::max(1, bc.nimm), NV = (size_t)std::max(1, bc.nv);
+  const size_t per = NP + NIm + NV;
+  std::vector<int64_t> host((size_t)K * per + (size_t)bc.nprefix * (K + 1), 0);
+  for (int i = 0; i < K; ++i) {
+    int64_t* d = &host[(size_t)i * per];
+    for (int k = 0; k < bc.nptr; ++k) {
+      StoreRec& r = c->stores.at(canon[i][ptr_canon[k]]);
+      const int rc = materialise(c, r);
+      if (rc) {
+        release_window(c);
+        return rc;
+      }
+      std::memcpy(&d[k], &r.ptr, sizeof r.ptr);
+    }
+    for (int k = 0; k < bc.nimm; ++k) {
+      const double v = iw[i][bc.imm_src[k].first].args[bc.imm_src[k].second].immv;
+      std::memcpy(&d[NP + k], &v, sizeof v);
+    }
+    for (int k = 0; k < bc.nv; ++k) {
+      const auto& src = bc.v_src[k];
+      const NPart& p = iw[i][src.task].args[src.arg].part;
+      const int64_t vals[] = {p.tile[0], p.off[0], p.vlo[0], p.vhi[0]};
+      d[NP + NIm + k] = vals[src.field];
+    }
+  }
+  int64_t red_stride = 1;
+  for (int s = 0; s < bc.nprefix; ++s) {
+    int64_t* pf = &host[(size_t)K * per + (size_t)s * (K + 1)];
+    pf[0] = 0;
+    for (int i = 0; i < K; ++i) pf[i + 1] = pf[i] + iw[i][bc.prefix_task[s]].npoints();
+    red_stride = std::max(red_stride, pf[K]);
+  }
+  const std::string hkey(reinterpret_cast<const char*>(host.data()), host.size() * sizeof(int64_t));
+  auto tit = c->tables.find(hkey);
+  if (tit == c->tables.end()) {
+    if (c->capturing) {
+      release_window(c);
+      return fail(c, DFS_ERR_STATE, "batch descriptors first seen inside a capture: run the batch once before");
+    }
+    if (c->tables.size() >= 256 && c->graphs.empty()) {
+      for (auto& kv : c->tables) cudaFreeAsync(kv.second.dev, c->stream);
+      c->tables.clear();
+    }
+    dfs_ctx::Table tb;
+    tb.bytes = hkey.size();
+    CUDA_OK(cudaMallocAsync(&tb.dev, tb.bytes, c->stream));
+    CUDA_OK(cudaMemcpyAsync(tb.dev, host.data(), tb.bytes, cudaMemcpyHostToDevice, c->stream));
+    tit = c->tables.emplace(hkey, tb).first;
+  }
+  const size_t sval_need = (size_t)K * (size_t)std::max(1, bc.nsval) * sizeof(double);
+  const size_t part_need = (size_t)std::max(1, bc.nred) * (size_t)red_stride * 8;
+  if (sval_need > c->sval_cap || part_need > c->partials_cap) {
+    if (c->capturing) {
+      release_window(c);
+      return fail(c, DFS_ERR_STATE, "batch scratch would grow inside a capture: run the batch once before");
+    }
+    if (sval_need > c->sval_cap) {
+      if (c->sval) cudaFreeAsync(c->sval, c->stream);
+      CUDA_OK(cudaMallocAsync((void**)&c->sval, sval_need, c->stream));
+      c->sval_cap = sval_need;
+    }
+    if (part_need > c->partials_cap) {
+      if (c->partials) cudaFreeAsync(c->partials, c->stream);
+      CUDA_OK(cudaMallocAsync(&c->partials, part_need, c->stream));
+      c->partials_cap = part_need;
+    }
+  }
+  // launch: struct BP { insts, prefix, sval, partials, ctl, timeout_ns, ninst, red_stride }
+  uint64_t blob[8];
+  void* insts = tit->second.dev;
+  void* prefix = (char*)tit->second.dev + (size_t)K * per * 8;
+  std::memcpy(&blob[0], &insts, 8);
+  std::memcpy(&blob[1], &prefix, 8);
+  std::memcpy(&blob[2], &c->sval, 8);
+  std::memcpy(&blob[3], &c->partials, 8);
+  std::memcpy(&blob[4], &c->ctl, 8);
+  blob[5] = (uint64_t)(c->cfg.barrier_timeout_s * 1e9);
+  const int64_t kk = K;
+  std::memcpy(&blob[6], &kk, 8);
+  std::memcpy(&blob[7], &red_stride, 8);
+  void* params[] = {blob};
+  int per_sm = be->k->occupancy > 0 ? be->k->occupancy : 1;
+  if (c->cfg.ctas_per_sm > 0) per_sm = std::min(per_sm, c->cfg.ctas_per_sm);
+  const int grid = std::max(1, per_sm * c->sms);
+  const bool coop = bc.nbarriers > 0;
+  if (coop && be->k->occupancy <= 0) {
+    release_window(c);
+    return fail(c, DFS_ERR_CUDA, "batched kernel cannot be resident for a cooperative launch");
+  }
+  const bool timing = c->cfg.time_launches && !c->capturing;
+  dfs_ctx::Timed tm{nullptr, nullptr, bc.name};
+  if (timing) {
+    for (cudaEvent_t* e : {&tm.a, &tm.b}) {
+      if (!c->event_pool.empty()) {
+        *e = c->event_pool.back();
+        c->event_pool.pop_back();
+      } else {
+        CUDA_OK(cudaEventCreate(e));
+      }
+    }
+    CUDA_OK(cudaEventRecord(tm.a, c->stream));
+  }
+  CUresult cr = coop ? c->drv.LaunchCooperativeKernel(be->k->fn, grid, 1, 1, spec.block, 1, 1, 0, (CUstream)c->stream, params)
+                     : c->drv.LaunchKernel(be->k->fn, grid, 1, 1, spec.block, 1, 1, 0, (CUstream)c->stream, params, nullptr);
+  if (cr != CUDA_SUCCESS) {
+    const char* es = nullptr;
+    c->drv.GetErrorString(cr, &es);
+    release_window(c);
+    return fail(c, DFS_ERR_CUDA, std::string("batched launch: ") + (es ? es : "?"));
+  }
+  if (timing) {
+    CUDA_OK(cudaEventRecord(tm.b, c->stream));
+    c->timed.push_back(tm);
+  }
+  if (c->capturing)
+    c->capture_launches += 1;
+  else
+    c->st.launches += 1;
+  c->st.barriers += bc.nbarriers;
+  c->st.groups += (int64_t)p0.groups.size() * K;
+  c->st.last_regs = be->k->regs;
+  c->st.last_occupancy = be->k->occupancy;
+  c->st.last_grid = grid;
+  c->st.last_block = spec.block;
+  // every written root that has memory now holds a value
+  for (const LaunchRoot& lr : spec.roots) {
+    if (lr.param < 0 || !lr.written) continue;
+    const int k = ci0.at(lr.root);
+    for (int i = 0; i < K; ++i) c->stores.at(canon[i][k]).valid = true;
+  }
+  c->batches += 1;
+  c->batched_instances += K;
+  release_window(c);
+  return DFS_OK;
+}
+
 int write_json(const std::string& s, char* buf, size_t len, size_t* needed) {
   if (needed) *needed = s.size() + 1;
   if (!buf || len < s.size() + 1) {
@@ -732,6 +1101,9 @@ int dfs_shutdown(dfs_ctx* c) {
     for (auto& kv : c->stores)
       if (kv.second.owned && kv.second.ptr) cudaFreeAsync(kv.second.ptr, c->stream);
     if (c->partials) cudaFreeAsync(c->partials, c->stream);
+    if (c->sval) cudaFreeAsync(c->sval, c->stream);
+    for (auto& kv : c->tables) cudaFreeAsync(kv.second.dev, c->stream);
+    c->tables.clear();
     cudaStreamSynchronize(c->stream);
     for (auto& t : c->timed) {
       cudaEventDestroy(t.a);
@@ -987,7 +1359,7 @@ int dfs_submit(dfs_ctx* c, int32_t op, int32_t ndim, const int64_t* dom, int32_t
   c->window.push_back(std::move(t));
   c->seq += 1;
   c->st.tasks += 1;
-  if ((int)c->window.size() >= c->cfg.window_size) return flush(c);
+  if ((int)c->window.size() >= c->cfg.window_size && !c->batching) return flush(c);
   return DFS_OK;
 }
 
@@ -1114,6 +1486,32 @@ int dfs_graph_destroy(dfs_ctx* c, dfs_graph h) {
   return DFS_OK;
 }
 
+int dfs_batch_begin(dfs_ctx* c) {
+  if (!c) return DFS_ERR_INVALID;
+  if (c->batching) return fail(c, DFS_ERR_STATE, "already batching");
+  const int rc = flush(c);
+  if (rc) return rc;
+  c->batching = true;
+  c->batch_marks.clear();
+  return DFS_OK;
+}
+
+int dfs_batch_next(dfs_ctx* c) {
+  if (!c) return DFS_ERR_INVALID;
+  if (!c->batching) return fail(c, DFS_ERR_STATE, "dfs_batch_next outside a batch");
+  c->batch_marks.push_back(c->window.size());
+  return DFS_OK;
+}
+
+int dfs_batch_end(dfs_ctx* c) {
+  if (!c) return DFS_ERR_INVALID;
+  if (!c->batching) return fail(c, DFS_ERR_STATE, "dfs_batch_end outside a batch");
+  c->batching = false;
+  const int rc = flush_batch(c);
+  c->batch_marks.clear();
+  return rc;
+}
+
 const char* dfs_last_error(dfs_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
 int dfs_plan_json(dfs_ctx* c, char* buf, size_t len, size_t* needed) {
@@ -1147,6 +1545,9 @@ int dfs_stats_json(dfs_ctx* c, char* buf, size_t len, size_t* needed) {
     first = false;
   }
   o << "}";
+  o << ", \"batches\": " << c->batches << ", \"batched_instances\": " << c->batched_instances
+    << ", \"batch_fallbacks\": " << c->batch_fallbacks << ", \"batch_fallback_reason\": \"" << c->batch_fallback_reason
+    << "\"";
   o << ", \"sms\": " << c->sms << "}";
   return write_json(o.str(), buf, len, needed);
 }

@@ -191,4 +191,29 @@ struct KernelCode {
 
 KernelCode generate(const LaunchSpec& spec);
 
+// Device template of an element-wise op ("op_add", ...), nullptr otherwise.
+const char* op_device_fn(int op);
+
+// ------------------------------------------------------ batched execution
+// One size-generic kernel for K isomorphic instances of a window.  Sizes,
+// pointers and immediates come from per-instance descriptors:
+//   struct Inst { void* p[nptr]; double imm[nimm]; i64 v[nv]; }
+// and every vector group walks a work list (prefix offsets of the instances'
+// point counts).  Stores are 0-d or 1-D.
+struct BatchCode {
+  std::string name, source;
+  int nptr = 0, nimm = 0, nv = 0, nsval = 0, nprefix = 0, nred = 0, nbarriers = 0;
+  int vec = 1;
+  std::vector<int64_t> ptr_roots;              // instance-0 root of each pointer slot
+  std::vector<std::pair<int, int>> imm_src;    // (task, arg) of each immediate slot
+  struct VSrc {
+    int task, arg, field;                      // field: 0 tile, 1 off, 2 vlo, 3 vhi
+  };
+  std::vector<VSrc> v_src;
+  std::vector<int> prefix_task;                // first task of the group each prefix array serves
+};
+
+// Returns false (with a reason) when the launch cannot be batched.
+bool generate_batch(const LaunchSpec& spec, int vec, BatchCode& out, std::string& why);
+
 }  // namespace dfs

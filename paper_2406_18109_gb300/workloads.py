@@ -121,6 +121,16 @@ def cg_iteration_inplace(Amat: CSR, s: CGInPlace) -> None:
     s.p += s.r
 
 
+def batched_cg_iteration(rt: Runtime, problems) -> None:
+    """One CG iteration of every (matrix, in-place state) pair in one batched
+    launch: each solve's 12 tasks form one instance of the batch."""
+    rt.batch_begin()
+    for Amat, s in problems:
+        cg_iteration_inplace(Amat, s)
+        rt.batch_next()
+    rt.batch_end()
+
+
 def jacobi_views(grid: Array):
     """center, north, east, west, south views of an (N+2)x(N+2) grid (Fig. 1a)."""
     return (grid[1:-1, 1:-1], grid[0:-2, 1:-1], grid[1:-1, 2:], grid[1:-1, 0:-2], grid[2:, 1:-1])

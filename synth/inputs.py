@@ -91,6 +91,38 @@ def poisson3d_csr(m: int):
     return rowptr.astype(np.int32), C[mask].astype(np.int32), V[mask].astype(np.float64)
 
 
+def batched_cg_problems(count: int = 256, seed: int = 4, mmin: int = 32, mmax: int = 1024,
+                        spd_min: int = 1024, spd_max: int = 65536):
+    """Specifications of a batch of uneven CG problems.
+
+    Each problem is, with probability 1/2, the 2-D 5-point Poisson matrix of an
+    m x m grid with m log-uniform in [mmin, mmax], else a random diagonally
+    dominant SPD matrix of n rows, n log-uniform in [spd_min, spd_max].
+    Returns (kind, size, matrix seed, solution seed) tuples; the matrices are
+    built by batched_cg_matrix.
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        if rng.random() < 0.5:
+            m = int(round(np.exp(rng.uniform(np.log(mmin), np.log(mmax)))))
+            out.append(("poisson", m, 0, 1000 + i))
+        else:
+            nn = int(round(np.exp(rng.uniform(np.log(spd_min), np.log(spd_max)))))
+            out.append(("spd", nn, 10_000 + i, 1000 + i))
+    return out
+
+
+def batched_cg_matrix(spec):
+    """(rowptr, col, val, x*) of one problem of batched_cg_problems."""
+    kind, size, mseed, xseed = spec
+    if kind == "poisson":
+        rp, col, val = poisson2d_csr(size)
+    else:
+        rp, col, val = random_spd_csr(size, mseed)
+    return rp, col, val, uniform(xseed, -1.0, 1.0, len(rp) - 1)
+
+
 def cg_inputs(m: int = 256, seed: int = 0):
     """Poisson matrix of an m x m grid and the manufactured solution x* ~ U[-1,1]."""
     rowptr, col, val = poisson2d_csr(m)
@@ -109,23 +141,18 @@ def jacobi_grid(N: int, seed: int = 2, dtype=np.float32) -> np.ndarray:
 def random_spd_csr(n: int, seed: int, kmin: int = 2, kmax: int = 13):
     """Random symmetric, strictly diagonally dominant CSR matrix (hence SPD).
 
-    Each row draws k in [kmin, kmax] off-diagonal columns with values U[-1, 0);
-    the pattern is symmetrised as B + B^T and the diagonal set to the row's
-    absolute off-diagonal sum plus one.  Returned with ascending columns.
+    Each row draws k in [kmin, kmax] off-diagonal column positions (uniform
+    over the other n-1 columns, repeats merged) with values U[-1, 0); the
+    pattern is symmetrised as B + B^T and the diagonal set to the row's
+    absolute off-diagonal sum plus one.  Rows hold about 5-27 entries.
+    Returned with ascending columns.
     """
     rng = np.random.default_rng(seed)
-    rows, cols, vals = [], [], []
-    for i in range(n):
-        k = int(rng.integers(kmin, kmax + 1))
-        k = min(k, n - 1)
-        c = rng.choice(n - 1, size=k, replace=False)
-        c = np.where(c >= i, c + 1, c)
-        rows.append(np.full(k, i))
-        cols.append(c)
-        vals.append(rng.uniform(-1.0, 0.0, k))
-    R = np.concatenate(rows) if rows else np.zeros(0, np.int64)
-    Cc = np.concatenate(cols) if cols else np.zeros(0, np.int64)
-    Vv = np.concatenate(vals) if vals else np.zeros(0)
+    k = np.minimum(rng.integers(kmin, kmax + 1, n), max(0, n - 1))
+    R = np.repeat(np.arange(n, dtype=np.int64), k)
+    off = rng.integers(0, max(1, n - 1), R.size)
+    Cc = (R + 1 + off) % n
+    Vv = rng.uniform(-1.0, 0.0, R.size)
     # symmetrise: entries (i,j) and (j,i) summed
     R2 = np.concatenate([R, Cc])
     C2 = np.concatenate([Cc, R])

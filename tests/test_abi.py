@@ -167,6 +167,38 @@ def test_cg_plan_two_iterations_memo_key():
     assert k1 == k2
 
 
+def test_batched_kernel_compiles_and_checks_isomorphism():
+    rt = rt0(tile=512)
+    probs = []
+    for m in (40, 33, 47):
+        Am = A.CSR.__new__(A.CSR)
+        Am.rt, Am.nrows, Am.ncols, Am.nnz = rt, m * m, m * m, 5 * m * m - 4 * m
+        Am.rowptr = rt.empty((m * m + 1,), np.int32)
+        Am.col = rt.empty((Am.nnz,), np.int32)
+        Am.val = rt.empty((Am.nnz,), np.float64)
+        Am.dtype = np.dtype(np.float64)
+        probs.append((Am, W.CGInPlace(*(rt.empty((m * m,)) for _ in range(4)), rt.empty(()))))
+    with pytest.raises(B.DfsError) as e:
+        W.batched_cg_iteration(rt, probs)
+    assert e.value.code == -2 and "batched kernel compiled" in str(e.value)
+    src = rt.kernel_source()
+    assert "find_inst" in src and src.count("grid_barrier") == 4
+    assert rt.stats()["batch_fallbacks"] == 0
+    # instances that are not isomorphic are flushed as an ordinary window
+    rt.batch_begin()
+    a = rt.empty((1000,))
+    b = a * 2.0
+    rt.batch_next()
+    c = A.sqrt(a)
+    rt.batch_next()
+    with pytest.raises(B.DfsError):
+        rt.batch_end()
+    assert rt.stats()["batch_fallbacks"] == 1
+    with pytest.raises(B.DfsError) as e:
+        rt.batch_next()
+    assert e.value.code == -7
+
+
 def test_capture_api_needs_a_device_and_checks_state():
     rt = rt0()
     with pytest.raises(B.DfsError) as e:

@@ -1,0 +1,126 @@
+"""Batched execution of isomorphic windows (many uneven problems, one launch).
+
+Every instance of a batch must give exactly what it gives when run alone
+with the same tiles (bit for bit: reductions keep per-point partials summed
+in point order), and agree with the oracle."""
+import numpy as np
+import pytest
+
+from oracle import programs
+from paper_2406_18109_gb300 import arrays as A
+from paper_2406_18109_gb300 import workloads as W
+from synth import inputs
+from tests.helpers import gpu_runtime
+
+pytestmark = pytest.mark.gpu
+
+SPECS = [("poisson", 33, 0, 1), ("spd", 5000, 7, 2), ("poisson", 71, 0, 3), ("spd", 1500, 8, 4),
+         ("poisson", 45, 0, 5), ("poisson", 90, 0, 6), ("spd", 12000, 9, 7)]
+
+
+def _problems(rt, specs, dtype=np.float64):
+    out = []
+    for spec in specs:
+        rp, col, val, xs = inputs.batched_cg_matrix(spec)
+        Am = A.CSR(rt, rp, col, val.astype(dtype))
+        b = Am @ rt.array(xs.astype(dtype))
+        out.append((Am, W.cg_start_inplace(b)))
+    rt.flush()
+    return out
+
+
+def _run(specs, iters, batched, dtype=np.float64, graph=False):
+    with gpu_runtime("persistent", tile=512) as rt:
+        probs = _problems(rt, specs, dtype)
+        if batched:
+            W.batched_cg_iteration(rt, probs)
+            if graph:
+                rt.capture_begin()
+                W.batched_cg_iteration(rt, probs)
+                g = rt.capture_end()
+                for _ in range(iters - 1):
+                    rt.graph_launch(g)
+            else:
+                for _ in range(iters - 1):
+                    W.batched_cg_iteration(rt, probs)
+        else:
+            for Am, s in probs:
+                for _ in range(iters):
+                    W.cg_iteration_inplace(Am, s)
+                    rt.flush()
+        xs = [s.x.numpy() for _, s in probs]
+        st = rt.stats()
+        if batched and graph:
+            rt.graph_destroy(g)
+        return xs, st
+
+
+def test_batched_equals_alone_and_oracle():
+    iters = 20
+    xb, st = _run(SPECS, iters, batched=True)
+    assert st["batches"] == iters and st["batched_instances"] == iters * len(SPECS)
+    assert st["batch_fallbacks"] == 0
+    xa, _ = _run(SPECS, iters, batched=False)
+    for i, spec in enumerate(SPECS):
+        assert np.array_equal(xb[i].view(np.uint64), xa[i].view(np.uint64)), spec
+        rp, col, val, xs = inputs.batched_cg_matrix(spec)
+        b = programs.spmv(rp, col, val, xs)
+        xo, _, _ = programs.cg(rp, col, val, b, iters)
+        assert np.linalg.norm(xb[i] - xo) / np.linalg.norm(xo) < 1e-12, spec
+
+
+def test_batched_fp32():
+    iters = 15
+    xb, st = _run(SPECS[:4], iters, batched=True, dtype=np.float32)
+    xa, _ = _run(SPECS[:4], iters, batched=False, dtype=np.float32)
+    for i in range(4):
+        assert xb[i].dtype == np.float32
+        assert np.array_equal(xb[i].view(np.uint32), xa[i].view(np.uint32))
+        rp, col, val, xs = inputs.batched_cg_matrix(SPECS[i])
+        b = programs.spmv(rp, col, val.astype(np.float32), xs.astype(np.float32), np.float32)
+        xo, _, _ = programs.cg(rp, col, val, b, iters, dt=np.float32)
+        assert np.linalg.norm(xb[i] - xo) / np.linalg.norm(xo) < 1e-4
+
+
+def test_batched_graph_replay():
+    iters = 12
+    xg, _ = _run(SPECS, iters, batched=True, graph=True)
+    xb, _ = _run(SPECS, iters, batched=True)
+    for i in range(len(SPECS)):
+        assert np.array_equal(xg[i].view(np.uint64), xb[i].view(np.uint64))
+
+
+def test_non_isomorphic_batch_falls_back_correctly():
+    with gpu_runtime("persistent", tile=512) as rt:
+        x = rt.array(inputs.uniform(1, 0.5, 2.0, 3000))
+        y = rt.array(inputs.uniform(2, 0.5, 2.0, 5000))
+        rt.batch_begin()
+        a = x * 2.0 + 1.0
+        rt.batch_next()
+        b = A.sqrt(y)
+        rt.batch_next()
+        rt.batch_end()
+        st = rt.stats()
+        assert st["batch_fallbacks"] == 1 and st["batches"] == 0
+        assert np.allclose(a.numpy(), x.numpy() * 2 + 1) and np.allclose(b.numpy(), np.sqrt(y.numpy()))
+
+
+def test_batched_black_scholes_instances_equal_alone():
+    sizes = [10_000, 70_001, 33_333]
+    prm = inputs.bs_params()
+    data = [inputs.bs_inputs(n, seed=20 + i) for i, n in enumerate(sizes)]
+    with gpu_runtime("persistent", tile=4096) as rt:
+        arrs = [[rt.array(v) for v in d] for d in data]
+        outs = []
+        rt.batch_begin()
+        for S, K, T in arrs:
+            outs.append(W.black_scholes(S, K, T, prm["r"], prm["sigma"]))
+            rt.batch_next()
+        rt.batch_end()
+        assert rt.stats()["batches"] == 1
+        got = [(c.numpy(), p.numpy()) for c, p in outs]
+    for (S, K, T), (c, p) in zip(data, got):
+        with gpu_runtime("persistent", tile=4096) as rt:
+            c1, p1 = W.black_scholes(rt.array(S), rt.array(K), rt.array(T), prm["r"], prm["sigma"])
+            assert np.array_equal(c.view(np.uint32), c1.numpy().view(np.uint32))
+            assert np.array_equal(p.view(np.uint32), p1.numpy().view(np.uint32))

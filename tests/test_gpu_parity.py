@@ -118,6 +118,16 @@ def test_cg_matches_oracle(mode):
         assert st["launches"] == iters + 1 and st["barriers"] == 2 * iters
 
 
+def test_cg_single_point_domain():
+    # n = 400 < one 512-row tile: the launch domain has one point, so the
+    # scalar divides share it and the paper's pass fuses them with vector tasks
+    x, r, rho, b, st = _cg_gpu("persistent", 20, 25, tile=512)
+    xo, ro, rhoo, bo = _cg_oracle(20, 25)
+    assert _rel(x, xo) < 1e-12 and abs(rho - rhoo) <= 1e-10 * abs(rhoo)
+    xu, *_ = _cg_gpu("unfused", 20, 25, tile=512)
+    assert np.array_equal(_bits(x), _bits(xu))
+
+
 def test_cg_fused_equals_unfused_bitwise():
     res = {m: _cg_gpu(m, 40, 20, tile=256) for m in MODES}
     for m in MODES[1:]:
