@@ -12,7 +12,7 @@ S, K, T and D2H of call, put every step), and the CPU oracle on a bounded
 sample.  Kernel durations come from CUDA events the runtime records
 immediately around each launch on the launching stream.
 
-  python bench.py [--steps K] [--warmup W] [--workload bs|cg|jacobi]
+  python bench.py [--steps K] [--warmup W] [--workload bs|cg|jacobi|batched] [--fp32]
   python bench.py --impl reference     # the CPU oracle as the reference arm
 Prints one JSON line.
 """
@@ -27,7 +27,11 @@ import sys
 import threading
 import time
 
-import numpy as np
+# the CPU oracle is timed on one core: keep BLAS single-threaded
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -37,9 +41,12 @@ from synth import inputs  # noqa: E402
 
 METRIC = {"bs": ("Black-Scholes options/s (fused window, 2^26 FP32)", "options/s", "f32"),
           "cg": ("CG iterations/s (fused windows, 256^2 Poisson FP64)", "iterations/s", "f64"),
-          "jacobi": ("Jacobi sweeps/s (fused windows, 8192^2 FP32)", "sweeps/s", "f32")}
+          "jacobi": ("Jacobi sweeps/s (fused windows, 8192^2 FP32)", "sweeps/s", "f32"),
+          "batched": ("Batched CG aggregate iterations/s (256 uneven solves, one launch per iteration)",
+                      "iterations/s", "f64")}
 WORKLOAD = {"bs": "black-scholes-2^26-fp32", "cg": "cg-poisson2d-256x256-fp64-50it",
-            "jacobi": "jacobi-fig1-stencil-8192x8192-fp32-200sweeps"}
+            "jacobi": "jacobi-fig1-stencil-8192x8192-fp32-200sweeps",
+            "batched": "batched-cg-256-uneven-100it"}
 
 
 def load_peaks():
@@ -133,6 +140,25 @@ def oracle_rate(workload: str, budget_s: float = 10.0):
                 break
         dt = time.perf_counter() - t0
         return done / dt, "iterations/s", f"{done} CG iterations on the 256^2 Poisson system"
+    if workload == "batched":
+        cfg = configs.BATCHED_CG
+        dtp = np.float64 if cfg["dtype"] == "f64" else np.float32
+        specs = inputs.batched_cg_problems(cfg["count"], cfg["seed"])
+        rng = np.random.default_rng(0)
+        sample = sorted(rng.choice(len(specs), 12, replace=False).tolist())
+        t_sample, done = 0.0, 0
+        for i in sample:
+            rp, col, val, xs = inputs.batched_cg_matrix(specs[i])
+            b = programs.spmv(rp, col, val, xs, dtp)
+            t0 = time.perf_counter()
+            programs.cg(rp, col, val, b, 5, dt=dtp)
+            t_sample += (time.perf_counter() - t0) / 5
+            done += 5
+        # one iteration of every solve, estimated from the sampled solves
+        per_batch = t_sample / len(sample) * len(specs)
+        return len(specs) / per_batch, "iterations/s", (f"{done} CG iterations on 12 sampled problems of the "
+                                                        f"batch; one iteration of all {len(specs)} solves "
+                                                        f"estimated from their mean")
     cfg = configs.JACOBI
     g = inputs.jacobi_grid(2046, seed=cfg["seed"])
     done, t0 = 0, time.perf_counter()
@@ -160,7 +186,8 @@ def kernel_delta(before: dict, after: dict) -> dict:
 class Arm:
     """One timed configuration of a workload: build state, warm up, time K steps."""
 
-    def __init__(self, workload, rt_kwargs, torch, stream, e2e=False, graph=False):
+    def __init__(self, workload, rt_kwargs, torch, stream, e2e=False, graph=False, per_solve=False):
+        self.per_solve = per_solve
         from paper_2406_18109_gb300 import arrays as A
         from paper_2406_18109_gb300 import dist as D
         from paper_2406_18109_gb300 import workloads as W
@@ -204,6 +231,56 @@ class Arm:
                     self.rt.flush()
                 self.graph = self.rt.capture_end()
                 self.step = self._cg_graph
+        elif workload == "batched":
+            cfg = self.cfg = configs.BATCHED_CG
+            dt = np.float64 if cfg["dtype"] == "f64" else np.float32
+            self.probs, self.nnz, self.rows = [], 0, 0
+            mats = []
+            for spec in inputs.batched_cg_problems(cfg["count"], cfg["seed"]):
+                rp, col, val, xs = inputs.batched_cg_matrix(spec)
+                mats.append((A.CSR(self.rt, rp, col, val.astype(dt)), self.rt.array(xs.astype(dt))))
+                self.nnz += len(col)
+                self.rows += len(rp) - 1
+            # b = A x* and the CG start of every problem, as one batch
+            self.rt.batch_begin()
+            for Am, xs_d in mats:
+                b = Am @ xs_d
+                self.probs.append((Am, W.cg_start_inplace(b), b))
+                self.rt.batch_next()
+            self.rt.batch_end()
+            del mats
+            pairs = [(Am, s) for Am, s, _ in self.probs]
+            rt = self.rt
+
+            def one_iteration():
+                if self.per_solve:
+                    for Am, s in pairs:
+                        W.cg_iteration_inplace(Am, s)
+                        rt.flush()
+                else:
+                    W.batched_cg_iteration(rt, pairs)
+
+            def reset():
+                if self.per_solve:
+                    for _, s, b in self.probs:
+                        W.cg_reset_inplace(s, b)
+                        rt.flush()
+                else:
+                    rt.batch_begin()
+                    for _, s, b in self.probs:
+                        W.cg_reset_inplace(s, b)
+                        rt.batch_next()
+                    rt.batch_end()
+            # one normal pass of each window (compiles kernels, uploads descriptors), then capture
+            reset()
+            one_iteration()
+            rt.capture_begin()
+            reset()
+            for _ in range(cfg["iters"]):
+                one_iteration()
+            self.graph = rt.capture_end()
+            self.units = cfg["count"] * cfg["iters"]
+            self.step = self._cg_graph
         else:
             cfg = self.cfg = configs.JACOBI
             grid = inputs.jacobi_grid(cfg["N"], seed=cfg["seed"])
@@ -324,7 +401,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="bs", choices=["bs", "cg", "jacobi"])
+    ap.add_argument("--workload", default="bs", choices=["bs", "cg", "jacobi", "batched"])
+    ap.add_argument("--fp32", action="store_true", help="batched CG in FP32 instead of FP64")
     ap.add_argument("--quick", action="store_true", help="skip the comparison arms (for profiling)")
     ap.add_argument("--bs-n", type=int, default=0, help="Black-Scholes batch size (profiling a smaller case)")
     ap.add_argument("--jac-n", type=int, default=0, help="Jacobi interior size N (profiling a smaller case)")
@@ -340,6 +418,10 @@ def main():
         configs.JACOBI["N"] = args.jac_n
     if args.sweeps:
         configs.JACOBI["sweeps"] = args.sweeps
+    if args.fp32:
+        configs.BATCHED_CG["dtype"] = "f32"
+        METRIC["batched"] = (METRIC["batched"][0], "iterations/s", "f32")
+        WORKLOAD["batched"] = "batched-cg-256-uneven-100it-fp32"
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     metric, unit, dtype = METRIC[args.workload]
@@ -368,9 +450,10 @@ def main():
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    cache = os.path.join(ROOT, "gpurun_out", "cubins") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None
-    if cache:
-        os.makedirs(cache, exist_ok=True)
+    # compiled kernels are kept on disk between runs (Section 7.2's suggested follow-up)
+    import tempfile
+    cache = os.path.join(tempfile.gettempdir(), "dfs_cubins")
+    os.makedirs(cache, exist_ok=True)
 
     from paper_2406_18109_gb300 import _build
     from paper_2406_18109_gb300 import dist as D
@@ -379,7 +462,9 @@ def main():
         print(json.dumps({"compile_report": compile_report(torch, stream, sms)}))
         return
 
-    cfg = {"bs": configs.BLACK_SCHOLES, "cg": configs.CG, "jacobi": configs.JACOBI}[args.workload]
+    metric, unit, dtype = METRIC[args.workload]
+    cfg = {"bs": configs.BLACK_SCHOLES, "cg": configs.CG, "jacobi": configs.JACOBI,
+           "batched": configs.BATCHED_CG}[args.workload]
     base = dict(block=cfg["block"], unroll=cfg["unroll"], sms=sms, cache_dir=cache)
     if "tile" in cfg:
         base["tile"] = cfg["tile"]
@@ -391,16 +476,17 @@ def main():
 
     # CG: the iteration windows are captured once (memoised windows + a CUDA
     # graph) and replayed; the Python-issued runs are reported beside them
-    graph = args.workload == "cg"
+    graph = args.workload in ("cg", "batched")
 
-    def arm(kw, steps, warmup, e2e=False, graph=graph):
-        a = Arm(args.workload, kw, torch, stream, e2e=e2e, graph=graph)
+    def arm(kw, steps, warmup, e2e=False, graph=graph, per_solve=False):
+        a = Arm(args.workload, kw, torch, stream, e2e=e2e, graph=graph, per_solve=per_solve)
         try:
             return a.run(steps, warmup)
         finally:
             a.close()
 
     fused_arm = Arm(args.workload, dict(base, fusion=True, launch="persistent"), torch, stream, graph=graph)
+    batch_sizes = (fused_arm.nnz, fused_arm.rows) if args.workload == "batched" else None
     clocks = Clocks(dev)
     if world > 1:
         torch.distributed.barrier()
@@ -412,7 +498,14 @@ def main():
     ms_step = fused["ms"] / args.steps
 
     extra = {}
-    if not args.quick:
+    if not args.quick and args.workload == "batched":
+        k2 = max(2, args.steps // 2)
+        ps = arm(dict(base, fusion=True, launch="persistent"), k2, 1, per_solve=True)
+        extra["per_solve_launches"] = {"value": ps["units"] / (ps["ms"] / 1e3), "ms_per_step": ps["ms"] / k2,
+                                       "note": "same fused windows, one launch per solve per iteration, "
+                                               "replayed from a CUDA graph"}
+        extra["batched_vs_per_solve"] = value / world / extra["per_solve_launches"]["value"]
+    elif not args.quick:
         k2 = max(3, args.steps // 4)
         unf = arm(dict(base, fusion=False, launch="per_task"), k2, 2)
         pt = arm(dict(base, fusion=True, launch="per_task"), k2, 2)
@@ -443,6 +536,13 @@ def main():
         m = cfg["m"]
         nn, nnz = m * m, 5 * m * m - 4 * m
         alg_bytes = 12 * nnz + 4 * (nn + 1) + 96 * nn     # one CG iteration (one launch)
+    elif args.workload == "batched":
+        nnz, rows = batch_sizes
+        esz = 8 if cfg["dtype"] == "f64" else 4
+        # per batched iteration, summed over the solves: CSR (value + int32
+        # column per entry, int32 row pointers) and the vector passes of the
+        # iteration (12 for the FP64 count of the single-solve CG line)
+        alg_bytes = (esz + 4) * nnz + 4 * (rows + cfg["count"]) + 12 * esz * rows
     else:
         alg_bytes = 16 * cfg["N"] * cfg["N"]               # one sweep (one launch)
     kern_ms = fused["dominant_ms"]
@@ -450,7 +550,8 @@ def main():
         # launches replayed from a graph are not timed one by one: use the
         # replayed time per iteration (kernel plus the gap to the next node)
         kern_ms = fused["ms"] / (args.steps * cfg["iters"])
-        fused["dominant"] = "CG iteration kernel, graph replay (time per iteration incl. launch gap)"
+        fused["dominant"] = ("batched CG iteration kernel" if args.workload == "batched" else
+                             "CG iteration kernel") + ", graph replay (time per iteration incl. launch gap)"
         fused["dominant_launches"] = args.steps * cfg["iters"]
     achieved = alg_bytes / (kern_ms / 1e3) / 1e9 if kern_ms > 0 else 0.0
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",

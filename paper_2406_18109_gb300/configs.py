@@ -15,6 +15,13 @@ BLACK_SCHOLES = dict(n=1 << 26, seed=1, r=0.02, sigma=0.3, tile=16384, block=512
 # int32 indices, x* ~ U[-1,1] (seed 0), b = A x*, x0 = 0
 CG = dict(m=256, iters=50, seed=0, tile=512, block=256, unroll=2)
 
+# Batched CG: 256 independent solves of uneven size (half 2-D Poisson with m
+# log-uniform in [32, 1024], half random diagonally dominant SPD with n
+# log-uniform in [1024, 65536]), 100 iterations each, one batched launch per
+# iteration, the whole solve replayed from a CUDA graph; FP64 (dtype "f32"
+# for the FP32 variant)
+BATCHED_CG = dict(count=256, seed=4, iters=100, dtype="f64", tile=512, block=256, unroll=2)
+
 # Jacobi: Fig. 1 stencil on an 8192x8192 FP32 grid (8190^2 interior),
 # 200 sweeps, interior U[0,1] (seed 2), boundary 1.0
 JACOBI = dict(N=8190, sweeps=200, seed=2, rows=16, block=256, unroll=8, sweeps_per_flush=1)

@@ -248,7 +248,7 @@ void BatchGen::vector_group(int g) {
         }
         if (is_out) {
           written.insert(key);
-          if (!R(a.root).temp) need_base(t, ai);
+          if (!R(a.root).temp || t.op == DFS_OP_SPMV) need_base(t, ai);
         }
       }
       if (t.op == DFS_OP_SPMV)

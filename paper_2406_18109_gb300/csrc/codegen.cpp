@@ -424,7 +424,8 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
       const bool is_out = (is_elementwise(t.op) && ai + 1 == t.args.size()) || (t.op == DFS_OP_SPMV && ai == 4);
       if (is_out) {
         written_keys.insert(k);
-        if (!R(a.root).temp) need_base(a);
+        // an SpMV output's offset also gives its row index, temporary or not
+        if (!R(a.root).temp || t.op == DFS_OP_SPMV) need_base(a);
       }
     }
     if (is_reduction(t.op)) {

@@ -199,6 +199,36 @@ def test_batched_kernel_compiles_and_checks_isomorphism():
     assert e.value.code == -7
 
 
+def test_spmv_output_temporary_compiles():
+    """An SpMV whose output dies in the window is eliminated (Def. 4); its row
+    index still comes from the output's offset."""
+    for batched in (False, True):
+        rt = rt0(tile=512)
+        keep = []
+        if batched:
+            rt.batch_begin()
+        for n in (1433, 8587):
+            Am = A.CSR.__new__(A.CSR)
+            Am.rt, Am.nrows, Am.ncols, Am.nnz = rt, n, n, 16 * n
+            Am.rowptr = rt.empty((n + 1,), np.int32)
+            Am.col = rt.empty((16 * n,), np.int32)
+            Am.val = rt.empty((16 * n,), np.float64)
+            Am.dtype = np.dtype(np.float64)
+            y = Am @ rt.empty((n,))
+            keep.append((Am, y * 2.0, A.dot(y, y)))
+            del y
+            if batched:
+                rt.batch_next()
+        if not batched:
+            p = rt.plan()
+            assert len(p["temporaries"]) == 2
+        with pytest.raises(B.DfsError) as e:
+            rt.batch_end() if batched else rt.flush()
+        assert e.value.code == -2
+        assert rt.stats()["batch_fallbacks"] == 0
+        assert "spmv_row" in rt.kernel_source()
+
+
 def test_capture_api_needs_a_device_and_checks_state():
     rt = rt0()
     with pytest.raises(B.DfsError) as e:

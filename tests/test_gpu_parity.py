@@ -264,6 +264,24 @@ def test_spmv_random_spd(dtype):
     assert np.max(np.abs(y - want)) <= tol * np.max(np.abs(want))
 
 
+@pytest.mark.parametrize("mode", ["persistent", "unfused"])
+def test_spmv_output_as_temporary(mode):
+    """y = A x dies inside its window (Def. 4): read straight from registers
+    by the fused consumers, never stored."""
+    rp, col, val = inputs.random_spd_csr(3000, seed=5)
+    x = inputs.uniform(7, -1, 1, 3000)
+    with gpu_runtime(mode, tile=512) as rt:
+        Am = A.CSR(rt, rp, col, val)
+        y = Am @ rt.array(x)
+        z = y * 2.0 + 1.0
+        r = A.dot(y, y)
+        del y
+        zg, rg = z.numpy(), float(r.numpy())
+    y = programs.spmv(rp, col, val, x)
+    assert np.max(np.abs(zg - (y * 2.0 + 1.0))) <= 1e-13 * np.max(np.abs(y))
+    assert abs(rg - y @ y) <= 1e-13 * (y @ y)
+
+
 # ------------------------------------------------------- runtime behaviour
 def test_temporaries_are_never_allocated():
     n = 1 << 16
