@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -43,10 +44,13 @@ METRIC = {"bs": ("Black-Scholes options/s (fused window, 2^26 FP32)", "options/s
           "cg": ("CG iterations/s (fused windows, 256^2 Poisson FP64)", "iterations/s", "f64"),
           "jacobi": ("Jacobi sweeps/s (fused windows, 8192^2 FP32)", "sweeps/s", "f32"),
           "batched": ("Batched CG aggregate iterations/s (256 uneven solves, one launch per iteration)",
-                      "iterations/s", "f64")}
+                      "iterations/s", "f64"),
+          "serve": ("Serving sustained requests/s with p50/p99 latency (CG/BiCGSTAB on 3-D Poisson 64^3..256^3 "
+                    "tol 1e-8, Black-Scholes 2^16..2^24; Poisson arrivals, mean gap 2 ms)", "requests/s", "f64+f32")}
 WORKLOAD = {"bs": "black-scholes-2^26-fp32", "cg": "cg-poisson2d-256x256-fp64-50it",
             "jacobi": "jacobi-fig1-stencil-8192x8192-fp32-200sweeps",
-            "batched": "batched-cg-256-uneven-100it"}
+            "batched": "batched-cg-256-uneven-100it",
+            "serve": "serving-cg-bicgstab-bs-poisson-arrivals-2ms-120GB"}
 
 
 def load_peaks():
@@ -159,6 +163,40 @@ def oracle_rate(workload: str, budget_s: float = 10.0):
         return len(specs) / per_batch, "iterations/s", (f"{done} CG iterations on 12 sampled problems of the "
                                                         f"batch; one iteration of all {len(specs)} solves "
                                                         f"estimated from their mean")
+    if workload == "serve":
+        cfg = configs.SERVING
+        m0 = inputs.SERVE_LADDER[0]
+        rp, col, val = inputs.poisson3d_csr(m0)
+        b = programs.spmv(rp, col, val, inputs.uniform(1, -1.0, 1.0, m0 ** 3))
+        hist = []
+        n_run = 400
+        t0 = time.perf_counter()
+        programs.cg(rp, col, val, b, n_run, history=hist)
+        t_it = (time.perf_counter() - t0) / n_run
+        bn = np.linalg.norm(b)
+        n_cg = next((k + 1 for k, x in enumerate(hist)
+                     if np.linalg.norm(b - programs.spmv(rp, col, val, x)) <= cfg["tol"] * bn), n_run)
+        t_cg = t_it * n_cg
+        t0 = time.perf_counter()
+        _, n_bi, _ = programs.bicgstab(rp, col, val, b, cfg["tol"], 2000)
+        t_bi = time.perf_counter() - t0
+        nb = 1 << 18
+        S, K, T = inputs.bs_inputs(nb, seed=1)
+        t0 = time.perf_counter()
+        programs.black_scholes(S, K, T, 0.02, 0.3, np.float32)
+        t_opt = (time.perf_counter() - t0) / nb
+        reqs = inputs.serving_requests(cfg["count"], seed=cfg["seed"], mean_gap_s=cfg["mean_gap_ms"] * 1e-3)
+        tot = 0.0
+        for r in reqs:
+            if r["kind"] == "bs":
+                tot += t_opt * r["size"]
+            else:
+                # unknowns grow as m^3 and Krylov iterations on Poisson as m
+                tot += (t_cg if r["kind"] == "cg" else t_bi) * (r["size"] / m0) ** 4
+        return len(reqs) / tot, "requests/s", (
+            f"CG ({n_cg} iterations) and BiCGSTAB ({n_bi}) solved to tol on the {m0}^3 operator, 2^18 options; "
+            f"each of the {len(reqs)} requests of the stream costed from these (solves scaled by (m/{m0})^4: "
+            f"m^3 unknowns x iterations growing as m), run back to back on one core")
     cfg = configs.JACOBI
     g = inputs.jacobi_grid(2046, seed=cfg["seed"])
     done, t0 = 0, time.perf_counter()
@@ -395,13 +433,122 @@ def compile_report(torch, stream, sms) -> dict:
     return out
 
 
+def serving_alg_bytes(results) -> int:
+    """Algorithmic HBM bytes of the served work: per solver iteration the CSR
+    matrix once per SpMV (12 B per entry, 4 B per row pointer) plus the vector
+    passes the phases need (CG 88 B per row; BiCGSTAB 168 B per row, two SpMVs),
+    per option batch 20 B per option."""
+    from paper_2406_18109_gb300 import serve as SV
+    tot = 0
+    for r in results:
+        if r.kind == "bs":
+            tot += 20 * r.size
+            continue
+        n = r.size ** 3
+        mat = SV.operator_bytes(r.size)
+        per = mat + 88 * n if r.kind == "cg" else 2 * mat + 168 * n
+        tot += r.iterations * per
+    return tot
+
+
+def run_serving(args, torch, stream, sms, cache, dev):
+    """The serving loop under its Poisson arrival stream, then again at a
+    fraction of the throughput it sustained; one JSON line."""
+    from paper_2406_18109_gb300 import arrays as A
+    from paper_2406_18109_gb300 import serve as SV
+    cfg = configs.SERVING
+    count = args.requests or cfg["count"]
+    peaks = load_peaks()
+    rt = A.Runtime(device=dev, stream=stream.cuda_stream, time_launches=True, tile=cfg["tile"],
+                   block=cfg["block"], unroll=cfg["unroll"], sms=sms, cache_dir=cache)
+
+    def server():
+        return SV.Server(rt, inputs.poisson3d_csr, budget_bytes=int(cfg["budget_gb"] * 1e9), tol=cfg["tol"],
+                         iters_per_tick=cfg["iters_per_tick"], max_active=cfg["max_active"], keep_outputs=False)
+
+    # resident operators (every rung of the ladder), loaded before serving
+    t_load = time.perf_counter()
+    srv = server()
+    for m in inputs.SERVE_LADDER:
+        srv._operator(m)
+    rt.sync()
+    t_load = time.perf_counter() - t_load
+    # warm-up: compile the kernels of every window shape on a few requests
+    warm = inputs.serving_requests(12, seed=99, mean_gap_s=1e-4, ladder=inputs.SERVE_LADDER[:2], bs_log2=(16, 17))
+    srv.run(warm, inputs.serving_payload)
+
+    def one_run(mean_gap_s):
+        reqs = inputs.serving_requests(count, seed=cfg["seed"], mean_gap_s=mean_gap_s)
+        pf = SV.Prefetch(inputs.serving_payload, reqs, depth=6)
+        s0 = rt.stats()
+        clocks = Clocks(dev)
+        clocks.start()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = srv.run(reqs, pf)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        clk = clocks.stop()
+        s1 = rt.stats()
+        kd = kernel_delta(s0["kernel_times"], s1["kernel_times"])
+        kern_ms = sum(v["ms"] for v in kd.values())
+        summ = SV.summarize(res, wall)
+        alg = serving_alg_bytes(res)
+        summ.update({"offered_rps": 1.0 / mean_gap_s, "mean_gap_ms": mean_gap_s * 1e3,
+                     "kernel_ms": kern_ms, "gpu_busy_frac": kern_ms / 1e3 / wall if wall > 0 else 0.0,
+                     "algorithmic_bytes": alg, "launches": s1["launches"] - s0["launches"],
+                     "batched_launches": s1["batches"] - s0["batches"],
+                     "repeated_launches": s1["batch_repeats"] - s0["batch_repeats"],
+                     "h2d_bytes": sum(r.size ** 3 * 8 if r.kind != "bs" else 12 * r.size for r in res),
+                     "d2h_bytes": sum(r.size ** 3 * 8 if r.kind != "bs" else 8 * r.size for r in res),
+                     "peak_device_bytes": srv.stats.peak_bytes, "max_active": dict(srv.stats.max_active)})
+        top = max(kd.items(), key=lambda kv: kv[1]["ms"]) if kd else (None, {"ms": 0.0, "launches": 0})
+        summ["dominant_kernel"] = {"name": top[0], "ms": top[1]["ms"], "launches": top[1]["launches"]}
+        return summ, clk
+
+    offered, clk = one_run(cfg["mean_gap_ms"] * 1e-3)
+    cap = offered["sustained_rps"]
+    at_load = None
+    if not args.quick and cap > 0:
+        at_load, _ = one_run(1.0 / (cfg["load_fraction"] * cap))
+    achieved = offered["algorithmic_bytes"] / (offered["kernel_ms"] / 1e3) / 1e9 if offered["kernel_ms"] > 0 else 0.0
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": peaks["source"],
+                "kernel": "all kernels of the run (batched CG/BiCGSTAB iterations dominate)",
+                "kernel_ms": offered["kernel_ms"], "launches": offered["launches"],
+                "algorithmic_bytes_per_launch": offered["algorithmic_bytes"] / max(1, offered["launches"])}
+    cpu = None
+    if not args.quick:
+        v, u, sample = oracle_rate("serve", budget_s=10.0)
+        cpu = {"value": v, "unit": u, "cores": 1, "kind": "oracle", "sample": sample}
+    n = offered["requests"]
+    line = {"metric": METRIC["serve"][0], "value": offered["sustained_rps"], "unit": "requests/s", "n_gpus": 1,
+            "steps": n, "warmup": len(warm), "ms_per_step": offered["wall_s"] * 1e3 / max(1, n),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+            "data": "synthetic (seeded generators of synth/inputs.py)",
+            "config": {"workload": WORKLOAD["serve"], "requests": n, "l2": "inputs larger than L2",
+                       "launch": "continuous batching: one batched persistent launch per solver kind per "
+                                 "iteration, dfs_batch_repeat within a tick",
+                       "parallelism": "replicas x1"},
+            "p50_ms": offered["p50_ms"], "p99_ms": offered["p99_ms"],
+            "e2e": {"value": offered["sustained_rps"], "unit": "requests/s",
+                    "h2d_bytes_per_step": offered["h2d_bytes"] / max(1, n),
+                    "d2h_bytes_per_step": offered["d2h_bytes"] / max(1, n),
+                    "note": "a step is one request; payload upload and result download are inside the loop"},
+            "gpu_launches": offered["launches"], "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
+            "serving": {"offered_load": offered, "at_fraction_of_capacity": at_load,
+                        "load_fraction": cfg["load_fraction"], "operator_load_s": t_load}}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="bs", choices=["bs", "cg", "jacobi", "batched"])
+    ap.add_argument("--workload", default="bs", choices=["bs", "cg", "jacobi", "batched", "serve"])
+    ap.add_argument("--requests", type=int, default=0, help="serving: requests per run (default: the config's)")
     ap.add_argument("--fp32", action="store_true", help="batched CG in FP32 instead of FP64")
     ap.add_argument("--quick", action="store_true", help="skip the comparison arms (for profiling)")
     ap.add_argument("--bs-n", type=int, default=0, help="Black-Scholes batch size (profiling a smaller case)")
@@ -460,6 +607,9 @@ def main():
     _build.build()
     if args.compile_report:
         print(json.dumps({"compile_report": compile_report(torch, stream, sms)}))
+        return
+    if args.workload == "serve":
+        run_serving(args, torch, stream, sms, cache, dev)
         return
 
     metric, unit, dtype = METRIC[args.workload]

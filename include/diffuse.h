@@ -293,6 +293,41 @@ int dfs_batch_begin(dfs_ctx *ctx);
 int dfs_batch_next(dfs_ctx *ctx);
 int dfs_batch_end(dfs_ctx *ctx);
 
+/*
+ * dfs_batch_repeat -- issue the most recent batch n more times, as if the
+ * application had submitted the same K instance windows again n times
+ * (memoisation of Section 5.2 carried to the launch itself: no analysis, no
+ * descriptor upload, one kernel launch per repetition).
+ *
+ * Allowed only while the batch is still "steady": every store it uses held a
+ * value before it ran or was eliminated as a temporary (so each instance
+ * only updates stores it already owns, as an in-place solver iteration
+ * does), and since then no other window was launched, no graph was captured
+ * or launched, and no store with device memory was freed.  dfs_batch_repeat
+ * first flushes the pending window; if that launches anything the batch is
+ * no longer steady.  n == 0 does nothing.
+ * Returns DFS_OK; DFS_ERR_INVALID for n < 0; DFS_ERR_STATE when there is no
+ * steady batch to repeat (nothing is launched); DFS_ERR_CUDA when a launch
+ * fails.  Device errors are deferred as for any launch.
+ */
+int dfs_batch_repeat(dfs_ctx *ctx, int32_t n);
+
+/*
+ * dfs_read_scalars -- flushes, then copies the values of n 0-d stores to
+ * host_out[0..n) as doubles (FP32 and integer values converted exactly where
+ * representable) with one gather kernel and one device-to-host copy, and
+ * synchronizes.  A serving loop uses it to read every active solve's
+ * residual norm at once instead of n separate dfs_store_read calls.
+ * stores: n handles of 0-d stores (roots or views) that hold values;
+ * host_out: n doubles owned by the caller.  The context keeps a small device
+ * buffer for the gather (grown as needed, freed at dfs_shutdown).
+ * Returns DFS_OK; DFS_ERR_INVALID for null pointers, n < 0 or a store that
+ * is not 0-d; DFS_ERR_STATE for an unknown or released store, one that holds
+ * no value, or a call while capturing; DFS_ERR_NO_DEVICE in an
+ * analysis-only context; any deferred device error, as dfs_store_read.
+ */
+int dfs_read_scalars(dfs_ctx *ctx, int32_t n, const dfs_store *stores, double *host_out);
+
 /* Source of the generated CUDA for the most recent launch (debugging). */
 int dfs_last_kernel_source(dfs_ctx *ctx, char *buf, size_t len, size_t *needed);
 

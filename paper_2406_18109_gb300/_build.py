@@ -24,7 +24,7 @@ LIB = os.path.join(LIBDIR, "libdiffuse.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 HOST_SOURCES = ["runtime.cpp", "fusion.cpp", "codegen.cpp", "batchgen.cpp", "jit.cpp"]
-DEVICE_SOURCES = ["dfs_check.cu", "noalloc.cu"]
+DEVICE_SOURCES = ["dfs_check.cu", "noalloc.cu", "gather.cu"]
 GENCODE = "arch=compute_103a,code=sm_103a"
 
 

@@ -214,6 +214,14 @@ class Runtime:
         """Run the batch: one launch over every instance."""
         B.dfs_batch_end(self.ctx)
 
+    def batch_repeat(self, n: int):
+        """Run the last (steady, in-place) batch n more times (dfs_batch_repeat)."""
+        B.dfs_batch_repeat(self.ctx, n)
+
+    def read_scalars(self, arrays) -> list:
+        """Values of many 0-d arrays with one gather and one copy (dfs_read_scalars)."""
+        return B.dfs_read_scalars(self.ctx, [a.handle for a in arrays])
+
     # ------------------------------------------------------- graph capture
     def capture_begin(self):
         B.dfs_capture_begin(self.ctx)

@@ -36,7 +36,7 @@ EXPORTS = ("dfs_config_default", "dfs_init", "dfs_shutdown", "dfs_store_create",
            "dfs_flush", "dfs_sync", "dfs_last_error", "dfs_plan_json", "dfs_stats_json",
            "dfs_last_kernel_source", "dfs_version", "dfs_dot_noalloc", "dfs_capture_begin",
            "dfs_capture_end", "dfs_graph_launch", "dfs_graph_destroy", "dfs_batch_begin",
-           "dfs_batch_next", "dfs_batch_end")
+           "dfs_batch_next", "dfs_batch_end", "dfs_batch_repeat", "dfs_read_scalars")
 
 
 class dfs_config(C.Structure):
@@ -98,6 +98,8 @@ def lib():
             "dfs_batch_begin": (C.c_int, [P]),
             "dfs_batch_next": (C.c_int, [P]),
             "dfs_batch_end": (C.c_int, [P]),
+            "dfs_batch_repeat": (C.c_int, [P, I32]),
+            "dfs_read_scalars": (C.c_int, [P, I32, pI64, C.POINTER(C.c_double)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -269,6 +271,20 @@ def dfs_batch_next(ctx) -> None:
 
 def dfs_batch_end(ctx) -> None:
     _check(ctx, lib().dfs_batch_end(ctx))
+
+
+def dfs_batch_repeat(ctx, n: int) -> None:
+    _check(ctx, lib().dfs_batch_repeat(ctx, n))
+
+
+def dfs_read_scalars(ctx, stores, out=None):
+    """Values of the 0-d stores `stores` as a list of floats (or written into
+    `out`, a C double array of at least len(stores) elements)."""
+    n = len(stores)
+    hs = _i64s(stores)
+    buf = out if out is not None else (C.c_double * max(1, n))()
+    _check(ctx, lib().dfs_read_scalars(ctx, n, hs, buf))
+    return buf[:n]
 
 
 def dfs_version() -> int:

@@ -25,3 +25,12 @@ BATCHED_CG = dict(count=256, seed=4, iters=100, dtype="f64", tile=512, block=256
 # Jacobi: Fig. 1 stencil on an 8192x8192 FP32 grid (8190^2 interior),
 # 200 sweeps, interior U[0,1] (seed 2), boundary 1.0
 JACOBI = dict(N=8190, sweeps=200, seed=2, rows=16, block=256, unroll=8, sweeps_per_flush=1)
+
+# Serving: Poisson arrivals (exponential gaps, mean 2 ms, seed 3) of CG and
+# BiCGSTAB solves on 3-D 7-point Poisson operators (m from a log-spaced
+# ladder 64..256, FP64, tol 1e-8) and Black-Scholes batches of 2^16..2^24
+# FP32 options, under a 120 GB device-memory budget; solves advance 8
+# iterations per tick; at most 64 active solves per kind.  `count` requests
+# per run (a bounded stand-in for an open-ended stream).
+SERVING = dict(count=240, seed=3, mean_gap_ms=2.0, budget_gb=120, tol=1e-8, iters_per_tick=8, max_active=64,
+               tile=2048, block=256, unroll=2, load_fraction=0.8)

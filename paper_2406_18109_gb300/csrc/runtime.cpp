@@ -56,6 +56,11 @@ struct Stats {
 
 }  // namespace dfs
 
+namespace dfs {
+// gather.cu
+cudaError_t launch_gather_scalars(const int64_t* desc_dev, int n, double* out_dev, cudaStream_t s);
+}  // namespace dfs
+
 struct dfs_ctx {
   dfs_config cfg{};
   bool device = false;
@@ -112,8 +117,23 @@ struct dfs_ctx {
   std::unordered_map<std::string, Table> tables;  // descriptor bytes -> device copy
   double* sval = nullptr;
   size_t sval_cap = 0;
-  int64_t batches = 0, batched_instances = 0, batch_fallbacks = 0;
+  int64_t batches = 0, batched_instances = 0, batch_fallbacks = 0, batch_repeats = 0;
   std::string batch_fallback_reason;
+  // the most recent batched launch, kept for dfs_batch_repeat while steady
+  struct LastBatch {
+    bool ok = false;
+    CUfunction fn = nullptr;
+    int grid = 0, block = 0, nbarriers = 0, ninst = 0;
+    bool coop = false;
+    uint64_t blob[8] = {};
+    int64_t groups = 0;
+    std::string name;
+  };
+  LastBatch lastb;
+  // dfs_read_scalars: descriptors (pinned) and gathered values (device)
+  int64_t* gather_host = nullptr;
+  void* gather_dev = nullptr;
+  size_t gather_cap = 0;  // scalars
 };
 
 namespace dfs {
@@ -143,6 +163,7 @@ void maybe_free(dfs_ctx* c, int64_t root) {
   StoreRec& r = it->second;
   if (r.app_refs > 0 || r.pending > 0) return;
   if (r.owned && r.ptr && c->device) {
+    c->lastb.ok = false;
     if (c->capturing && !c->captured_allocs.count(root)) {
       // allocated before the capture: replays of the graph may still read it
       c->capture_deferred.push_back(r.ptr);
@@ -523,6 +544,7 @@ int build_window(dfs_ctx* c, const WindowInfo& wi, std::unique_ptr<CachedWindow>
 }
 
 int run_window(dfs_ctx* c, const CachedWindow& cw, const WindowInfo& wi) {
+  c->lastb.ok = false;
   for (int id : cw.materialise) {
     StoreRec& r = c->stores.at(wi.by_canon[id]);
     int rc = materialise(c, r);
@@ -725,6 +747,47 @@ std::string batch_key(const std::vector<Task>& w, const std::map<int64_t, RootIn
     }
   }
   return k;
+}
+
+// One launch of a batched kernel (timing, statistics); also used by
+// dfs_batch_repeat.
+int launch_batched(dfs_ctx* c, const dfs_ctx::LastBatch& L) {
+  const bool timing = c->cfg.time_launches && !c->capturing;
+  dfs_ctx::Timed tm{nullptr, nullptr, L.name};
+  if (timing) {
+    for (cudaEvent_t* e : {&tm.a, &tm.b}) {
+      if (!c->event_pool.empty()) {
+        *e = c->event_pool.back();
+        c->event_pool.pop_back();
+      } else {
+        CUDA_OK(cudaEventCreate(e));
+      }
+    }
+    CUDA_OK(cudaEventRecord(tm.a, c->stream));
+  }
+  uint64_t blob[8];
+  std::memcpy(blob, L.blob, sizeof blob);
+  void* params[] = {blob};
+  CUresult cr = L.coop ? c->drv.LaunchCooperativeKernel(L.fn, L.grid, 1, 1, L.block, 1, 1, 0, (CUstream)c->stream, params)
+                       : c->drv.LaunchKernel(L.fn, L.grid, 1, 1, L.block, 1, 1, 0, (CUstream)c->stream, params, nullptr);
+  if (cr != CUDA_SUCCESS) {
+    const char* es = nullptr;
+    c->drv.GetErrorString(cr, &es);
+    return fail(c, DFS_ERR_CUDA, std::string("batched launch: ") + (es ? es : "?"));
+  }
+  if (timing) {
+    CUDA_OK(cudaEventRecord(tm.b, c->stream));
+    c->timed.push_back(tm);
+  }
+  if (c->capturing)
+    c->capture_launches += 1;
+  else
+    c->st.launches += 1;
+  c->st.barriers += L.nbarriers;
+  c->st.groups += L.groups;
+  c->st.last_grid = L.grid;
+  c->st.last_block = L.block;
+  return DFS_OK;
 }
 
 int flush_batch(dfs_ctx* c) {
@@ -937,7 +1000,6 @@ int flush_batch(dfs_ctx* c) {
   const int64_t kk = K;
   std::memcpy(&blob[6], &kk, 8);
   std::memcpy(&blob[7], &red_stride, 8);
-  void* params[] = {blob};
   int per_sm = be->k->occupancy > 0 ? be->k->occupancy : 1;
   if (c->cfg.ctas_per_sm > 0) per_sm = std::min(per_sm, c->cfg.ctas_per_sm);
   const int grid = std::max(1, per_sm * c->sms);
@@ -946,41 +1008,24 @@ int flush_batch(dfs_ctx* c) {
     release_window(c);
     return fail(c, DFS_ERR_CUDA, "batched kernel cannot be resident for a cooperative launch");
   }
-  const bool timing = c->cfg.time_launches && !c->capturing;
-  dfs_ctx::Timed tm{nullptr, nullptr, bc.name};
-  if (timing) {
-    for (cudaEvent_t* e : {&tm.a, &tm.b}) {
-      if (!c->event_pool.empty()) {
-        *e = c->event_pool.back();
-        c->event_pool.pop_back();
-      } else {
-        CUDA_OK(cudaEventCreate(e));
-      }
-    }
-    CUDA_OK(cudaEventRecord(tm.a, c->stream));
-  }
-  CUresult cr = coop ? c->drv.LaunchCooperativeKernel(be->k->fn, grid, 1, 1, spec.block, 1, 1, 0, (CUstream)c->stream, params)
-                     : c->drv.LaunchKernel(be->k->fn, grid, 1, 1, spec.block, 1, 1, 0, (CUstream)c->stream, params, nullptr);
-  if (cr != CUDA_SUCCESS) {
-    const char* es = nullptr;
-    c->drv.GetErrorString(cr, &es);
+  dfs_ctx::LastBatch L;
+  L.fn = be->k->fn;
+  L.grid = grid;
+  L.block = spec.block;
+  L.coop = coop;
+  L.nbarriers = bc.nbarriers;
+  L.ninst = K;
+  L.groups = (int64_t)p0.groups.size() * K;
+  L.name = bc.name;
+  std::memcpy(L.blob, blob, sizeof blob);
+  c->lastb.ok = false;
+  const int lrc = launch_batched(c, L);
+  if (lrc) {
     release_window(c);
-    return fail(c, DFS_ERR_CUDA, std::string("batched launch: ") + (es ? es : "?"));
+    return lrc;
   }
-  if (timing) {
-    CUDA_OK(cudaEventRecord(tm.b, c->stream));
-    c->timed.push_back(tm);
-  }
-  if (c->capturing)
-    c->capture_launches += 1;
-  else
-    c->st.launches += 1;
-  c->st.barriers += bc.nbarriers;
-  c->st.groups += (int64_t)p0.groups.size() * K;
   c->st.last_regs = be->k->regs;
   c->st.last_occupancy = be->k->occupancy;
-  c->st.last_grid = grid;
-  c->st.last_block = spec.block;
   // every written root that has memory now holds a value
   for (const LaunchRoot& lr : spec.roots) {
     if (lr.param < 0 || !lr.written) continue;
@@ -989,6 +1034,16 @@ int flush_batch(dfs_ctx* c) {
   }
   c->batches += 1;
   c->batched_instances += K;
+  // steady: every store of the batch held a value before it ran (or is a
+  // temporary), so running the same kernel again is the same as submitting
+  // the same instances again
+  bool steady = !c->capturing;
+  for (const LaunchRoot& lr : spec.roots)
+    if (!lr.temp && !lr.valid_before) steady = false;
+  if (steady) {
+    c->lastb = L;
+    c->lastb.ok = true;
+  }
   release_window(c);
   return DFS_OK;
 }
@@ -1105,6 +1160,8 @@ int dfs_shutdown(dfs_ctx* c) {
     for (auto& kv : c->tables) cudaFreeAsync(kv.second.dev, c->stream);
     c->tables.clear();
     cudaStreamSynchronize(c->stream);
+    if (c->gather_host) cudaFreeHost(c->gather_host);
+    if (c->gather_dev) cudaFree(c->gather_dev);
     for (auto& t : c->timed) {
       cudaEventDestroy(t.a);
       cudaEventDestroy(t.b);
@@ -1395,6 +1452,7 @@ int dfs_capture_begin(dfs_ctx* c) {
   if (c->capturing) return fail(c, DFS_ERR_STATE, "already capturing");
   int rc = flush(c);
   if (rc) return rc;
+  c->lastb.ok = false;
   // reduction scratch cannot be reallocated inside a capture: reserve 1 MB
   const size_t want = 1 << 20;
   if (c->partials_cap < want) {
@@ -1470,6 +1528,7 @@ int dfs_graph_launch(dfs_ctx* c, dfs_graph h) {
   if (c->capturing) return fail(c, DFS_ERR_STATE, "cannot launch a graph while capturing");
   int rc = flush(c);
   if (rc) return rc;
+  c->lastb.ok = false;
   CUDA_OK(cudaGraphLaunch(it->second.exec, c->stream));
   c->st.launches += it->second.launches;
   return DFS_OK;
@@ -1512,6 +1571,76 @@ int dfs_batch_end(dfs_ctx* c) {
   return rc;
 }
 
+int dfs_batch_repeat(dfs_ctx* c, int32_t n) {
+  if (!c) return DFS_ERR_INVALID;
+  if (n < 0) return fail(c, DFS_ERR_INVALID, "negative repeat count");
+  if (c->batching) return fail(c, DFS_ERR_STATE, "dfs_batch_repeat inside a batch");
+  if (!c->device) return fail(c, DFS_ERR_NO_DEVICE, "analysis-only context");
+  const int rc = flush(c);
+  if (rc) return rc;
+  if (!c->lastb.ok) return fail(c, DFS_ERR_STATE, "no steady batch to repeat");
+  for (int32_t i = 0; i < n; ++i) {
+    const int lrc = launch_batched(c, c->lastb);
+    if (lrc) {
+      c->lastb.ok = false;
+      return lrc;
+    }
+    c->batches += 1;
+    c->batch_repeats += 1;
+    c->batched_instances += c->lastb.ninst;
+  }
+  return DFS_OK;
+}
+
+int dfs_read_scalars(dfs_ctx* c, int32_t n, const dfs_store* hs, double* out) {
+  if (!c) return DFS_ERR_INVALID;
+  if (n < 0 || (n > 0 && (!hs || !out))) return fail(c, DFS_ERR_INVALID, "bad arguments");
+  if (!c->device) return fail(c, DFS_ERR_NO_DEVICE, "analysis-only context");
+  if (c->capturing) return fail(c, DFS_ERR_STATE, "dfs_read_scalars while capturing");
+  for (int32_t i = 0; i < n; ++i) {
+    StoreRec* r = find_store(c, hs[i]);
+    if (!r) return fail(c, DFS_ERR_STATE, "unknown or released store");
+    if (r->ndim != 0) return fail(c, DFS_ERR_INVALID, "dfs_read_scalars takes 0-d stores");
+  }
+  int rc = flush(c);
+  if (rc) return rc;
+  if (n == 0) {
+    CUDA_OK(cudaStreamSynchronize(c->stream));
+    return check_device_error(c);
+  }
+  if ((size_t)n > c->gather_cap) {
+    CUDA_OK(cudaStreamSynchronize(c->stream));
+    if (c->gather_host) cudaFreeHost(c->gather_host);
+    if (c->gather_dev) cudaFree(c->gather_dev);
+    c->gather_host = nullptr;
+    c->gather_dev = nullptr;
+    c->gather_cap = 0;
+    const size_t cap = std::max<size_t>(1024, (size_t)n);
+    // per scalar: descriptor (address, dtype) then the gathered double
+    CUDA_OK(cudaMallocHost((void**)&c->gather_host, cap * 3 * sizeof(int64_t)));
+    CUDA_OK(cudaMalloc(&c->gather_dev, cap * 3 * sizeof(int64_t)));
+    c->gather_cap = cap;
+  }
+  for (int32_t i = 0; i < n; ++i) {
+    const StoreRec& r = *find_store(c, hs[i]);
+    const StoreRec& root = c->stores.at(r.root);
+    if (!root.ptr || !root.valid) return fail(c, DFS_ERR_STATE, "store has no value");
+    const char* p = (const char*)root.ptr;
+    for (int d = 0; d < root.ndim; ++d) p += (size_t)r.off[d] * root.stride[d] * dtype_size(r.dtype);
+    c->gather_host[2 * i] = (int64_t)(uintptr_t)p;
+    c->gather_host[2 * i + 1] = r.dtype;
+  }
+  int64_t* desc = static_cast<int64_t*>(c->gather_dev);
+  double* vals = reinterpret_cast<double*>(desc + 2 * c->gather_cap);
+  CUDA_OK(cudaMemcpyAsync(desc, c->gather_host, (size_t)n * 2 * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+  CUDA_OK(launch_gather_scalars(desc, n, vals, c->stream));
+  double* hv = reinterpret_cast<double*>(c->gather_host + 2 * c->gather_cap);
+  CUDA_OK(cudaMemcpyAsync(hv, vals, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(cudaStreamSynchronize(c->stream));
+  std::memcpy(out, hv, (size_t)n * sizeof(double));
+  return check_device_error(c);
+}
+
 const char* dfs_last_error(dfs_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
 int dfs_plan_json(dfs_ctx* c, char* buf, size_t len, size_t* needed) {
@@ -1546,7 +1675,7 @@ int dfs_stats_json(dfs_ctx* c, char* buf, size_t len, size_t* needed) {
   }
   o << "}";
   o << ", \"batches\": " << c->batches << ", \"batched_instances\": " << c->batched_instances
-    << ", \"batch_fallbacks\": " << c->batch_fallbacks << ", \"batch_fallback_reason\": \"" << c->batch_fallback_reason
+    << ", \"batch_repeats\": " << c->batch_repeats << ", \"batch_fallbacks\": " << c->batch_fallbacks << ", \"batch_fallback_reason\": \"" << c->batch_fallback_reason
     << "\"";
   o << ", \"sms\": " << c->sms << "}";
   return write_json(o.str(), buf, len, needed);

@@ -10,7 +10,12 @@ fuses.  The task counts are those of the unfused streams.
   * The Fig. 1a stencil (Jacobi relaxation over five aliased views): 6 tasks
     per sweep.
   * BiCGSTAB: 4 dots, 2 SpMVs, scalar arithmetic and vector updates per
-    iteration.
+    iteration (plus r.r for the convergence test).
+
+The *_inplace variants keep a solve's whole state in stores created once and
+updated in place, so one iteration is a steady window: it can be captured in
+a CUDA graph, batched with other solves of other sizes, and re-run with
+dfs_batch_repeat.
 """
 from __future__ import annotations
 
@@ -95,8 +100,10 @@ class CGInPlace:
 
 
 def cg_start_inplace(b: Array) -> CGInPlace:
+    """cg_start plus q = 0, so that every state store holds a value and the
+    first iteration is already a steady window."""
     st = cg_start(b)
-    q = b.rt.empty(b.shape, b.dtype)
+    q = A.full(b.rt, b.shape, 0.0, b.dtype)
     return CGInPlace(st.x, st.r, st.p, q, st.rho)
 
 
@@ -180,3 +187,49 @@ def bicgstab_iteration(Amat: CSR, s: BiCGState) -> Array:
     s.r = sv - s.omega * t
     s.rho = rho
     return A.dot(s.r, s.r)
+
+
+@dataclass
+class BiCGInPlace:
+    """BiCGSTAB state in fixed stores (vectors x, r, rhat, p, v, s, t; scalars
+    rho, alpha, omega and rr = r.r after the last iteration)."""
+    x: Array
+    r: Array
+    rhat: Array
+    p: Array
+    v: Array
+    s: Array
+    t: Array
+    rho: Array
+    alpha: Array
+    omega: Array
+    rr: Array
+
+
+def bicgstab_start_inplace(b: Array) -> BiCGInPlace:
+    """x0 = 0, r0 = rhat = b, p0 = v0 = 0, rho = alpha = omega = 1, rr = b.b."""
+    rt = b.rt
+    st = BiCGInPlace(A.full(rt, b.shape, 0.0, b.dtype), A.copy(b), A.copy(b), A.full(rt, b.shape, 0.0, b.dtype),
+                     A.full(rt, b.shape, 0.0, b.dtype), A.full(rt, b.shape, 0.0, b.dtype),
+                     A.full(rt, b.shape, 0.0, b.dtype), A.full(rt, (), 1.0, b.dtype), A.full(rt, (), 1.0, b.dtype),
+                     A.full(rt, (), 1.0, b.dtype), None)
+    st.rr = A.dot(st.r, st.r)
+    return st
+
+
+def bicgstab_iteration_inplace(Amat: CSR, st: BiCGInPlace) -> None:
+    """One BiCGSTAB iteration (van der Vorst) written into the state stores, in
+    the oracle's operation order; leaves r.r in st.rr."""
+    rho = A.dot(st.rhat, st.r)
+    beta = (rho / st.rho) * (st.alpha / st.omega)
+    st.p[...] = st.r + beta * (st.p - st.omega * st.v)
+    Amat.spmv(st.p, st.v)
+    st.alpha[...] = rho / A.dot(st.rhat, st.v)
+    st.s[...] = st.r - st.alpha * st.v
+    Amat.spmv(st.s, st.t)
+    st.omega[...] = A.dot(st.t, st.s) / A.dot(st.t, st.t)
+    st.x += st.alpha * st.p
+    st.x += st.omega * st.s
+    st.r[...] = st.s - st.omega * st.t
+    st.rr[...] = A.dot(st.r, st.r)
+    st.rho[...] = rho

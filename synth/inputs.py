@@ -175,3 +175,41 @@ def random_spd_csr(n: int, seed: int, kmin: int = 2, kmax: int = 13):
     np.add.at(rowptr, Rall + 1, 1)
     rowptr = np.cumsum(rowptr)
     return rowptr.astype(np.int32), Call.astype(np.int32), Vall.astype(np.float64)
+
+
+# 3-D grid sides of the served Poisson operators: log-spaced from 64 to 256
+# (64 * 2^(k/4), k = 0..8), so that drawing a side uniformly from the ladder is
+# a log-uniform draw of m in [64, 256]
+SERVE_LADDER = tuple(int(round(64 * 2 ** (k / 4))) for k in range(9))
+
+
+def serving_requests(count: int, seed: int = 3, mean_gap_s: float = 2e-3, ladder=SERVE_LADDER,
+                     bs_log2=(16, 24)):
+    """A Poisson-arrival request stream (exponential gaps of mean mean_gap_s).
+
+    Each request is, with probability 1/3 each, a CG solve or a BiCGSTAB solve
+    on the 3-D 7-point Poisson matrix of an m^3 grid (m drawn uniformly from
+    `ladder`), or a Black-Scholes batch of n = 2^u options, u uniform in
+    bs_log2.  Returns dicts {rid, arrival, kind, size, seed} in arrival order;
+    the request's data come from serving_payload.
+    """
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(mean_gap_s, count)
+    kinds = rng.integers(0, 3, count)
+    rungs = rng.integers(0, len(ladder), count)
+    u = rng.uniform(bs_log2[0], bs_log2[1], count)
+    t = np.cumsum(gaps) - gaps[0]
+    out = []
+    for i in range(count):
+        kind = ("cg", "bicgstab", "bs")[int(kinds[i])]
+        size = int(ladder[int(rungs[i])]) if kind != "bs" else int(round(2.0 ** u[i]))
+        out.append({"rid": i, "arrival": float(t[i]), "kind": kind, "size": size, "seed": 100_000 + seed * 10_000 + i})
+    return out
+
+
+def serving_payload(req: dict):
+    """Host data of one request: x* ~ U[-1,1] over the m^3 unknowns of a
+    solve (its right-hand side is b = A x*), or (S, K, T) of an option batch."""
+    if req["kind"] == "bs":
+        return bs_inputs(req["size"], seed=req["seed"])
+    return uniform(req["seed"], -1.0, 1.0, req["size"] ** 3)

@@ -240,6 +240,17 @@ def test_capture_api_needs_a_device_and_checks_state():
     with pytest.raises(B.DfsError) as e:
         rt.graph_launch(12345)
     assert e.value.code == -7
+    # batch repetition and the scalar gather need a device; bad arguments first
+    with pytest.raises(B.DfsError) as e:
+        rt.batch_repeat(-1)
+    assert e.value.code == -1
+    with pytest.raises(B.DfsError) as e:
+        rt.batch_repeat(1)
+    assert e.value.code == -2
+    s = rt.empty(())
+    with pytest.raises(B.DfsError) as e:
+        rt.read_scalars([s])
+    assert e.value.code == -2
 
 
 def test_window_size_triggers_analysis():
