@@ -108,6 +108,9 @@ struct dfs_ctx {
     dfs::BatchCode code;
     const dfs::Compiled* k = nullptr;
     dfs::Plan plan;
+    // canonical index (first-use order within an instance) of the root of
+    // each pointer slot: later batches of the same structure use other stores
+    std::vector<int> ptr_canon;
   };
   std::unordered_map<std::string, std::unique_ptr<BatchEntry>> bcache;
   struct Table {
@@ -805,7 +808,9 @@ int flush_batch(dfs_ctx* c) {
     c->batch_fallback_reason = why;
     return flush(c);
   };
-  if (inst.size() < 2) return flush(c);
+  // a single instance also takes the size-generic batched kernel: a stream
+  // of one-off problems of new sizes then compiles nothing new
+  if (inst.empty()) return flush(c);
   if (c->cfg.launch_mode != DFS_LAUNCH_PERSISTENT || !c->cfg.fusion) return fallback("batching runs fused, persistent launches");
   const int K = (int)inst.size();
   std::vector<std::vector<Task>> iw(K);
@@ -911,14 +916,18 @@ int flush_batch(dfs_ctx* c) {
       return fail(c, DFS_ERR_COMPILE, err);
     }
     ne->plan = p0;
+    {
+      std::map<int64_t, int> ci;
+      for (size_t k = 0; k < canon[0].size(); ++k) ci[canon[0][k]] = (int)k;
+      for (int64_t r : ne->code.ptr_roots) ne->ptr_canon.push_back(ci.at(r));
+    }
     be = ne.get();
     c->bcache[ckey] = std::move(ne);
   }
   const BatchCode& bc = be->code;
   std::map<int64_t, int> ci0;
   for (size_t k = 0; k < canon[0].size(); ++k) ci0[canon[0][k]] = (int)k;
-  std::vector<int> ptr_canon;
-  for (int64_t r : bc.ptr_roots) ptr_canon.push_back(ci0.at(r));
+  const std::vector<int>& ptr_canon = be->ptr_canon;
   // descriptors and work lists
   const size_t NP = (size_t)std::max(1, bc.nptr), NIm = (size_t)std::max(1, bc.nimm), NV = (size_t)std::max(1, bc.nv);
   const size_t per = NP + NIm + NV;
@@ -1063,6 +1072,13 @@ int write_json(const std::string& s, char* buf, size_t len, size_t* needed) {
 
 using namespace dfs;
 
+// No C++ exception may cross the C ABI: an internal failure (a violated
+// invariant surfacing as std::out_of_range, or std::bad_alloc) is reported
+// as DFS_ERR_INVALID with its message in dfs_last_error.
+static int internal_error(dfs_ctx* c, const char* what) {
+  return fail(c, DFS_ERR_INVALID, std::string("internal error: ") + (what ? what : "?"));
+}
+
 extern "C" {
 
 int dfs_version(void) { return 100; }
@@ -1083,96 +1099,108 @@ void dfs_config_default(dfs_config* cfg) {
 }
 
 int dfs_init(dfs_ctx** out, const dfs_config* cfg_in) {
-  if (!out) return DFS_ERR_INVALID;
-  *out = nullptr;
-  auto c = std::make_unique<dfs_ctx>();
-  dfs_config cfg;
-  dfs_config_default(&cfg);
-  if (cfg_in) cfg = *cfg_in;
-  if (cfg.window_size < 1) cfg.window_size = 1;
-  if (cfg.block_threads == 0) cfg.block_threads = 256;
-  if (cfg.block_threads != 128 && cfg.block_threads != 256 && cfg.block_threads != 512 && cfg.block_threads != 1024)
-    return DFS_ERR_INVALID;
-  if (cfg.unroll <= 0) cfg.unroll = 2;
-  if (cfg.unroll > 8) cfg.unroll = 8;
-  if (cfg.barrier_timeout_s <= 0) cfg.barrier_timeout_s = 2.0;
-  if (cfg.launch_mode != DFS_LAUNCH_PER_TASK && cfg.launch_mode != DFS_LAUNCH_PERSISTENT) return DFS_ERR_INVALID;
-  c->cfg = cfg;
-  std::string cache_dir = cfg.cache_dir ? cfg.cache_dir : "";
-  c->cfg.cache_dir = nullptr;
-  if (cfg.device >= 0) {
-    dfs_ctx* cp = c.get();
-    int n = 0;
-    cudaError_t e = cudaGetDeviceCount(&n);
-    if (e != cudaSuccess || n <= cfg.device) return fail(nullptr, DFS_ERR_NO_DEVICE, "");
-    if (cudaSetDevice(cfg.device) != cudaSuccess) return DFS_ERR_CUDA;
-    cudaDeviceProp prop;
-    if (cudaGetDeviceProperties(&prop, cfg.device) != cudaSuccess) return DFS_ERR_CUDA;
-    c->sms = prop.multiProcessorCount;
-    std::string err;
-    if (!driver_load(c->drv, err)) return DFS_ERR_CUDA;
-    char arch[32];
-    snprintf(arch, sizeof arch, "sm_%d%d%s", prop.major, prop.minor, prop.major >= 9 ? "a" : "");
-    c->jit = std::make_unique<Jit>(&c->drv, arch, cache_dir);
-    if (cfg.stream) {
-      c->stream = (cudaStream_t)cfg.stream;
+  try {
+    if (!out) return DFS_ERR_INVALID;
+    *out = nullptr;
+    auto c = std::make_unique<dfs_ctx>();
+    dfs_config cfg;
+    dfs_config_default(&cfg);
+    if (cfg_in) cfg = *cfg_in;
+    if (cfg.window_size < 1) cfg.window_size = 1;
+    if (cfg.block_threads == 0) cfg.block_threads = 256;
+    if (cfg.block_threads != 128 && cfg.block_threads != 256 && cfg.block_threads != 512 && cfg.block_threads != 1024)
+      return DFS_ERR_INVALID;
+    if (cfg.unroll <= 0) cfg.unroll = 2;
+    if (cfg.unroll > 8) cfg.unroll = 8;
+    if (cfg.barrier_timeout_s <= 0) cfg.barrier_timeout_s = 2.0;
+    if (cfg.launch_mode != DFS_LAUNCH_PER_TASK && cfg.launch_mode != DFS_LAUNCH_PERSISTENT) return DFS_ERR_INVALID;
+    c->cfg = cfg;
+    std::string cache_dir = cfg.cache_dir ? cfg.cache_dir : "";
+    c->cfg.cache_dir = nullptr;
+    if (cfg.device >= 0) {
+      dfs_ctx* cp = c.get();
+      int n = 0;
+      cudaError_t e = cudaGetDeviceCount(&n);
+      if (e != cudaSuccess || n <= cfg.device) return fail(nullptr, DFS_ERR_NO_DEVICE, "");
+      if (cudaSetDevice(cfg.device) != cudaSuccess) return DFS_ERR_CUDA;
+      cudaDeviceProp prop;
+      if (cudaGetDeviceProperties(&prop, cfg.device) != cudaSuccess) return DFS_ERR_CUDA;
+      c->sms = prop.multiProcessorCount;
+      std::string err;
+      if (!driver_load(c->drv, err)) return DFS_ERR_CUDA;
+      char arch[32];
+      snprintf(arch, sizeof arch, "sm_%d%d%s", prop.major, prop.minor, prop.major >= 9 ? "a" : "");
+      c->jit = std::make_unique<Jit>(&c->drv, arch, cache_dir);
+      if (cfg.stream) {
+        c->stream = (cudaStream_t)cfg.stream;
+      } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return DFS_ERR_CUDA;
+        c->own_stream = true;
+      }
+      if (cudaMalloc(&c->ctl, sizeof(Ctl)) != cudaSuccess) return DFS_ERR_OOM;
+      if (cudaMemset(c->ctl, 0, sizeof(Ctl)) != cudaSuccess) return DFS_ERR_CUDA;
+      if (cudaDeviceSynchronize() != cudaSuccess) return DFS_ERR_CUDA;
+      c->device = true;
+      (void)cp;
     } else {
-      if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return DFS_ERR_CUDA;
-      c->own_stream = true;
+      // analysis-only: NVRTC still compiles generated kernels for sm_103a
+      c->sms = 152;
+      c->jit = std::make_unique<Jit>(&c->drv, "sm_103a", "");
     }
-    if (cudaMalloc(&c->ctl, sizeof(Ctl)) != cudaSuccess) return DFS_ERR_OOM;
-    if (cudaMemset(c->ctl, 0, sizeof(Ctl)) != cudaSuccess) return DFS_ERR_CUDA;
-    if (cudaDeviceSynchronize() != cudaSuccess) return DFS_ERR_CUDA;
-    c->device = true;
-    (void)cp;
-  } else {
-    // analysis-only: NVRTC still compiles generated kernels for sm_103a
-    c->sms = 152;
-    c->jit = std::make_unique<Jit>(&c->drv, "sm_103a", "");
+    *out = c.release();
+    return DFS_OK;
+  } catch (const std::exception& e_) {
+    return internal_error(nullptr, e_.what());
+  } catch (...) {
+    return internal_error(nullptr, "unknown exception");
   }
-  *out = c.release();
-  return DFS_OK;
 }
 
 int dfs_shutdown(dfs_ctx* c) {
-  if (!c) return DFS_OK;
-  int rc = DFS_OK;
-  if (c->device) {
-    if (c->capturing) {
-      cudaGraph_t g = nullptr;
-      cudaStreamEndCapture(c->stream, &g);
-      if (g) cudaGraphDestroy(g);
-      c->capturing = false;
-      for (void* p : c->capture_deferred) cudaFreeAsync(p, c->stream);
+  try {
+    if (!c) return DFS_OK;
+    int rc = DFS_OK;
+    if (c->device) {
+      if (c->capturing) {
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(c->stream, &g);
+        if (g) cudaGraphDestroy(g);
+        c->capturing = false;
+        for (void* p : c->capture_deferred) cudaFreeAsync(p, c->stream);
+      }
+      rc = flush(c);
+      cudaStreamSynchronize(c->stream);
+      for (auto& kv : c->graphs) {
+        cudaGraphExecDestroy(kv.second.exec);
+        cudaGraphDestroy(kv.second.graph);
+        for (void* p : kv.second.owned) cudaFreeAsync(p, c->stream);
+      }
+      c->graphs.clear();
+      for (auto& kv : c->stores)
+        if (kv.second.owned && kv.second.ptr) cudaFreeAsync(kv.second.ptr, c->stream);
+      if (c->partials) cudaFreeAsync(c->partials, c->stream);
+      if (c->sval) cudaFreeAsync(c->sval, c->stream);
+      for (auto& kv : c->tables) cudaFreeAsync(kv.second.dev, c->stream);
+      c->tables.clear();
+      cudaStreamSynchronize(c->stream);
+      if (c->gather_host) cudaFreeHost(c->gather_host);
+      if (c->gather_dev) cudaFree(c->gather_dev);
+      for (auto& t : c->timed) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+      }
+      for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
+      if (c->ctl) cudaFree(c->ctl);
+      c->jit.reset();
+      if (c->own_stream) cudaStreamDestroy(c->stream);
     }
-    rc = flush(c);
-    cudaStreamSynchronize(c->stream);
-    for (auto& kv : c->graphs) {
-      cudaGraphExecDestroy(kv.second.exec);
-      cudaGraphDestroy(kv.second.graph);
-      for (void* p : kv.second.owned) cudaFreeAsync(p, c->stream);
-    }
-    c->graphs.clear();
-    for (auto& kv : c->stores)
-      if (kv.second.owned && kv.second.ptr) cudaFreeAsync(kv.second.ptr, c->stream);
-    if (c->partials) cudaFreeAsync(c->partials, c->stream);
-    if (c->sval) cudaFreeAsync(c->sval, c->stream);
-    for (auto& kv : c->tables) cudaFreeAsync(kv.second.dev, c->stream);
-    c->tables.clear();
-    cudaStreamSynchronize(c->stream);
-    if (c->gather_host) cudaFreeHost(c->gather_host);
-    if (c->gather_dev) cudaFree(c->gather_dev);
-    for (auto& t : c->timed) {
-      cudaEventDestroy(t.a);
-      cudaEventDestroy(t.b);
-    }
-    for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
-    if (c->ctl) cudaFree(c->ctl);
-    c->jit.reset();
-    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return rc;
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
   }
-  delete c;
-  return rc;
 }
 
 static int new_store(dfs_ctx* c, int32_t dtype, int32_t ndim, const int64_t* shape, dfs_store* out) {
@@ -1201,71 +1229,101 @@ static int new_store(dfs_ctx* c, int32_t dtype, int32_t ndim, const int64_t* sha
 }
 
 int dfs_store_create(dfs_ctx* c, int32_t dtype, int32_t ndim, const int64_t* shape, dfs_store* out) {
-  return new_store(c, dtype, ndim, shape, out);
+  try {
+    return new_store(c, dtype, ndim, shape, out);
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
+  }
 }
 
 int dfs_store_wrap(dfs_ctx* c, int32_t dtype, int32_t ndim, const int64_t* shape, void* dev_ptr, dfs_store* out) {
-  if (!c) return DFS_ERR_INVALID;
-  if (!dev_ptr) return fail(c, DFS_ERR_INVALID, "null device pointer");
-  int rc = new_store(c, dtype, ndim, shape, out);
-  if (rc) return rc;
-  StoreRec& r = c->stores.at(*out);
-  r.ptr = dev_ptr;
-  r.wrapped = true;
-  r.valid = true;
-  return DFS_OK;
+  try {
+    if (!c) return DFS_ERR_INVALID;
+    if (!dev_ptr) return fail(c, DFS_ERR_INVALID, "null device pointer");
+    int rc = new_store(c, dtype, ndim, shape, out);
+    if (rc) return rc;
+    StoreRec& r = c->stores.at(*out);
+    r.ptr = dev_ptr;
+    r.wrapped = true;
+    r.valid = true;
+    return DFS_OK;
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
+  }
 }
 
 int dfs_store_view(dfs_ctx* c, dfs_store parent, const int64_t* offset, const int64_t* shape, dfs_store* out) {
-  if (!c || !out) return DFS_ERR_INVALID;
-  StoreRec* p = find_store(c, parent);
-  if (!p) return fail(c, DFS_ERR_STATE, "unknown or released parent store");
-  if (p->ndim > 0 && (!offset || !shape)) return fail(c, DFS_ERR_INVALID, "view needs offset and shape");
-  StoreRec v;
-  v.handle = c->next_handle++;
-  v.dtype = p->dtype;
-  v.ndim = p->ndim;
-  v.root = p->root;
-  for (int d = 0; d < p->ndim; ++d) {
-    if (offset[d] < 0 || shape[d] < 0 || offset[d] + shape[d] > p->shape[d])
-      return fail(c, DFS_ERR_INVALID, "view box outside its parent");
-    v.shape[d] = shape[d];
-    v.off[d] = p->off[d] + offset[d];
+  try {
+    if (!c || !out) return DFS_ERR_INVALID;
+    StoreRec* p = find_store(c, parent);
+    if (!p) return fail(c, DFS_ERR_STATE, "unknown or released parent store");
+    if (p->ndim > 0 && (!offset || !shape)) return fail(c, DFS_ERR_INVALID, "view needs offset and shape");
+    StoreRec v;
+    v.handle = c->next_handle++;
+    v.dtype = p->dtype;
+    v.ndim = p->ndim;
+    v.root = p->root;
+    for (int d = 0; d < p->ndim; ++d) {
+      if (offset[d] < 0 || shape[d] < 0 || offset[d] + shape[d] > p->shape[d])
+        return fail(c, DFS_ERR_INVALID, "view box outside its parent");
+      v.shape[d] = shape[d];
+      v.off[d] = p->off[d] + offset[d];
+    }
+    StoreRec& root = c->stores.at(p->root);
+    root.app_refs += 1;
+    c->stores[v.handle] = v;
+    *out = v.handle;
+    return DFS_OK;
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
   }
-  StoreRec& root = c->stores.at(p->root);
-  root.app_refs += 1;
-  c->stores[v.handle] = v;
-  *out = v.handle;
-  return DFS_OK;
 }
 
 int dfs_store_release(dfs_ctx* c, dfs_store s) {
-  if (!c) return DFS_ERR_INVALID;
-  StoreRec* r = find_store(c, s);
-  if (!r) return fail(c, DFS_ERR_STATE, "unknown or already released store");
-  const int64_t root = r->root;
-  r->released = true;
-  StoreRec& rr = c->stores.at(root);
-  rr.app_refs -= 1;
-  if (r->handle != root) c->stores.erase(s);
-  maybe_free(c, root);
-  return DFS_OK;
+  try {
+    if (!c) return DFS_ERR_INVALID;
+    StoreRec* r = find_store(c, s);
+    if (!r) return fail(c, DFS_ERR_STATE, "unknown or already released store");
+    const int64_t root = r->root;
+    r->released = true;
+    StoreRec& rr = c->stores.at(root);
+    rr.app_refs -= 1;
+    if (r->handle != root) c->stores.erase(s);
+    maybe_free(c, root);
+    return DFS_OK;
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
+  }
 }
 
 int dfs_store_write(dfs_ctx* c, dfs_store s, const void* host_src, size_t bytes) {
-  if (!c) return DFS_ERR_INVALID;
-  StoreRec* r = find_store(c, s);
-  if (!r) return fail(c, DFS_ERR_STATE, "unknown or released store");
-  if (r->root != r->handle) return fail(c, DFS_ERR_INVALID, "write a root store, not a view");
-  if (bytes != r->nbytes) return fail(c, DFS_ERR_INVALID, "byte count does not match the store");
-  if (!c->device) return fail(c, DFS_ERR_NO_DEVICE, "analysis-only context");
-  int rc = flush(c);
-  if (rc) return rc;
-  rc = materialise(c, *r);
-  if (rc) return rc;
-  CUDA_OK(cudaMemcpyAsync(r->ptr, host_src, bytes, cudaMemcpyHostToDevice, c->stream));
-  r->valid = true;
-  return DFS_OK;
+  try {
+    if (!c) return DFS_ERR_INVALID;
+    StoreRec* r = find_store(c, s);
+    if (!r) return fail(c, DFS_ERR_STATE, "unknown or released store");
+    if (r->root != r->handle) return fail(c, DFS_ERR_INVALID, "write a root store, not a view");
+    if (bytes != r->nbytes) return fail(c, DFS_ERR_INVALID, "byte count does not match the store");
+    if (!c->device) return fail(c, DFS_ERR_NO_DEVICE, "analysis-only context");
+    int rc = flush(c);
+    if (rc) return rc;
+    rc = materialise(c, *r);
+    if (rc) return rc;
+    CUDA_OK(cudaMemcpyAsync(r->ptr, host_src, bytes, cudaMemcpyHostToDevice, c->stream));
+    r->valid = true;
+    return DFS_OK;
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
+  }
 }
 
 static int check_device_error(dfs_ctx* c) {
@@ -1280,410 +1338,524 @@ static int check_device_error(dfs_ctx* c) {
 }
 
 int dfs_store_read(dfs_ctx* c, dfs_store s, void* host_dst, size_t bytes) {
-  if (!c) return DFS_ERR_INVALID;
-  StoreRec* r = find_store(c, s);
-  if (!r) return fail(c, DFS_ERR_STATE, "unknown or released store");
-  if (!c->device) return fail(c, DFS_ERR_NO_DEVICE, "analysis-only context");
-  if (c->capturing) return fail(c, DFS_ERR_STATE, "dfs_store_read while capturing");
-  const size_t es = dtype_size(r->dtype);
-  if (bytes != (size_t)r->nelem() * es) return fail(c, DFS_ERR_INVALID, "byte count does not match the store");
-  int rc = flush(c);
-  if (rc) return rc;
-  StoreRec& root = c->stores.at(r->root);
-  if (!root.ptr) return fail(c, DFS_ERR_STATE, "store has no value");
-  if (bytes) {
-    if (r->ndim <= 1) {
-      const char* src = (const char*)root.ptr + (size_t)(r->ndim ? r->off[0] : 0) * es;
-      CUDA_OK(cudaMemcpyAsync(host_dst, src, bytes, cudaMemcpyDeviceToHost, c->stream));
-    } else if (r->ndim == 2) {
-      const char* src = (const char*)root.ptr + ((size_t)r->off[0] * root.stride[0] + (size_t)r->off[1]) * es;
-      CUDA_OK(cudaMemcpy2DAsync(host_dst, (size_t)r->shape[1] * es, src, (size_t)root.stride[0] * es,
-                                (size_t)r->shape[1] * es, (size_t)r->shape[0], cudaMemcpyDeviceToHost, c->stream));
-    } else {
-      for (int64_t i = 0; i < r->shape[0]; ++i) {
-        const char* src = (const char*)root.ptr +
-                          ((size_t)(r->off[0] + i) * root.stride[0] + (size_t)r->off[1] * root.stride[1] + (size_t)r->off[2]) * es;
-        CUDA_OK(cudaMemcpy2DAsync((char*)host_dst + (size_t)i * r->shape[1] * r->shape[2] * es, (size_t)r->shape[2] * es,
-                                  src, (size_t)root.stride[1] * es, (size_t)r->shape[2] * es, (size_t)r->shape[1],
-                                  cudaMemcpyDeviceToHost, c->stream));
+  try {
+    if (!c) return DFS_ERR_INVALID;
+    StoreRec* r = find_store(c, s);
+    if (!r) return fail(c, DFS_ERR_STATE, "unknown or released store");
+    if (!c->device) return fail(c, DFS_ERR_NO_DEVICE, "analysis-only context");
+    if (c->capturing) return fail(c, DFS_ERR_STATE, "dfs_store_read while capturing");
+    const size_t es = dtype_size(r->dtype);
+    if (bytes != (size_t)r->nelem() * es) return fail(c, DFS_ERR_INVALID, "byte count does not match the store");
+    int rc = flush(c);
+    if (rc) return rc;
+    StoreRec& root = c->stores.at(r->root);
+    if (!root.ptr) return fail(c, DFS_ERR_STATE, "store has no value");
+    if (bytes) {
+      if (r->ndim <= 1) {
+        const char* src = (const char*)root.ptr + (size_t)(r->ndim ? r->off[0] : 0) * es;
+        CUDA_OK(cudaMemcpyAsync(host_dst, src, bytes, cudaMemcpyDeviceToHost, c->stream));
+      } else if (r->ndim == 2) {
+        const char* src = (const char*)root.ptr + ((size_t)r->off[0] * root.stride[0] + (size_t)r->off[1]) * es;
+        CUDA_OK(cudaMemcpy2DAsync(host_dst, (size_t)r->shape[1] * es, src, (size_t)root.stride[0] * es,
+                                  (size_t)r->shape[1] * es, (size_t)r->shape[0], cudaMemcpyDeviceToHost, c->stream));
+      } else {
+        for (int64_t i = 0; i < r->shape[0]; ++i) {
+          const char* src = (const char*)root.ptr +
+                            ((size_t)(r->off[0] + i) * root.stride[0] + (size_t)r->off[1] * root.stride[1] + (size_t)r->off[2]) * es;
+          CUDA_OK(cudaMemcpy2DAsync((char*)host_dst + (size_t)i * r->shape[1] * r->shape[2] * es, (size_t)r->shape[2] * es,
+                                    src, (size_t)root.stride[1] * es, (size_t)r->shape[2] * es, (size_t)r->shape[1],
+                                    cudaMemcpyDeviceToHost, c->stream));
+        }
       }
     }
+    CUDA_OK(cudaStreamSynchronize(c->stream));
+    return check_device_error(c);
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
   }
-  CUDA_OK(cudaStreamSynchronize(c->stream));
-  return check_device_error(c);
 }
 
 int dfs_store_device_ptr(dfs_ctx* c, dfs_store s, void** out) {
-  if (!c || !out) return DFS_ERR_INVALID;
-  StoreRec* r = find_store(c, s);
-  if (!r) return fail(c, DFS_ERR_STATE, "unknown or released store");
-  int rc = flush(c);
-  if (rc) return rc;
-  StoreRec& root = c->stores.at(r->root);
-  rc = materialise(c, root);
-  if (rc) return rc;
-  size_t off = 0;
-  for (int d = 0; d < r->ndim; ++d) off += (size_t)r->off[d] * root.stride[d];
-  *out = (char*)root.ptr + off * dtype_size(r->dtype);
-  return DFS_OK;
+  try {
+    if (!c || !out) return DFS_ERR_INVALID;
+    StoreRec* r = find_store(c, s);
+    if (!r) return fail(c, DFS_ERR_STATE, "unknown or released store");
+    int rc = flush(c);
+    if (rc) return rc;
+    StoreRec& root = c->stores.at(r->root);
+    rc = materialise(c, root);
+    if (rc) return rc;
+    size_t off = 0;
+    for (int d = 0; d < r->ndim; ++d) off += (size_t)r->off[d] * root.stride[d];
+    *out = (char*)root.ptr + off * dtype_size(r->dtype);
+    return DFS_OK;
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
+  }
 }
 
 int dfs_partition_none(dfs_ctx* c, dfs_partition* out) {
-  if (!c || !out) return DFS_ERR_INVALID;
-  PartRec p;
-  p.kind = 0;
-  const int64_t h = c->next_handle++;
-  c->parts[h] = p;
-  *out = h;
-  return DFS_OK;
+  try {
+    if (!c || !out) return DFS_ERR_INVALID;
+    PartRec p;
+    p.kind = 0;
+    const int64_t h = c->next_handle++;
+    c->parts[h] = p;
+    *out = h;
+    return DFS_OK;
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
+  }
 }
 
 int dfs_partition_tiling(dfs_ctx* c, int32_t ndim, const int64_t* tile, const int64_t* offset, const int32_t* proj,
                          dfs_partition* out) {
-  if (!c || !out) return DFS_ERR_INVALID;
-  if (ndim < 1 || ndim > MAXD || !tile) return fail(c, DFS_ERR_INVALID, "bad tiling rank");
-  PartRec p;
-  p.kind = 1;
-  p.ndim = ndim;
-  for (int d = 0; d < ndim; ++d) {
-    if (tile[d] <= 0) return fail(c, DFS_ERR_INVALID, "tile extents must be positive");
-    p.tile[d] = tile[d];
-    p.off[d] = offset ? offset[d] : 0;
-    p.proj[d] = proj ? proj[d] : d;
-    if (p.proj[d] < 0 || p.proj[d] >= MAXD) return fail(c, DFS_ERR_INVALID, "bad projection");
+  try {
+    if (!c || !out) return DFS_ERR_INVALID;
+    if (ndim < 1 || ndim > MAXD || !tile) return fail(c, DFS_ERR_INVALID, "bad tiling rank");
+    PartRec p;
+    p.kind = 1;
+    p.ndim = ndim;
+    for (int d = 0; d < ndim; ++d) {
+      if (tile[d] <= 0) return fail(c, DFS_ERR_INVALID, "tile extents must be positive");
+      p.tile[d] = tile[d];
+      p.off[d] = offset ? offset[d] : 0;
+      p.proj[d] = proj ? proj[d] : d;
+      if (p.proj[d] < 0 || p.proj[d] >= MAXD) return fail(c, DFS_ERR_INVALID, "bad projection");
+    }
+    const int64_t h = c->next_handle++;
+    c->parts[h] = p;
+    *out = h;
+    return DFS_OK;
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
   }
-  const int64_t h = c->next_handle++;
-  c->parts[h] = p;
-  *out = h;
-  return DFS_OK;
 }
 
 int dfs_submit(dfs_ctx* c, int32_t op, int32_t ndim, const int64_t* dom, int32_t nargs, const dfs_arg* args) {
-  if (!c) return DFS_ERR_INVALID;
-  if (!arity_ok(op, nargs) || !args) return fail(c, DFS_ERR_INVALID, "unknown op or wrong argument count");
-  if (ndim < 1 || ndim > MAXD || !dom) return fail(c, DFS_ERR_INVALID, "launch domain rank must be 1..3");
-  Task t;
-  t.op = op;
-  t.dnd = ndim;
-  for (int d = 0; d < ndim; ++d) {
-    if (dom[d] < 1) return fail(c, DFS_ERR_INVALID, "launch domain extents must be >= 1");
-    t.dom[d] = dom[d];
-  }
-  t.seq = c->seq;
-  for (int i = 0; i < nargs; ++i) {
-    const dfs_arg& in = args[i];
-    Arg a;
-    if (in.privilege == DFS_PRIV_IMM) {
-      a.imm = true;
-      a.immv = in.imm;
-      a.priv = DFS_PRIV_IMM;
-      t.args.push_back(a);
-      continue;
+  try {
+    if (!c) return DFS_ERR_INVALID;
+    if (!arity_ok(op, nargs) || !args) return fail(c, DFS_ERR_INVALID, "unknown op or wrong argument count");
+    if (ndim < 1 || ndim > MAXD || !dom) return fail(c, DFS_ERR_INVALID, "launch domain rank must be 1..3");
+    Task t;
+    t.op = op;
+    t.dnd = ndim;
+    for (int d = 0; d < ndim; ++d) {
+      if (dom[d] < 1) return fail(c, DFS_ERR_INVALID, "launch domain extents must be >= 1");
+      t.dom[d] = dom[d];
     }
-    if (in.privilege != DFS_PRIV_R && in.privilege != DFS_PRIV_W && in.privilege != DFS_PRIV_RW &&
-        in.privilege != DFS_PRIV_RD)
-      return fail(c, DFS_ERR_INVALID, "bad privilege");
-    if (in.privilege == DFS_PRIV_RD && in.redop != DFS_REDOP_SUM) return fail(c, DFS_ERR_INVALID, "RD needs a reduction operator");
-    StoreRec* s = find_store(c, in.store);
-    if (!s) return fail(c, DFS_ERR_STATE, "task names an unknown or released store");
-    auto pit = c->parts.find(in.partition);
-    if (pit == c->parts.end()) return fail(c, DFS_ERR_STATE, "task names an unknown partition");
-    const PartRec& P = pit->second;
-    a.store = in.store;
-    a.root = s->root;
-    a.priv = in.privilege;
-    a.redop = in.redop;
-    a.dtype = s->dtype;
-    a.nd = s->ndim;
-    a.part.kind = P.kind;
-    a.part.nd = s->ndim;
-    if (P.kind == 1 && P.ndim != s->ndim) return fail(c, DFS_ERR_INVALID, "tiling rank differs from the store's");
-    for (int d = 0; d < s->ndim; ++d) {
-      a.part.vlo[d] = s->off[d];
-      a.part.vhi[d] = s->off[d] + s->shape[d];
-      if (P.kind == 1) {
-        a.part.tile[d] = P.tile[d];
-        a.part.off[d] = s->off[d] + P.off[d];
-        a.part.proj[d] = P.proj[d];
+    t.seq = c->seq;
+    for (int i = 0; i < nargs; ++i) {
+      const dfs_arg& in = args[i];
+      Arg a;
+      if (in.privilege == DFS_PRIV_IMM) {
+        a.imm = true;
+        a.immv = in.imm;
+        a.priv = DFS_PRIV_IMM;
+        t.args.push_back(a);
+        continue;
       }
+      if (in.privilege != DFS_PRIV_R && in.privilege != DFS_PRIV_W && in.privilege != DFS_PRIV_RW &&
+          in.privilege != DFS_PRIV_RD)
+        return fail(c, DFS_ERR_INVALID, "bad privilege");
+      if (in.privilege == DFS_PRIV_RD && in.redop != DFS_REDOP_SUM) return fail(c, DFS_ERR_INVALID, "RD needs a reduction operator");
+      StoreRec* s = find_store(c, in.store);
+      if (!s) return fail(c, DFS_ERR_STATE, "task names an unknown or released store");
+      auto pit = c->parts.find(in.partition);
+      if (pit == c->parts.end()) return fail(c, DFS_ERR_STATE, "task names an unknown partition");
+      const PartRec& P = pit->second;
+      a.store = in.store;
+      a.root = s->root;
+      a.priv = in.privilege;
+      a.redop = in.redop;
+      a.dtype = s->dtype;
+      a.nd = s->ndim;
+      a.part.kind = P.kind;
+      a.part.nd = s->ndim;
+      if (P.kind == 1 && P.ndim != s->ndim) return fail(c, DFS_ERR_INVALID, "tiling rank differs from the store's");
+      for (int d = 0; d < s->ndim; ++d) {
+        a.part.vlo[d] = s->off[d];
+        a.part.vhi[d] = s->off[d] + s->shape[d];
+        if (P.kind == 1) {
+          a.part.tile[d] = P.tile[d];
+          a.part.off[d] = s->off[d] + P.off[d];
+          a.part.proj[d] = P.proj[d];
+        }
+      }
+      t.args.push_back(a);
     }
-    t.args.push_back(a);
+    int rc = validate(c, t);
+    if (rc) return rc;
+    for (const Arg& a : t.args)
+      if (!a.imm) c->stores.at(a.root).pending += 1;
+    c->window.push_back(std::move(t));
+    c->seq += 1;
+    c->st.tasks += 1;
+    if ((int)c->window.size() >= c->cfg.window_size && !c->batching) return flush(c);
+    return DFS_OK;
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
   }
-  int rc = validate(c, t);
-  if (rc) return rc;
-  for (const Arg& a : t.args)
-    if (!a.imm) c->stores.at(a.root).pending += 1;
-  c->window.push_back(std::move(t));
-  c->seq += 1;
-  c->st.tasks += 1;
-  if ((int)c->window.size() >= c->cfg.window_size && !c->batching) return flush(c);
-  return DFS_OK;
 }
 
 int dfs_flush(dfs_ctx* c) {
-  if (!c) return DFS_ERR_INVALID;
-  return flush(c);
+  try {
+    if (!c) return DFS_ERR_INVALID;
+    return flush(c);
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
+  }
 }
 
 int dfs_sync(dfs_ctx* c) {
-  if (!c) return DFS_ERR_INVALID;
-  if (!c->device) return DFS_OK;
-  if (c->capturing) return fail(c, DFS_ERR_STATE, "dfs_sync while capturing");
-  int rc = flush(c);
-  if (rc) return rc;
-  CUDA_OK(cudaStreamSynchronize(c->stream));
-  for (auto& t : c->timed) {
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
-      auto& kt = c->ktime[t.name];
-      kt.first += ms;
-      kt.second += 1;
+  try {
+    if (!c) return DFS_ERR_INVALID;
+    if (!c->device) return DFS_OK;
+    if (c->capturing) return fail(c, DFS_ERR_STATE, "dfs_sync while capturing");
+    int rc = flush(c);
+    if (rc) return rc;
+    CUDA_OK(cudaStreamSynchronize(c->stream));
+    for (auto& t : c->timed) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+        auto& kt = c->ktime[t.name];
+        kt.first += ms;
+        kt.second += 1;
+      }
+      c->event_pool.push_back(t.a);
+      c->event_pool.push_back(t.b);
     }
-    c->event_pool.push_back(t.a);
-    c->event_pool.push_back(t.b);
+    c->timed.clear();
+    return check_device_error(c);
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
   }
-  c->timed.clear();
-  return check_device_error(c);
 }
 
 int dfs_capture_begin(dfs_ctx* c) {
-  if (!c) return DFS_ERR_INVALID;
-  if (!c->device) return fail(c, DFS_ERR_NO_DEVICE, "analysis-only context");
-  if (c->capturing) return fail(c, DFS_ERR_STATE, "already capturing");
-  int rc = flush(c);
-  if (rc) return rc;
-  c->lastb.ok = false;
-  // reduction scratch cannot be reallocated inside a capture: reserve 1 MB
-  const size_t want = 1 << 20;
-  if (c->partials_cap < want) {
-    if (c->partials) cudaFreeAsync(c->partials, c->stream);
-    c->partials = nullptr;
-    CUDA_OK(cudaMallocAsync(&c->partials, want, c->stream));
-    c->partials_cap = want;
+  try {
+    if (!c) return DFS_ERR_INVALID;
+    if (!c->device) return fail(c, DFS_ERR_NO_DEVICE, "analysis-only context");
+    if (c->capturing) return fail(c, DFS_ERR_STATE, "already capturing");
+    int rc = flush(c);
+    if (rc) return rc;
+    c->lastb.ok = false;
+    // reduction scratch cannot be reallocated inside a capture: reserve 1 MB
+    const size_t want = 1 << 20;
+    if (c->partials_cap < want) {
+      if (c->partials) cudaFreeAsync(c->partials, c->stream);
+      c->partials = nullptr;
+      CUDA_OK(cudaMallocAsync(&c->partials, want, c->stream));
+      c->partials_cap = want;
+    }
+    CUDA_OK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    c->capturing = true;
+    c->captured_allocs.clear();
+    c->capture_deferred.clear();
+    c->capture_launches = 0;
+    return DFS_OK;
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
   }
-  CUDA_OK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-  c->capturing = true;
-  c->captured_allocs.clear();
-  c->capture_deferred.clear();
-  c->capture_launches = 0;
-  return DFS_OK;
 }
 
 int dfs_capture_end(dfs_ctx* c, dfs_graph* out) {
-  if (!c || !out) return DFS_ERR_INVALID;
-  if (!c->capturing) return fail(c, DFS_ERR_STATE, "not capturing");
-  int rc = flush(c);
-  cudaGraph_t graph = nullptr;
-  const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
-  c->capturing = false;
-  std::vector<void*> deferred;
-  deferred.swap(c->capture_deferred);
-  auto give_back = [&]() {
-    for (void* p : deferred) cudaFreeAsync(p, c->stream);
-    // addresses handed out inside an abandoned capture belong to no live
-    // allocation: those stores lose their memory (and value)
-    for (int64_t r : c->captured_allocs) {
-      auto it = c->stores.find(r);
-      if (it == c->stores.end()) continue;
-      it->second.ptr = nullptr;
-      it->second.owned = false;
-      it->second.valid = false;
+  try {
+    if (!c || !out) return DFS_ERR_INVALID;
+    if (!c->capturing) return fail(c, DFS_ERR_STATE, "not capturing");
+    int rc = flush(c);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    c->capturing = false;
+    std::vector<void*> deferred;
+    deferred.swap(c->capture_deferred);
+    auto give_back = [&]() {
+      for (void* p : deferred) cudaFreeAsync(p, c->stream);
+      // addresses handed out inside an abandoned capture belong to no live
+      // allocation: those stores lose their memory (and value)
+      for (int64_t r : c->captured_allocs) {
+        auto it = c->stores.find(r);
+        if (it == c->stores.end()) continue;
+        it->second.ptr = nullptr;
+        it->second.owned = false;
+        it->second.valid = false;
+      }
+      c->captured_allocs.clear();
+    };
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      give_back();
+      return rc;
     }
-    c->captured_allocs.clear();
-  };
-  if (rc) {
-    if (graph) cudaGraphDestroy(graph);
-    give_back();
-    return rc;
+    if (e != cudaSuccess || !graph) {
+      give_back();
+      return fail(c, DFS_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+    }
+    if (!c->captured_allocs.empty()) {
+      cudaGraphDestroy(graph);
+      give_back();
+      return fail(c, DFS_ERR_STATE, "a store created inside the captured region is still referenced");
+    }
+    dfs_ctx::GraphRec g;
+    g.graph = graph;
+    const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+    if (ie != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      give_back();
+      return fail(c, DFS_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+    }
+    g.owned.swap(deferred);
+    g.launches = c->capture_launches;
+    const int64_t h = c->next_handle++;
+    c->graphs[h] = std::move(g);
+    *out = h;
+    return DFS_OK;
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
   }
-  if (e != cudaSuccess || !graph) {
-    give_back();
-    return fail(c, DFS_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
-  }
-  if (!c->captured_allocs.empty()) {
-    cudaGraphDestroy(graph);
-    give_back();
-    return fail(c, DFS_ERR_STATE, "a store created inside the captured region is still referenced");
-  }
-  dfs_ctx::GraphRec g;
-  g.graph = graph;
-  const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
-  if (ie != cudaSuccess) {
-    cudaGraphDestroy(graph);
-    give_back();
-    return fail(c, DFS_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
-  }
-  g.owned.swap(deferred);
-  g.launches = c->capture_launches;
-  const int64_t h = c->next_handle++;
-  c->graphs[h] = std::move(g);
-  *out = h;
-  return DFS_OK;
 }
 
 int dfs_graph_launch(dfs_ctx* c, dfs_graph h) {
-  if (!c) return DFS_ERR_INVALID;
-  auto it = c->graphs.find(h);
-  if (it == c->graphs.end()) return fail(c, DFS_ERR_STATE, "unknown graph");
-  if (c->capturing) return fail(c, DFS_ERR_STATE, "cannot launch a graph while capturing");
-  int rc = flush(c);
-  if (rc) return rc;
-  c->lastb.ok = false;
-  CUDA_OK(cudaGraphLaunch(it->second.exec, c->stream));
-  c->st.launches += it->second.launches;
-  return DFS_OK;
+  try {
+    if (!c) return DFS_ERR_INVALID;
+    auto it = c->graphs.find(h);
+    if (it == c->graphs.end()) return fail(c, DFS_ERR_STATE, "unknown graph");
+    if (c->capturing) return fail(c, DFS_ERR_STATE, "cannot launch a graph while capturing");
+    int rc = flush(c);
+    if (rc) return rc;
+    c->lastb.ok = false;
+    CUDA_OK(cudaGraphLaunch(it->second.exec, c->stream));
+    c->st.launches += it->second.launches;
+    return DFS_OK;
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
+  }
 }
 
 int dfs_graph_destroy(dfs_ctx* c, dfs_graph h) {
-  if (!c) return DFS_ERR_INVALID;
-  auto it = c->graphs.find(h);
-  if (it == c->graphs.end()) return fail(c, DFS_ERR_STATE, "unknown graph");
-  cudaGraphExecDestroy(it->second.exec);
-  cudaGraphDestroy(it->second.graph);
-  for (void* p : it->second.owned) cudaFreeAsync(p, c->stream);
-  c->graphs.erase(it);
-  return DFS_OK;
+  try {
+    if (!c) return DFS_ERR_INVALID;
+    auto it = c->graphs.find(h);
+    if (it == c->graphs.end()) return fail(c, DFS_ERR_STATE, "unknown graph");
+    cudaGraphExecDestroy(it->second.exec);
+    cudaGraphDestroy(it->second.graph);
+    for (void* p : it->second.owned) cudaFreeAsync(p, c->stream);
+    c->graphs.erase(it);
+    return DFS_OK;
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
+  }
 }
 
 int dfs_batch_begin(dfs_ctx* c) {
-  if (!c) return DFS_ERR_INVALID;
-  if (c->batching) return fail(c, DFS_ERR_STATE, "already batching");
-  const int rc = flush(c);
-  if (rc) return rc;
-  c->batching = true;
-  c->batch_marks.clear();
-  return DFS_OK;
+  try {
+    if (!c) return DFS_ERR_INVALID;
+    if (c->batching) return fail(c, DFS_ERR_STATE, "already batching");
+    const int rc = flush(c);
+    if (rc) return rc;
+    c->batching = true;
+    c->batch_marks.clear();
+    return DFS_OK;
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
+  }
 }
 
 int dfs_batch_next(dfs_ctx* c) {
-  if (!c) return DFS_ERR_INVALID;
-  if (!c->batching) return fail(c, DFS_ERR_STATE, "dfs_batch_next outside a batch");
-  c->batch_marks.push_back(c->window.size());
-  return DFS_OK;
+  try {
+    if (!c) return DFS_ERR_INVALID;
+    if (!c->batching) return fail(c, DFS_ERR_STATE, "dfs_batch_next outside a batch");
+    c->batch_marks.push_back(c->window.size());
+    return DFS_OK;
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
+  }
 }
 
 int dfs_batch_end(dfs_ctx* c) {
-  if (!c) return DFS_ERR_INVALID;
-  if (!c->batching) return fail(c, DFS_ERR_STATE, "dfs_batch_end outside a batch");
-  c->batching = false;
-  const int rc = flush_batch(c);
-  c->batch_marks.clear();
-  return rc;
+  try {
+    if (!c) return DFS_ERR_INVALID;
+    if (!c->batching) return fail(c, DFS_ERR_STATE, "dfs_batch_end outside a batch");
+    c->batching = false;
+    const int rc = flush_batch(c);
+    c->batch_marks.clear();
+    return rc;
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
+  }
 }
 
 int dfs_batch_repeat(dfs_ctx* c, int32_t n) {
-  if (!c) return DFS_ERR_INVALID;
-  if (n < 0) return fail(c, DFS_ERR_INVALID, "negative repeat count");
-  if (c->batching) return fail(c, DFS_ERR_STATE, "dfs_batch_repeat inside a batch");
-  if (!c->device) return fail(c, DFS_ERR_NO_DEVICE, "analysis-only context");
-  const int rc = flush(c);
-  if (rc) return rc;
-  if (!c->lastb.ok) return fail(c, DFS_ERR_STATE, "no steady batch to repeat");
-  for (int32_t i = 0; i < n; ++i) {
-    const int lrc = launch_batched(c, c->lastb);
-    if (lrc) {
-      c->lastb.ok = false;
-      return lrc;
+  try {
+    if (!c) return DFS_ERR_INVALID;
+    if (n < 0) return fail(c, DFS_ERR_INVALID, "negative repeat count");
+    if (c->batching) return fail(c, DFS_ERR_STATE, "dfs_batch_repeat inside a batch");
+    if (!c->device) return fail(c, DFS_ERR_NO_DEVICE, "analysis-only context");
+    const int rc = flush(c);
+    if (rc) return rc;
+    if (!c->lastb.ok) return fail(c, DFS_ERR_STATE, "no steady batch to repeat");
+    for (int32_t i = 0; i < n; ++i) {
+      const int lrc = launch_batched(c, c->lastb);
+      if (lrc) {
+        c->lastb.ok = false;
+        return lrc;
+      }
+      c->batches += 1;
+      c->batch_repeats += 1;
+      c->batched_instances += c->lastb.ninst;
     }
-    c->batches += 1;
-    c->batch_repeats += 1;
-    c->batched_instances += c->lastb.ninst;
+    return DFS_OK;
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
   }
-  return DFS_OK;
 }
 
 int dfs_read_scalars(dfs_ctx* c, int32_t n, const dfs_store* hs, double* out) {
-  if (!c) return DFS_ERR_INVALID;
-  if (n < 0 || (n > 0 && (!hs || !out))) return fail(c, DFS_ERR_INVALID, "bad arguments");
-  if (!c->device) return fail(c, DFS_ERR_NO_DEVICE, "analysis-only context");
-  if (c->capturing) return fail(c, DFS_ERR_STATE, "dfs_read_scalars while capturing");
-  for (int32_t i = 0; i < n; ++i) {
-    StoreRec* r = find_store(c, hs[i]);
-    if (!r) return fail(c, DFS_ERR_STATE, "unknown or released store");
-    if (r->ndim != 0) return fail(c, DFS_ERR_INVALID, "dfs_read_scalars takes 0-d stores");
-  }
-  int rc = flush(c);
-  if (rc) return rc;
-  if (n == 0) {
+  try {
+    if (!c) return DFS_ERR_INVALID;
+    if (n < 0 || (n > 0 && (!hs || !out))) return fail(c, DFS_ERR_INVALID, "bad arguments");
+    if (!c->device) return fail(c, DFS_ERR_NO_DEVICE, "analysis-only context");
+    if (c->capturing) return fail(c, DFS_ERR_STATE, "dfs_read_scalars while capturing");
+    for (int32_t i = 0; i < n; ++i) {
+      StoreRec* r = find_store(c, hs[i]);
+      if (!r) return fail(c, DFS_ERR_STATE, "unknown or released store");
+      if (r->ndim != 0) return fail(c, DFS_ERR_INVALID, "dfs_read_scalars takes 0-d stores");
+    }
+    int rc = flush(c);
+    if (rc) return rc;
+    if (n == 0) {
+      CUDA_OK(cudaStreamSynchronize(c->stream));
+      return check_device_error(c);
+    }
+    if ((size_t)n > c->gather_cap) {
+      CUDA_OK(cudaStreamSynchronize(c->stream));
+      if (c->gather_host) cudaFreeHost(c->gather_host);
+      if (c->gather_dev) cudaFree(c->gather_dev);
+      c->gather_host = nullptr;
+      c->gather_dev = nullptr;
+      c->gather_cap = 0;
+      const size_t cap = std::max<size_t>(1024, (size_t)n);
+      // per scalar: descriptor (address, dtype) then the gathered double
+      CUDA_OK(cudaMallocHost((void**)&c->gather_host, cap * 3 * sizeof(int64_t)));
+      CUDA_OK(cudaMalloc(&c->gather_dev, cap * 3 * sizeof(int64_t)));
+      c->gather_cap = cap;
+    }
+    for (int32_t i = 0; i < n; ++i) {
+      const StoreRec& r = *find_store(c, hs[i]);
+      const StoreRec& root = c->stores.at(r.root);
+      if (!root.ptr || !root.valid) return fail(c, DFS_ERR_STATE, "store has no value");
+      const char* p = (const char*)root.ptr;
+      for (int d = 0; d < root.ndim; ++d) p += (size_t)r.off[d] * root.stride[d] * dtype_size(r.dtype);
+      c->gather_host[2 * i] = (int64_t)(uintptr_t)p;
+      c->gather_host[2 * i + 1] = r.dtype;
+    }
+    int64_t* desc = static_cast<int64_t*>(c->gather_dev);
+    double* vals = reinterpret_cast<double*>(desc + 2 * c->gather_cap);
+    CUDA_OK(cudaMemcpyAsync(desc, c->gather_host, (size_t)n * 2 * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+    CUDA_OK(launch_gather_scalars(desc, n, vals, c->stream));
+    double* hv = reinterpret_cast<double*>(c->gather_host + 2 * c->gather_cap);
+    CUDA_OK(cudaMemcpyAsync(hv, vals, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CUDA_OK(cudaStreamSynchronize(c->stream));
+    std::memcpy(out, hv, (size_t)n * sizeof(double));
     return check_device_error(c);
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
   }
-  if ((size_t)n > c->gather_cap) {
-    CUDA_OK(cudaStreamSynchronize(c->stream));
-    if (c->gather_host) cudaFreeHost(c->gather_host);
-    if (c->gather_dev) cudaFree(c->gather_dev);
-    c->gather_host = nullptr;
-    c->gather_dev = nullptr;
-    c->gather_cap = 0;
-    const size_t cap = std::max<size_t>(1024, (size_t)n);
-    // per scalar: descriptor (address, dtype) then the gathered double
-    CUDA_OK(cudaMallocHost((void**)&c->gather_host, cap * 3 * sizeof(int64_t)));
-    CUDA_OK(cudaMalloc(&c->gather_dev, cap * 3 * sizeof(int64_t)));
-    c->gather_cap = cap;
-  }
-  for (int32_t i = 0; i < n; ++i) {
-    const StoreRec& r = *find_store(c, hs[i]);
-    const StoreRec& root = c->stores.at(r.root);
-    if (!root.ptr || !root.valid) return fail(c, DFS_ERR_STATE, "store has no value");
-    const char* p = (const char*)root.ptr;
-    for (int d = 0; d < root.ndim; ++d) p += (size_t)r.off[d] * root.stride[d] * dtype_size(r.dtype);
-    c->gather_host[2 * i] = (int64_t)(uintptr_t)p;
-    c->gather_host[2 * i + 1] = r.dtype;
-  }
-  int64_t* desc = static_cast<int64_t*>(c->gather_dev);
-  double* vals = reinterpret_cast<double*>(desc + 2 * c->gather_cap);
-  CUDA_OK(cudaMemcpyAsync(desc, c->gather_host, (size_t)n * 2 * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
-  CUDA_OK(launch_gather_scalars(desc, n, vals, c->stream));
-  double* hv = reinterpret_cast<double*>(c->gather_host + 2 * c->gather_cap);
-  CUDA_OK(cudaMemcpyAsync(hv, vals, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  CUDA_OK(cudaStreamSynchronize(c->stream));
-  std::memcpy(out, hv, (size_t)n * sizeof(double));
-  return check_device_error(c);
 }
 
 const char* dfs_last_error(dfs_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
 int dfs_plan_json(dfs_ctx* c, char* buf, size_t len, size_t* needed) {
-  if (!c) return DFS_ERR_INVALID;
-  WindowInfo wi = window_info(c);
-  Plan p = analyse(c->window, wi.roots, c->cfg.fusion != 0, c->cfg.launch_mode);
-  std::string s = plan_json(p, c->window, wi);
-  s.insert(s.size() - 1, ", \"key\": \"" + std::to_string(std::hash<std::string>{}(wi.key)) + "\"");
-  return write_json(s, buf, len, needed);
+  try {
+    if (!c) return DFS_ERR_INVALID;
+    WindowInfo wi = window_info(c);
+    Plan p = analyse(c->window, wi.roots, c->cfg.fusion != 0, c->cfg.launch_mode);
+    std::string s = plan_json(p, c->window, wi);
+    s.insert(s.size() - 1, ", \"key\": \"" + std::to_string(std::hash<std::string>{}(wi.key)) + "\"");
+    return write_json(s, buf, len, needed);
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
+  }
 }
 
 int dfs_stats_json(dfs_ctx* c, char* buf, size_t len, size_t* needed) {
-  if (!c) return DFS_ERR_INVALID;
-  std::ostringstream o;
-  const Stats& s = c->st;
-  o << "{\"tasks\": " << s.tasks << ", \"groups\": " << s.groups << ", \"launches\": " << s.launches
-    << ", \"barriers\": " << s.barriers << ", \"flushes\": " << s.flushes << ", \"plan_hits\": " << s.plan_hits
-    << ", \"plan_misses\": " << s.plan_misses << ", \"temporaries\": " << s.temporaries
-    << ", \"bytes_allocated\": " << s.bytes_allocated << ", \"allocations\": " << s.allocations
-    << ", \"analysis_s\": " << s.analysis_s;
-  if (c->jit)
-    o << ", \"compile_s\": " << c->jit->compile_seconds() << ", \"kernels_compiled\": " << c->jit->compiles()
-      << ", \"kernel_cache_hits\": " << c->jit->hits() << ", \"kernel_disk_hits\": " << c->jit->disk_hits();
-  o << ", \"last_regs\": " << s.last_regs << ", \"last_occupancy\": " << s.last_occupancy
-    << ", \"last_grid\": " << s.last_grid << ", \"last_block\": " << s.last_block;
-  o << ", \"kernel_times\": {";
-  bool first = true;
-  for (const auto& kv : c->ktime) {
-    o << (first ? "" : ", ") << "\"" << kv.first << "\": {\"ms\": " << kv.second.first
-      << ", \"launches\": " << kv.second.second << "}";
-    first = false;
+  try {
+    if (!c) return DFS_ERR_INVALID;
+    std::ostringstream o;
+    const Stats& s = c->st;
+    o << "{\"tasks\": " << s.tasks << ", \"groups\": " << s.groups << ", \"launches\": " << s.launches
+      << ", \"barriers\": " << s.barriers << ", \"flushes\": " << s.flushes << ", \"plan_hits\": " << s.plan_hits
+      << ", \"plan_misses\": " << s.plan_misses << ", \"temporaries\": " << s.temporaries
+      << ", \"bytes_allocated\": " << s.bytes_allocated << ", \"allocations\": " << s.allocations
+      << ", \"analysis_s\": " << s.analysis_s;
+    if (c->jit)
+      o << ", \"compile_s\": " << c->jit->compile_seconds() << ", \"kernels_compiled\": " << c->jit->compiles()
+        << ", \"kernel_cache_hits\": " << c->jit->hits() << ", \"kernel_disk_hits\": " << c->jit->disk_hits();
+    o << ", \"last_regs\": " << s.last_regs << ", \"last_occupancy\": " << s.last_occupancy
+      << ", \"last_grid\": " << s.last_grid << ", \"last_block\": " << s.last_block;
+    o << ", \"kernel_times\": {";
+    bool first = true;
+    for (const auto& kv : c->ktime) {
+      o << (first ? "" : ", ") << "\"" << kv.first << "\": {\"ms\": " << kv.second.first
+        << ", \"launches\": " << kv.second.second << "}";
+      first = false;
+    }
+    o << "}";
+    o << ", \"batches\": " << c->batches << ", \"batched_instances\": " << c->batched_instances
+      << ", \"batch_repeats\": " << c->batch_repeats << ", \"batch_fallbacks\": " << c->batch_fallbacks << ", \"batch_fallback_reason\": \"" << c->batch_fallback_reason
+      << "\"";
+    o << ", \"sms\": " << c->sms << "}";
+    return write_json(o.str(), buf, len, needed);
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
   }
-  o << "}";
-  o << ", \"batches\": " << c->batches << ", \"batched_instances\": " << c->batched_instances
-    << ", \"batch_repeats\": " << c->batch_repeats << ", \"batch_fallbacks\": " << c->batch_fallbacks << ", \"batch_fallback_reason\": \"" << c->batch_fallback_reason
-    << "\"";
-  o << ", \"sms\": " << c->sms << "}";
-  return write_json(o.str(), buf, len, needed);
 }
 
 int dfs_last_kernel_source(dfs_ctx* c, char* buf, size_t len, size_t* needed) {
-  if (!c) return DFS_ERR_INVALID;
-  return write_json(c->last_source, buf, len, needed);
+  try {
+    if (!c) return DFS_ERR_INVALID;
+    return write_json(c->last_source, buf, len, needed);
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
+  }
 }
 
 }  // extern "C"

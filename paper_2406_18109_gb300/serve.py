@@ -203,9 +203,7 @@ class Server:
             xs = rt.array(np.ascontiguousarray(payloads(req), dtype=np.float64))
             items.append((req, Am, xs))
         sols = []
-        batched = len(items) > 1
-        if batched:
-            rt.batch_begin()
+        rt.batch_begin()
         for req, Am, xs in items:
             b = Am @ xs
             st = W.cg_start_inplace(b) if kind == "cg" else W.bicgstab_start_inplace(b)
@@ -214,12 +212,8 @@ class Server:
             res = Result(req["rid"], kind, req["size"], req["arrival"], admitted=now)
             sols.append(_Solve(req, res, req["size"], Am, st, bb,
                                nbytes=request_bytes(kind, req["size"])))
-            if batched:
-                rt.batch_next()
-        if batched:
-            rt.batch_end()
-        else:
-            rt.flush()
+            rt.batch_next()
+        rt.batch_end()
         del items                       # x* of every new solve
         return sols
 
@@ -227,12 +221,6 @@ class Server:
         """iters_per_tick iterations of every solve of one kind."""
         rt = self.rt
         step = W.cg_iteration_inplace if kind == "cg" else W.bicgstab_iteration_inplace
-        if len(sols) == 1:
-            s = sols[0]
-            for _ in range(self.C):
-                step(s.Am, s.st)
-                rt.flush()
-            return
         done = 0
         while done < self.C:
             rt.batch_begin()
@@ -257,15 +245,11 @@ class Server:
             S, K, T = payloads(req)
             data.append((req, rt.array(S), rt.array(K), rt.array(T)))
         outs = []
-        batched = len(data) > 1
-        if batched:
-            rt.batch_begin()
+        rt.batch_begin()
         for req, S, K, T in data:
             outs.append(W.black_scholes(S, K, T, self.bs_rate, self.bs_sigma))
-            if batched:
-                rt.batch_next()
-        if batched:
-            rt.batch_end()
+            rt.batch_next()
+        rt.batch_end()
         results = []
         for (req, *_), (call, put) in zip(data, outs):
             c, p = call.numpy(), put.numpy()
@@ -393,29 +377,3 @@ def summarize(results, wall_s: float) -> dict:
     out["unconverged"] = sum(1 for r in results if not r.converged)
     return out
 
-
-class Prefetch:
-    """Produces request payloads ahead of the loop on a background thread (the
-    generators release the GIL), in arrival order, at most `depth` ahead.
-    Use the instance as the `payloads` argument of Server.run."""
-
-    def __init__(self, payload_fn, requests, depth: int = 8):
-        import queue
-        import threading
-        self.fn = payload_fn
-        self.order = [r["rid"] for r in requests]
-        self.q: "queue.Queue" = queue.Queue(maxsize=depth)
-        self.ready: dict = {}
-        self.thread = threading.Thread(target=self._work, args=(list(requests),), daemon=True)
-        self.thread.start()
-
-    def _work(self, requests):
-        for r in requests:
-            self.q.put((r["rid"], self.fn(r)))
-
-    def __call__(self, req):
-        rid = req["rid"]
-        while rid not in self.ready:
-            k, v = self.q.get()
-            self.ready[k] = v
-        return self.ready.pop(rid)

@@ -124,3 +124,27 @@ def test_batched_black_scholes_instances_equal_alone():
             c1, p1 = W.black_scholes(rt.array(S), rt.array(K), rt.array(T), prm["r"], prm["sigma"])
             assert np.array_equal(c.view(np.uint32), c1.numpy().view(np.uint32))
             assert np.array_equal(p.view(np.uint32), p1.numpy().view(np.uint32))
+
+
+def test_cached_batch_kernel_serves_new_stores():
+    """A second batch of the same structure over other stores reuses the
+    memoised kernel with its own pointers."""
+    prm = inputs.bs_params()
+    with gpu_runtime("persistent", tile=256) as rt:
+        for rnd in range(3):
+            sizes = [1000 + 7 * rnd, 3001, 555 + rnd]
+            data = [inputs.bs_inputs(n, seed=40 + 3 * rnd + i) for i, n in enumerate(sizes)]
+            arrs = [[rt.array(v) for v in d] for d in data]
+            rt.batch_begin()
+            outs = []
+            for S, K, T in arrs:
+                outs.append(W.black_scholes(S, K, T, prm["r"], prm["sigma"]))
+                rt.batch_next()
+            rt.batch_end()
+            st = rt.stats()
+            assert st["batches"] == rnd + 1 and st["batch_fallbacks"] == 0
+            for (S, K, T), (c, p) in zip(data, outs):
+                co, po = programs.black_scholes(S, K, T, prm["r"], prm["sigma"], np.float32)
+                tol = 1e-5 * (S.astype(np.float64) + K)
+                assert np.all(np.abs(c.numpy() - co) <= tol) and np.all(np.abs(p.numpy() - po) <= tol)
+            del arrs, outs

@@ -68,3 +68,22 @@ def test_bicgstab_converges_to_manufactured_solution():
                 break
         x = s.x.numpy()
     assert np.linalg.norm(x - xs) / np.linalg.norm(xs) < 1e-8
+
+
+def test_inplace_iteration_matches_oracle():
+    """The in-place form (state stores updated in place, used by batching and
+    serving) before convergence: 1e-10 norm-wise, as the naturally written one."""
+    m, iters = 13, 15
+    rp, col, val = inputs.poisson3d_csr(m)
+    xs = inputs.uniform(9, -1, 1, m ** 3)
+    with gpu_runtime("persistent", tile=512) as rt:
+        Am = A.CSR(rt, rp, col, val)
+        s = W.bicgstab_start_inplace(Am @ rt.array(xs))
+        for _ in range(iters):
+            W.bicgstab_iteration_inplace(Am, s)
+            rt.flush()
+        x, rr = s.x.numpy(), float(s.rr.numpy())
+    b = programs.spmv(rp, col, val, xs)
+    xo, it, rel = programs.bicgstab(rp, col, val, b, 0.0, iters)
+    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-10
+    assert abs(np.sqrt(rr) / np.linalg.norm(b) - rel) <= 1e-8 * rel + 1e-14
