@@ -224,8 +224,10 @@ def kernel_delta(before: dict, after: dict) -> dict:
 class Arm:
     """One timed configuration of a workload: build state, warm up, time K steps."""
 
-    def __init__(self, workload, rt_kwargs, torch, stream, e2e=False, graph=False, per_solve=False):
+    def __init__(self, workload, rt_kwargs, torch, stream, e2e=False, graph=False, per_solve=False,
+                 autotune=False):
         self.per_solve = per_solve
+        self.tuned = None
         from paper_2406_18109_gb300 import arrays as A
         from paper_2406_18109_gb300 import dist as D
         from paper_2406_18109_gb300 import workloads as W
@@ -309,6 +311,17 @@ class Arm:
                         W.cg_reset_inplace(s, b)
                         rt.batch_next()
                     rt.batch_end()
+            if autotune:
+                # tile and launch shape of the batched iteration, by timing it
+                # (coordinate descent; the choice is cached per GPU and dtype)
+                import tempfile
+                from paper_2406_18109_gb300 import autotune as AT
+                space = {"tile": [256, 512], "block": [128, 256, 512], "unroll": [1, 2, 4], "ctas_per_sm": [0, 2, 3]}
+                best, trials = AT.tune(rt, one_iteration, space=space, warmup=1, reps=3,
+                                       key=f"batched-cg-{cfg['count']}-{cfg['seed']}-{cfg['dtype']}",
+                                       cache_path=os.path.join(tempfile.gettempdir(), "dfs_autotune.json"),
+                                       gpu=torch.cuda.get_device_name())
+                self.tuned = {"config": best, "trials": [{"config": c, "ms_per_iteration": m} for c, m in trials]}
             # one normal pass of each window (compiles kernels, uploads descriptors), then capture
             reset()
             one_iteration()
@@ -562,6 +575,7 @@ def main():
     ap.add_argument("--sweeps", type=int, default=0, help="Jacobi sweeps per step (profiling)")
     for k in ("block", "unroll", "tile", "rows"):
         ap.add_argument(f"--{k}", type=int, default=0, help=f"override the workload's {k} (tuning)")
+    ap.add_argument("--no-autotune", action="store_true", help="batched CG: keep the configured tile/launch shape")
     ap.add_argument("--compile-report", action="store_true",
                     help="print the warm-up/compilation cost table instead of the bench line")
     args = ap.parse_args()
@@ -641,8 +655,14 @@ def main():
         finally:
             a.close()
 
-    fused_arm = Arm(args.workload, dict(base, fusion=True, launch="persistent"), torch, stream, graph=graph)
+    fused_arm = Arm(args.workload, dict(base, fusion=True, launch="persistent"), torch, stream, graph=graph,
+                    autotune=args.workload == "batched" and not args.no_autotune)
     batch_sizes = (fused_arm.nnz, fused_arm.rows) if args.workload == "batched" else None
+    tuned = fused_arm.tuned
+    if tuned:
+        # the comparison arms run with the tuned setting too
+        c = tuned["config"]
+        base.update(tile=c["tile"], block=c["block"], unroll=c["unroll"], ctas_per_sm=c["ctas_per_sm"])
     clocks = Clocks(dev)
     if world > 1:
         torch.distributed.barrier()
@@ -746,6 +766,9 @@ def main():
             "e2e": extra.pop("e2e", None), "gpu_launches": fused["launches"], "roofline": roofline,
             "cpu_baseline": cpu, "clocks": clk}
     line.update(extra)
+    if tuned:
+        line["config"]["autotuned"] = tuned["config"]
+        line["autotune"] = tuned["trials"]
     st = fused["stats"]
     line["runtime_stats"] = {k: st.get(k) for k in ("compile_s", "kernels_compiled", "plan_hits", "plan_misses",
                                                      "kernel_disk_hits", "last_regs", "last_occupancy",

@@ -328,6 +328,20 @@ int dfs_batch_repeat(dfs_ctx *ctx, int32_t n);
  */
 int dfs_read_scalars(dfs_ctx *ctx, int32_t n, const dfs_store *stores, double *host_out);
 
+/*
+ * dfs_set_launch_config -- changes the launch parameters of a live context
+ * (block_threads: 128, 256, 512 or 1024; unroll: 1..8; ctas_per_sm: 0 =
+ * as many as fit, else at most that many), as an autotuner does between
+ * timed trials.  Flushes the pending window first.  Kernels already
+ * generated for other parameters stay cached.  Block size changes the
+ * per-thread order of reductions inside a point, so reduction results may
+ * differ in the last bits between settings; unroll and ctas_per_sm do not
+ * change any result.
+ * Returns DFS_OK; DFS_ERR_INVALID for values outside those ranges (nothing
+ * changes); DFS_ERR_STATE inside a batch or a capture.
+ */
+int dfs_set_launch_config(dfs_ctx *ctx, int32_t block_threads, int32_t unroll, int32_t ctas_per_sm);
+
 /* Source of the generated CUDA for the most recent launch (debugging). */
 int dfs_last_kernel_source(dfs_ctx *ctx, char *buf, size_t len, size_t *needed);
 

@@ -55,6 +55,7 @@ class Runtime:
         cfg.block_threads = block
         cfg.unroll = unroll
         cfg.ctas_per_sm = ctas_per_sm
+        self.block, self.unroll, self.ctas_per_sm = block, unroll, ctas_per_sm
         cfg.barrier_timeout_s = timeout_s
         cfg.stream = stream
         cfg.debug_skip_arrival = debug_skip_arrival
@@ -192,6 +193,13 @@ class Runtime:
     def sync(self):
         B.dfs_sync(self.ctx)
 
+    def sync_quiet(self):
+        """Synchronise and drop any deferred device error (after a failed trial)."""
+        try:
+            B.dfs_sync(self.ctx)
+        except B.DfsError:
+            pass
+
     def plan(self) -> dict:
         return B.dfs_plan_json(self.ctx)
 
@@ -217,6 +225,19 @@ class Runtime:
     def batch_repeat(self, n: int):
         """Run the last (steady, in-place) batch n more times (dfs_batch_repeat)."""
         B.dfs_batch_repeat(self.ctx, n)
+
+    def set_launch(self, block: int, unroll: int, ctas_per_sm: int = 0):
+        """New launch parameters for the following windows (dfs_set_launch_config)."""
+        B.dfs_set_launch_config(self.ctx, block, unroll, ctas_per_sm)
+        self.block, self.unroll, self.ctas_per_sm = block, unroll, ctas_per_sm
+
+    def set_tiling(self, tile: int | None = None, rows: int | None = None):
+        """New tile (1-D, elements) / row block (2-D) for arrays' partitions
+        from now on.  Tasks already submitted keep theirs; a store may be
+        partitioned differently by later tasks."""
+        self.flush()
+        self.tile, self.rows = tile, rows
+        self._layouts.clear()
 
     def read_scalars(self, arrays) -> list:
         """Values of many 0-d arrays with one gather and one copy (dfs_read_scalars)."""

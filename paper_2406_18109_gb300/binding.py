@@ -36,7 +36,8 @@ EXPORTS = ("dfs_config_default", "dfs_init", "dfs_shutdown", "dfs_store_create",
            "dfs_flush", "dfs_sync", "dfs_last_error", "dfs_plan_json", "dfs_stats_json",
            "dfs_last_kernel_source", "dfs_version", "dfs_dot_noalloc", "dfs_capture_begin",
            "dfs_capture_end", "dfs_graph_launch", "dfs_graph_destroy", "dfs_batch_begin",
-           "dfs_batch_next", "dfs_batch_end", "dfs_batch_repeat", "dfs_read_scalars")
+           "dfs_batch_next", "dfs_batch_end", "dfs_batch_repeat", "dfs_read_scalars",
+           "dfs_set_launch_config")
 
 
 class dfs_config(C.Structure):
@@ -100,6 +101,7 @@ def lib():
             "dfs_batch_end": (C.c_int, [P]),
             "dfs_batch_repeat": (C.c_int, [P, I32]),
             "dfs_read_scalars": (C.c_int, [P, I32, pI64, C.POINTER(C.c_double)]),
+            "dfs_set_launch_config": (C.c_int, [P, I32, I32, I32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -285,6 +287,10 @@ def dfs_read_scalars(ctx, stores, out=None):
     buf = out if out is not None else (C.c_double * max(1, n))()
     _check(ctx, lib().dfs_read_scalars(ctx, n, hs, buf))
     return buf[:n]
+
+
+def dfs_set_launch_config(ctx, block_threads: int, unroll: int, ctas_per_sm: int) -> None:
+    _check(ctx, lib().dfs_set_launch_config(ctx, block_threads, unroll, ctas_per_sm))
 
 
 def dfs_version() -> int:

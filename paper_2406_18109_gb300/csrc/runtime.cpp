@@ -1795,6 +1795,26 @@ int dfs_read_scalars(dfs_ctx* c, int32_t n, const dfs_store* hs, double* out) {
   }
 }
 
+int dfs_set_launch_config(dfs_ctx* c, int32_t block_threads, int32_t unroll, int32_t ctas_per_sm) {
+  try {
+    if (!c) return DFS_ERR_INVALID;
+    if (block_threads != 128 && block_threads != 256 && block_threads != 512 && block_threads != 1024)
+      return fail(c, DFS_ERR_INVALID, "block_threads must be 128, 256, 512 or 1024");
+    if (unroll < 1 || unroll > 8) return fail(c, DFS_ERR_INVALID, "unroll must be in 1..8");
+    if (ctas_per_sm < 0) return fail(c, DFS_ERR_INVALID, "negative ctas_per_sm");
+    if (c->batching || c->capturing) return fail(c, DFS_ERR_STATE, "inside a batch or a capture");
+    const int rc = flush(c);
+    if (rc) return rc;
+    c->cfg.block_threads = block_threads;
+    c->cfg.unroll = unroll;
+    c->cfg.ctas_per_sm = ctas_per_sm;
+    c->lastb.ok = false;
+    return DFS_OK;
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  }
+}
+
 const char* dfs_last_error(dfs_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
 int dfs_plan_json(dfs_ctx* c, char* buf, size_t len, size_t* needed) {

@@ -148,3 +148,49 @@ def test_cached_batch_kernel_serves_new_stores():
                 tol = 1e-5 * (S.astype(np.float64) + K)
                 assert np.all(np.abs(c.numpy() - co) <= tol) and np.all(np.abs(p.numpy() - po) <= tol)
             del arrs, outs
+
+
+def test_autotuned_batch_matches_fresh_run_and_oracle():
+    """Tuning changes the context's tile and launch shape between timed
+    trials; afterwards (state reset) the solves equal a fresh context built
+    with the chosen setting, bit for bit, and the oracle."""
+    from paper_2406_18109_gb300 import autotune
+    iters = 15
+
+    def setup(rt):
+        probs, bs = [], []
+        for spec in SPECS:
+            rp, col, val, xs = inputs.batched_cg_matrix(spec)
+            Am = A.CSR(rt, rp, col, val)
+            b = Am @ rt.array(xs)
+            probs.append((Am, W.cg_start_inplace(b)))
+            bs.append(b)
+        rt.flush()
+        return probs, bs
+
+    with gpu_runtime("persistent", tile=512, time_launches=True) as rt:
+        probs, bs = setup(rt)
+        best, trials = autotune.tune(rt, lambda: W.batched_cg_iteration(rt, probs),
+                                     space={"tile": [256, 512], "block": [128, 256], "unroll": [1, 2],
+                                            "ctas_per_sm": [0, 2]}, warmup=1, reps=2)
+        assert len(trials) == 5 and all(np.isfinite(ms) for _, ms in trials)
+        assert autotune.current(rt) == best
+        rt.batch_begin()
+        for (_, s), b in zip(probs, bs):
+            W.cg_reset_inplace(s, b)
+            rt.batch_next()
+        rt.batch_end()
+        for _ in range(iters):
+            W.batched_cg_iteration(rt, probs)
+        tuned = [s.x.numpy() for _, s in probs]
+    with gpu_runtime("persistent", tile=best["tile"], block=best["block"], unroll=best["unroll"],
+                     ctas_per_sm=best["ctas_per_sm"]) as rt:
+        probs, _ = setup(rt)
+        for _ in range(iters):
+            W.batched_cg_iteration(rt, probs)
+        fresh = [s.x.numpy() for _, s in probs]
+    for i, spec in enumerate(SPECS):
+        assert np.array_equal(tuned[i].view(np.uint64), fresh[i].view(np.uint64)), spec
+        rp, col, val, xs = inputs.batched_cg_matrix(spec)
+        xo, _, _ = programs.cg(rp, col, val, programs.spmv(rp, col, val, xs), iters)
+        assert np.linalg.norm(tuned[i] - xo) / np.linalg.norm(xo) < 1e-12, spec
