@@ -316,7 +316,8 @@ class Arm:
                 # (coordinate descent; the choice is cached per GPU and dtype)
                 import tempfile
                 from paper_2406_18109_gb300 import autotune as AT
-                space = {"tile": [256, 512], "block": [128, 256, 512], "unroll": [1, 2, 4], "ctas_per_sm": [0, 2, 3]}
+                space = {"tile_max": [512, 1024, 2048, 4096, 8192], "block": [128, 256, 512], "unroll": [1, 2],
+                         "ctas_per_sm": [0, 2]}
                 best, trials = AT.tune(rt, one_iteration, space=space, warmup=1, reps=3,
                                        key=f"batched-cg-{cfg['count']}-{cfg['seed']}-{cfg['dtype']}",
                                        cache_path=os.path.join(tempfile.gettempdir(), "dfs_autotune.json"),
@@ -636,8 +637,9 @@ def main():
     cfg = {"bs": configs.BLACK_SCHOLES, "cg": configs.CG, "jacobi": configs.JACOBI,
            "batched": configs.BATCHED_CG}[args.workload]
     base = dict(block=cfg["block"], unroll=cfg["unroll"], sms=sms, cache_dir=cache)
-    if "tile" in cfg:
-        base["tile"] = cfg["tile"]
+    for k in ("tile", "tile_max", "min_points"):
+        if k in cfg:
+            base[k] = cfg[k]
     if "rows" in cfg:
         base["rows"] = cfg["rows"]
     for k in ("block", "unroll", "tile", "rows"):       # command-line overrides (tuning)
@@ -661,8 +663,7 @@ def main():
     tuned = fused_arm.tuned
     if tuned:
         # the comparison arms run with the tuned setting too
-        c = tuned["config"]
-        base.update(tile=c["tile"], block=c["block"], unroll=c["unroll"], ctas_per_sm=c["ctas_per_sm"])
+        base.update(tuned["config"])
     clocks = Clocks(dev)
     if world > 1:
         torch.distributed.barrier()

@@ -46,7 +46,8 @@ class Runtime:
                  window_size: int = 256, block: int = 256, unroll: int = 2, ctas_per_sm: int = 0,
                  stream: int | None = None, cache_dir: str | None = None, timeout_s: float = 2.0,
                  tile: int | None = None, rows: int | None = None, sms: int = 152,
-                 debug_skip_arrival: int = 0, time_launches: bool = False):
+                 debug_skip_arrival: int = 0, time_launches: bool = False, tile_max: int = 16384,
+                 min_points: int | None = None):
         cfg = B.dfs_config_default()
         cfg.device = device
         cfg.fusion = 1 if fusion else 0
@@ -71,6 +72,8 @@ class Runtime:
         self.tile = tile
         self.rows = rows
         self.sms = sms
+        self.tile_max = tile_max
+        self.min_points = min_points
         self._alive = True
         L = B.lib()
         self._lib_submit = L.dfs_submit
@@ -103,12 +106,13 @@ class Runtime:
         return h
 
     def tile_1d(self, n: int) -> int:
+        """Elements per point of a length-n vector: the fixed `tile`, else the
+        smallest multiple of 256 giving at most `min_points` points (default
+        4 per SM), within [256, tile_max]."""
         if self.tile:
             return self.tile
-        # a few points per SM, tiles a multiple of 256 elements, at most 16384
-        t = math.ceil(n / (self.sms * 4))
-        t = max(256, min(16384, ((t + 255) // 256) * 256))
-        return t
+        t = math.ceil(n / (self.min_points or self.sms * 4))
+        return max(256, min(self.tile_max, ((t + 255) // 256) * 256))
 
     def rows_2d(self, m: int, w: int) -> int:
         if self.rows:
@@ -231,12 +235,18 @@ class Runtime:
         B.dfs_set_launch_config(self.ctx, block, unroll, ctas_per_sm)
         self.block, self.unroll, self.ctas_per_sm = block, unroll, ctas_per_sm
 
-    def set_tiling(self, tile: int | None = None, rows: int | None = None):
-        """New tile (1-D, elements) / row block (2-D) for arrays' partitions
-        from now on.  Tasks already submitted keep theirs; a store may be
+    def set_tiling(self, tile: int | None = None, rows: int | None = None, tile_max: int | None = None,
+                   min_points: int | None = None):
+        """New tiling policy for arrays' partitions from now on: a fixed tile
+        (1-D, elements) and row block (2-D), or (tile None) the size-dependent
+        policy of tile_1d.  Tasks already submitted keep theirs; a store may be
         partitioned differently by later tasks."""
         self.flush()
         self.tile, self.rows = tile, rows
+        if tile_max is not None:
+            self.tile_max = tile_max
+        if min_points is not None:
+            self.min_points = min_points
         self._layouts.clear()
 
     def read_scalars(self, arrays) -> list:

@@ -24,19 +24,21 @@ import time
 
 from .binding import DfsError
 
-PARAMS = ("tile", "block", "unroll", "ctas_per_sm")
+# search order; a space names any subset.  tile: a fixed tile for every
+# vector; tile_max: the cap of the size-dependent tile policy (tile None)
+PARAMS = ("tile", "tile_max", "block", "unroll", "ctas_per_sm")
 DEFAULT_SPACE = {"tile": [256, 512, 1024, 2048], "block": [128, 256, 512], "unroll": [1, 2, 4],
                  "ctas_per_sm": [0, 1, 2]}
 
 
-def current(rt) -> dict:
-    return {"tile": rt.tile, "block": rt.block, "unroll": rt.unroll, "ctas_per_sm": rt.ctas_per_sm}
+def current(rt, params=("tile", "block", "unroll", "ctas_per_sm")) -> dict:
+    return {p: getattr(rt, p) for p in params}
 
 
 def apply(rt, cfg: dict) -> None:
-    if cfg["tile"] != rt.tile:
-        rt.set_tiling(cfg["tile"], rt.rows)
-    rt.set_launch(cfg["block"], cfg["unroll"], cfg["ctas_per_sm"])
+    if ("tile" in cfg and cfg["tile"] != rt.tile) or ("tile_max" in cfg and cfg["tile_max"] != rt.tile_max):
+        rt.set_tiling(cfg.get("tile", rt.tile), rt.rows, tile_max=cfg.get("tile_max"))
+    rt.set_launch(cfg.get("block", rt.block), cfg.get("unroll", rt.unroll), cfg.get("ctas_per_sm", rt.ctas_per_sm))
 
 
 def _kernel_ms(st: dict) -> float:
@@ -66,7 +68,8 @@ def tune(rt, step, space: dict | None = None, warmup: int = 1, reps: int = 3, ke
          cache_path: str | None = None, gpu: str = "") -> tuple[dict, list]:
     """Tunes rt for `step`; leaves rt configured with the best setting and
     returns (setting, trials) where trials is a list of (setting, ms)."""
-    space = dict(DEFAULT_SPACE, **(space or {}))
+    space = dict(space) if space else dict(DEFAULT_SPACE)
+    params = [p for p in PARAMS if p in space]
     ck = f"{gpu}|{key}" if key else None
     cache = {}
     if cache_path and os.path.exists(cache_path):
@@ -89,9 +92,9 @@ def tune(rt, step, space: dict | None = None, warmup: int = 1, reps: int = 3, ke
         trials.append((dict(cfg), ms))
         return ms
 
-    best = current(rt)
+    best = current(rt, params)
     best_ms = trial(best)
-    for p in PARAMS:
+    for p in params:
         base = dict(best)
         for v in space[p]:
             if v == base[p]:

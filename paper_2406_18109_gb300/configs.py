@@ -19,8 +19,10 @@ CG = dict(m=256, iters=50, seed=0, tile=512, block=256, unroll=2)
 # log-uniform in [32, 1024], half random diagonally dominant SPD with n
 # log-uniform in [1024, 65536]), 100 iterations each, one batched launch per
 # iteration, the whole solve replayed from a CUDA graph; FP64 (dtype "f32"
-# for the FP32 variant)
-BATCHED_CG = dict(count=256, seed=4, iters=100, dtype="f64", tile=512, block=256, unroll=2)
+# for the FP32 variant).  Tiles follow the size-dependent policy (at least two
+# points per problem, at most tile_max elements); the bench autotunes
+# tile_max and the launch shape before capturing.
+BATCHED_CG = dict(count=256, seed=4, iters=100, dtype="f64", tile_max=512, min_points=2, block=256, unroll=2)
 
 # Jacobi: Fig. 1 stencil on an 8192x8192 FP32 grid (8190^2 interior),
 # 200 sweeps, interior U[0,1] (seed 2), boundary 1.0

@@ -9,16 +9,19 @@ from paper_2406_18109_gb300.binding import DfsError
 class FakeRuntime:
     def __init__(self, cost, fallback=lambda cfg: False, fails=lambda cfg: False):
         self.tile, self.rows, self.block, self.unroll, self.ctas_per_sm = 512, None, 256, 2, 0
+        self.tile_max = 16384
         self.cost, self.fallback, self.fails = cost, fallback, fails
         self.ms = 0.0
         self.fallbacks = 0
         self.steps = 0
 
     def cfg(self):
-        return autotune.current(self)
+        return autotune.current(self, autotune.PARAMS)
 
-    def set_tiling(self, tile, rows=None):
+    def set_tiling(self, tile, rows=None, tile_max=None):
         self.tile, self.rows = tile, rows
+        if tile_max is not None:
+            self.tile_max = tile_max
 
     def set_launch(self, block, unroll, ctas_per_sm=0):
         self.block, self.unroll, self.ctas_per_sm = block, unroll, ctas_per_sm
@@ -52,6 +55,7 @@ def test_coordinate_descent_finds_the_separable_optimum():
     best, trials = autotune.tune(rt, rt.step)
     assert best == {"tile": 1024, "block": 128, "unroll": 4, "ctas_per_sm": 2}
     assert autotune.current(rt) == best
+    assert autotune.current(rt) == best
     assert len(trials) == 1 + 3 + 2 + 2 + 2     # start, then every other value of each parameter
     for cfg, ms in trials:
         assert abs(ms - separable(cfg)) < 1e-12
@@ -76,3 +80,12 @@ def test_cache_reuses_the_choice(tmp_path):
     rt3 = FakeRuntime(lambda cfg: 1.0)
     autotune.tune(rt3, rt3.step, key="w1", cache_path=path, gpu="other")
     assert rt3.steps > 0
+
+
+def test_subset_space_and_tile_policy_cap():
+    rt = FakeRuntime(lambda cfg: abs(math.log2(cfg["tile_max"] / 4096)) + (cfg["block"] != 128))
+    rt.tile = None
+    best, trials = autotune.tune(rt, lambda: rt.step(), space={"tile_max": [1024, 2048, 4096, 8192],
+                                                               "block": [128, 256]})
+    assert best == {"tile_max": 4096, "block": 128} and len(trials) == 1 + 4 + 1
+    assert rt.tile is None and rt.tile_max == 4096
