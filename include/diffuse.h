@@ -154,6 +154,11 @@ typedef struct {
   /* 1: record CUDA events immediately around every kernel launch; the
    * per-kernel device times appear in dfs_stats_json after dfs_sync. */
   int32_t time_launches;
+  /* 1: automatic window growth (Section 7.2): when a window that filled up
+   * (window_size tasks) fused completely into one task, the window size
+   * doubles, up to window_max.  The current size is in dfs_stats_json. */
+  int32_t window_growth;
+  int32_t window_max;        /* cap of the growth (0 = 4096) */
 } dfs_config;
 
 /* Fills *cfg with the defaults above (device 0, fusion on, persistent). */

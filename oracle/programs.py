@@ -142,6 +142,24 @@ def jacobi(grid, sweeps: int, dt=np.float32):
 JACOBI_TASKS_PER_SWEEP = 6
 
 
+def jacobi3d(grid, sweeps: int, dt=np.float32):
+    """The Fig. 1a pattern carried to a 3-D (N+2)^3 grid (a 7-point average
+    over shifted interior slices; not a program of the paper): per sweep
+    work = (1/7) * ((((((c + zm) + zp) + ym) + yp) + xm) + xp), summed left to
+    right, then COPY(work, center).  The boundary is never written."""
+    g = _c(grid, dt).copy()
+    c = g[1:-1, 1:-1, 1:-1]
+    nb = (g[0:-2, 1:-1, 1:-1], g[2:, 1:-1, 1:-1], g[1:-1, 0:-2, 1:-1], g[1:-1, 2:, 1:-1],
+          g[1:-1, 1:-1, 0:-2], g[1:-1, 1:-1, 2:])
+    for _ in range(sweeps):
+        acc = c
+        for v in nb:
+            acc = ops.binary("ADD", acc, v, dt)
+        work = ops.binary("MUL", 1.0 / 7.0, acc, dt)
+        c[:] = ops.unary("COPY", work, dt)
+    return g
+
+
 def bicgstab(rowptr, col, val, b, tol: float, max_iters: int, dt=np.float64):
     """BiCGSTAB from x0 = 0 until ||r|| <= tol ||b||; returns (x, iterations, ||r||/||b||)."""
     b = _c(b, dt)

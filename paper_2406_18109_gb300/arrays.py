@@ -47,7 +47,7 @@ class Runtime:
                  stream: int | None = None, cache_dir: str | None = None, timeout_s: float = 2.0,
                  tile: int | None = None, rows: int | None = None, sms: int = 152,
                  debug_skip_arrival: int = 0, time_launches: bool = False, tile_max: int = 16384,
-                 min_points: int | None = None):
+                 min_points: int | None = None, window_growth: bool = False, window_max: int = 0):
         cfg = B.dfs_config_default()
         cfg.device = device
         cfg.fusion = 1 if fusion else 0
@@ -61,6 +61,8 @@ class Runtime:
         cfg.stream = stream
         cfg.debug_skip_arrival = debug_skip_arrival
         cfg.time_launches = 1 if time_launches else 0
+        cfg.window_growth = 1 if window_growth else 0
+        cfg.window_max = window_max
         self._cache_dir = cache_dir.encode() if cache_dir else None
         cfg.cache_dir = self._cache_dir
         self.ctx = B.dfs_init(cfg)
@@ -135,8 +137,12 @@ class Runtime:
         elif len(shape) == 2:
             r = self.rows_2d(shape[0], shape[1])
             dom, part = (max(1, math.ceil(shape[0] / r)), 1), self.tiling((r, shape[1]))
+        elif len(shape) == 3:
+            # blocks of whole planes, as many as rows_2d allows for a plane's elements
+            r = self.rows_2d(shape[0], shape[1] * shape[2])
+            dom, part = (max(1, math.ceil(shape[0] / r)), 1, 1), self.tiling((r, shape[1], shape[2]))
         else:
-            raise ValueError("arrays of rank > 2 are not supported by the front end")
+            raise ValueError("arrays of rank > 3 are not supported by the front end")
         lay = (dom, part, (C.c_int64 * len(dom))(*dom), len(dom))
         self._layouts[shape] = lay
         return lay

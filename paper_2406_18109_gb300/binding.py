@@ -44,7 +44,8 @@ class dfs_config(C.Structure):
     _fields_ = [("device", C.c_int32), ("fusion", C.c_int32), ("launch_mode", C.c_int32),
                 ("window_size", C.c_int32), ("stream", C.c_void_p), ("block_threads", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("unroll", C.c_int32), ("barrier_timeout_s", C.c_double),
-                ("cache_dir", C.c_char_p), ("debug_skip_arrival", C.c_int32), ("time_launches", C.c_int32)]
+                ("cache_dir", C.c_char_p), ("debug_skip_arrival", C.c_int32), ("time_launches", C.c_int32),
+                ("window_growth", C.c_int32), ("window_max", C.c_int32)]
 
 
 class dfs_arg(C.Structure):

@@ -87,6 +87,7 @@ struct Nest {
   int first, last;  // task indices [first, last)
   int dims;         // 1 (flat) or 2 (row loop)
   int vec;          // elements per vector access
+  int rank = 1;     // rank of the iteration space (rows of a 3-D space are (plane, row) pairs)
 };
 
 class Gen {
@@ -184,22 +185,27 @@ std::vector<Nest> Gen::nests_of(int g) {
     // dimensionality and vector width
     const Arg& sa = space_arg(S.tasks[i]);
     const int nd = sa.nd;
-    // collapse a 2-D space into a flat one when every access spans whole root rows
+    // collapse a 2-D or 3-D space into a flat one when every access spans
+    // whole root rows (and planes): its elements are then contiguous
     bool flat = nd <= 1;
-    if (nd == 2) {
+    if (nd >= 2) {
       flat = true;
       for (int t = i; t < j && flat; ++t)
         for (const Arg& a : S.tasks[t].args) {
           if (a.imm || a.nd == 0) continue;
           if (S.tasks[t].op == DFS_OP_SPMV && &a != &S.tasks[t].args[4]) continue;
           const LaunchRoot& r = R(a.root);
-          if (a.part.kind != 1 || a.part.vlo[1] != 0 || a.part.vhi[1] != r.shape[1] ||
-              a.part.off[1] > 0 || a.part.tile[1] < r.shape[1])
-            flat = false;
+          if (a.part.kind != 1) flat = false;
+          for (int d = 1; d < nd && flat; ++d)
+            if (a.part.vlo[d] != 0 || a.part.vhi[d] != r.shape[d] || a.part.off[d] > 0 ||
+                a.part.tile[d] < r.shape[d])
+              flat = false;
         }
     }
-    if (nd > 2) throw std::runtime_error("3-D element-wise iteration spaces are not supported");
+    if (nd > 3) throw std::runtime_error("iteration spaces of rank > 3 are not supported");
+    // rows mode: ext0 rows (2-D) or ext0 x ext1 rows (3-D) of the last dimension
     n.dims = flat ? 1 : 2;
+    n.rank = nd;
     // widest element over the memory accesses of the nest
     size_t esz = 0;
     bool aligned = true;
@@ -229,8 +235,11 @@ std::vector<Nest> Gen::nests_of(int g) {
               aligned = false;
           }
         } else {
-          if (r.stride[0] % vec || a.part.tile[1] % vec || a.part.off[1] % vec || a.part.vlo[1] % vec ||
-              (a.part.vhi[1] - a.part.vlo[1]) % vec)
+          const int cd = a.nd - 1;  // the column dimension
+          for (int d = 0; d < cd; ++d)
+            if (r.stride[d] % vec) aligned = false;
+          if (a.part.tile[cd] % vec || a.part.off[cd] % vec || a.part.vlo[cd] % vec ||
+              (a.part.vhi[cd] - a.part.vlo[cd]) % vec)
             aligned = false;
         }
       }
@@ -311,7 +320,7 @@ void Gen::emit_vector_group(int g) {
   bool flat = nests.size() == 1;
   for (int i = G.begin; i < G.end && flat; ++i)
     if (is_reduction(S.tasks[i].op)) flat = false;
-  if (flat && space_arg(t0).nd > 2) flat = false;
+  if (flat && space_arg(t0).nd > 3) flat = false;
   if (flat) {
     kc.has_flat = true;
     o << "    { // group " << g << ": tasks " << G.begin << ".." << G.end - 1 << ", one flat nest over "
@@ -468,6 +477,9 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
   auto addr = [&](const Arg& a, const std::string& e_flat, const std::string& row, const std::string& col) {
     const LaunchRoot& r = R(a.root);
     if (n.dims == 1) return ptr(a.root) + " + " + base.at(akey(a)) + " + " + e_flat;
+    if (n.rank == 3)
+      return ptr(a.root) + " + " + base.at(akey(a)) + " + ((" + row + ") / ext1) * " + std::to_string(r.stride[0]) +
+             "LL + ((" + row + ") % ext1) * " + std::to_string(r.stride[1]) + "LL + " + col;
     return ptr(a.root) + " + " + base.at(akey(a)) + " + (" + row + ") * " + std::to_string(r.stride[0]) + "LL + " + col;
   };
   // emits loads for slot u (vector width w), compute, stores; returns nothing
@@ -612,10 +624,12 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
     }
     o << ind << "  }\n";
   } else if (flat) {
-    // a rectangle of ext0 rows x ext1 columns swept as one range of
+    // a rectangle of nrows rows x ncols columns swept as one range of
     // (row, vector) cells with a grid stride
-    o << ind << "  const i64 nvr = ext1 / " << V << ";\n";
-    o << ind << "  const i64 ncell = ext0 * nvr;\n";
+    o << ind << "  const i64 nrows = " << (n.rank == 3 ? "ext0 * ext1" : "ext0") << ";\n";
+    o << ind << "  const i64 ncols = " << (n.rank == 3 ? "ext2" : "ext1") << ";\n";
+    o << ind << "  const i64 nvr = ncols / " << V << ";\n";
+    o << ind << "  const i64 ncell = nrows * nvr;\n";
     o << ind << "  i64 c = " << st0 << ";\n";
     // 32-bit division by the constant row length when the range allows it
     const bool narrow = flat_cells < (int64_t(1) << 31);
@@ -644,17 +658,19 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
     body(V, {"r"}, {""}, {"ir"}, {"jr"}, ind + "      ");
     o << ind << "  }\n";
   } else {
-    // rows: each row of ext1 elements is swept by the whole block
-    o << ind << "  for (i64 i = 0; i < ext0; ++i) {\n";
+    // rows: each row of ncols elements is swept by the whole block
+    o << ind << "  const i64 nrows = " << (n.rank == 3 ? "ext0 * ext1" : "ext0") << ";\n";
+    o << ind << "  const i64 ncols = " << (n.rank == 3 ? "ext2" : "ext1") << ";\n";
+    o << ind << "  for (i64 i = 0; i < nrows; ++i) {\n";
     if (V > 1) {
-      o << ind << "    const i64 nv = ext1 / " << V << ";\n";
+      o << ind << "    const i64 nv = ncols / " << V << ";\n";
       o << ind << "    for (i64 v = threadIdx.x; v < nv; v += " << BD << ") {\n";
       body(V, {"r"}, {""}, {"i"}, {"v * " + std::to_string(V)}, ind + "      ");
       o << ind << "    }\n";
     } else {
       o << ind << "    i64 j = threadIdx.x;\n";
       if (U > 1) {
-        o << ind << "    for (; j + " << (U - 1) * BD << " < ext1; j += " << U * BD << ") {\n";
+        o << ind << "    for (; j + " << (U - 1) * BD << " < ncols; j += " << U * BD << ") {\n";
         std::vector<std::string> sl, ef, er, ec;
         for (int u = 0; u < U; ++u) {
           sl.push_back("u" + std::to_string(u));
@@ -665,7 +681,7 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
         body(1, sl, ef, er, ec, ind + "      ");
         o << ind << "    }\n";
       }
-      o << ind << "    for (; j < ext1; j += " << BD << ") {\n";
+      o << ind << "    for (; j < ncols; j += " << BD << ") {\n";
       body(1, {"t"}, {""}, {"i"}, {"j"}, ind + "      ");
       o << ind << "    }\n";
     }

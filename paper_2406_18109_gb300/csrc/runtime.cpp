@@ -48,7 +48,7 @@ struct CachedWindow {
 
 struct Stats {
   int64_t tasks = 0, groups = 0, launches = 0, barriers = 0, flushes = 0;
-  int64_t plan_hits = 0, plan_misses = 0, temporaries = 0;
+  int64_t plan_hits = 0, plan_misses = 0, temporaries = 0, window_growths = 0;
   int last_regs = 0, last_occupancy = 0, last_grid = 0, last_block = 0;
   int64_t bytes_allocated = 0, allocations = 0;
   double analysis_s = 0.0;
@@ -642,7 +642,17 @@ void release_window(dfs_ctx* c) {
   for (int64_t r : roots) maybe_free(c, r);
 }
 
-int flush(dfs_ctx* c) {
+// Window growth (Section 7.2): a full window that fused into one task
+// doubles the window size, up to the configured cap.
+void grow_window(dfs_ctx* c, const Plan& p) {
+  const int cap = c->cfg.window_max > 0 ? c->cfg.window_max : 4096;
+  if (c->cfg.window_growth && p.groups.size() == 1 && c->cfg.window_size < cap) {
+    c->cfg.window_size = std::min(cap, 2 * c->cfg.window_size);
+    c->st.window_growths += 1;
+  }
+}
+
+int flush(dfs_ctx* c, bool size_trigger = false) {
   if (c->window.empty()) return DFS_OK;
   c->st.flushes += 1;
   const auto t0 = std::chrono::steady_clock::now();
@@ -652,6 +662,7 @@ int flush(dfs_ctx* c) {
   if (it != c->wcache.end()) {
     c->st.plan_hits += 1;
     cw = it->second.get();
+    if (size_trigger) grow_window(c, cw->plan);
   } else {
     c->st.plan_misses += 1;
     std::unique_ptr<CachedWindow> built;
@@ -660,6 +671,7 @@ int flush(dfs_ctx* c) {
       release_window(c);
       return rc;
     }
+    if (size_trigger) grow_window(c, built->plan);
     if (!c->device) {
       c->st.groups += (int64_t)built->plan.groups.size();
       release_window(c);
@@ -1499,7 +1511,7 @@ int dfs_submit(dfs_ctx* c, int32_t op, int32_t ndim, const int64_t* dom, int32_t
     c->window.push_back(std::move(t));
     c->seq += 1;
     c->st.tasks += 1;
-    if ((int)c->window.size() >= c->cfg.window_size && !c->batching) return flush(c);
+    if ((int)c->window.size() >= c->cfg.window_size && !c->batching) return flush(c, true);
     return DFS_OK;
   } catch (const std::exception& e_) {
     return internal_error(c, e_.what());
@@ -1856,7 +1868,8 @@ int dfs_stats_json(dfs_ctx* c, char* buf, size_t len, size_t* needed) {
     }
     o << "}";
     o << ", \"batches\": " << c->batches << ", \"batched_instances\": " << c->batched_instances
-      << ", \"batch_repeats\": " << c->batch_repeats << ", \"batch_fallbacks\": " << c->batch_fallbacks << ", \"batch_fallback_reason\": \"" << c->batch_fallback_reason
+      << ", \"window_size\": " << c->cfg.window_size << ", \"window_growths\": " << s.window_growths
+    << ", \"batch_repeats\": " << c->batch_repeats << ", \"batch_fallbacks\": " << c->batch_fallbacks << ", \"batch_fallback_reason\": \"" << c->batch_fallback_reason
       << "\"";
     o << ", \"sms\": " << c->sms << "}";
     return write_json(o.str(), buf, len, needed);

@@ -150,6 +150,24 @@ def jacobi_sweep(views) -> None:
     center[:] = work
 
 
+def jacobi3d_views(grid: Array):
+    """center and its six face neighbours of an (N+2)^3 grid, as shifted
+    interior views (the Fig. 1a pattern in 3-D)."""
+    i, lo, hi = slice(1, -1), slice(0, -2), slice(2, None)
+    return (grid[i, i, i], grid[lo, i, i], grid[hi, i, i], grid[i, lo, i], grid[i, hi, i],
+            grid[i, i, lo], grid[i, i, hi])
+
+
+def jacobi3d_sweep(views) -> None:
+    """work = (1/7)(c + z- + z+ + y- + y+ + x- + x+), then center[:] = work (8 tasks)."""
+    center = views[0]
+    acc = center
+    for v in views[1:]:
+        acc = acc + v
+    work = (1.0 / 7.0) * acc
+    center[:] = work
+
+
 @dataclass
 class BiCGState:
     x: Array

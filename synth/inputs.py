@@ -213,3 +213,10 @@ def serving_payload(req: dict):
     if req["kind"] == "bs":
         return bs_inputs(req["size"], seed=req["seed"])
     return uniform(req["seed"], -1.0, 1.0, req["size"] ** 3)
+
+
+def jacobi3d_grid(N: int, seed: int = 2, dtype=np.float32) -> np.ndarray:
+    """(N+2)^3 grid: interior U[0,1] from `seed`, boundary 1.0."""
+    g = np.ones((N + 2, N + 2, N + 2), dtype=np.float64)
+    g[1:-1, 1:-1, 1:-1] = np.random.default_rng(seed).uniform(0.0, 1.0, (N, N, N))
+    return g.astype(dtype)

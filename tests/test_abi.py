@@ -262,3 +262,74 @@ def test_window_size_triggers_analysis():
         d = c - 3.0                              # third task: window full, analysed
     st = rt.stats()
     assert st["flushes"] == 1 and st["tasks"] == 3
+
+
+def test_window_grows_while_everything_fuses():
+    """Section 7.2: the window size doubles whenever a full window fused into
+    one task, up to the cap; a window that does not fuse completely keeps it."""
+    rt = rt0(tile=4, window_size=2, window_growth=True, window_max=16)
+    a = rt.empty((8,), np.float32)
+    x = a
+    sizes = []
+    for _ in range(40):                      # an element-wise chain: every window fuses
+        try:
+            x = x * 1.5
+        except B.DfsError as e:
+            assert e.code == -2
+        sizes.append(rt.stats()["window_size"])
+    assert sizes[-1] == 16 and sorted(set(sizes)) == [2, 4, 8, 16]
+    assert rt.stats()["window_growths"] == 3
+    # reductions cut the window into several tasks: no growth
+    rt = rt0(tile=4, window_size=4, window_growth=True)
+    v = rt.empty((8,), np.float32)
+    for _ in range(12):
+        try:
+            s = A.dot(v, v)
+            v = v * s
+        except B.DfsError:
+            pass
+    assert rt.stats()["window_size"] == 4 and rt.stats()["window_growths"] == 0
+    # growth is off by default
+    rt = rt0(tile=4, window_size=2)
+    y = rt.empty((8,), np.float32)
+    for _ in range(10):
+        try:
+            y = y + 1.0
+        except B.DfsError:
+            pass
+    assert rt.stats()["window_size"] == 2
+
+
+def test_3d_stencil_plan_and_kernel_compiles():
+    """Slices with offsets in 3-D: the 7-point stencil fuses like Fig. 1's
+    (six ADDs and the MULT in one task, COPY after the barrier)."""
+    rt = rt0(rows=2)
+    g = rt.empty((6, 7, 8), np.float32)
+    W.jacobi3d_sweep(W.jacobi3d_views(g))
+    p = rt.plan()
+    assert p["groups"] == [[0, 1, 2, 3, 4, 5, 6], [7]]
+    assert len(p["temporaries"]) == 6 and p["barriers"] == 1
+    with pytest.raises(B.DfsError) as e:
+        rt.flush()
+    assert e.value.code == -2
+    assert "% ext1" in rt.kernel_source()        # rows of a 3-D space are (plane, row) pairs
+
+
+def test_fig6_temporary_example_plan():
+    """Section 5.1's example: z = 2x; w = y + z; v = w**2; a reduction over the
+    view w[n/2:]; del x, y, z, w.  MULT, ADD, POW fuse; the reduction over the
+    view is a separate task; only z is temporary."""
+    rt = rt0(tile=4)
+    x = A.full(rt, (16,), 0.0)
+    y = A.full(rt, (16,), 1.0)
+    with pytest.raises(B.DfsError):
+        rt.flush()
+    z = 2.0 * x
+    w = y + z
+    v = w ** 2.0
+    nrm = A.dot(w[8:], w[8:])
+    zh, wh = z.handle, w.handle
+    del x, y, z, w
+    p = rt.plan()
+    assert p["groups"][0] == [0, 1, 2] and [3] in p["groups"]
+    assert p["temporaries"] == [zh] and wh not in p["temporaries"]

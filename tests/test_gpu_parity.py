@@ -282,6 +282,50 @@ def test_spmv_output_as_temporary(mode):
     assert abs(rg - y @ y) <= 1e-13 * (y @ y)
 
 
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("rows", [3, 64])
+def test_jacobi3d_matches_oracle_bitwise(mode, rows):
+    """Slices with offsets in 3-D: a 7-point stencil over shifted views of a
+    15^3 grid (blocks of 3 planes: 5 points with a ragged last one; or one
+    block), fused rows of (plane, row) pairs and the flat sweep."""
+    g = inputs.jacobi3d_grid(13, seed=3)
+    with gpu_runtime(mode, rows=rows) as rt:
+        grid = rt.array(g)
+        views = W.jacobi3d_views(grid)
+        for _ in range(4):
+            W.jacobi3d_sweep(views)
+            rt.flush()
+        got = grid.numpy()
+    want = programs.jacobi3d(g, 4, np.float32)
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+
+
+def test_fig6_example_values_and_temporary():
+    """Section 5.1's fragment with random x, y: v = (y + 2x)^2 within 1e-15
+    relative per element (CUDA's pow and the host's may round differently by
+    an ulp), the reduction over w[n/2:] within 1e-13, and z never allocated."""
+    n = 10_000
+    x, y = inputs.uniform(11, -1, 1, n), inputs.uniform(12, -1, 1, n)
+    with gpu_runtime("persistent", tile=1024) as rt:
+        X, Y = rt.array(x), rt.array(y)
+        rt.flush()
+        a0 = rt.stats()["allocations"]
+        z = 2.0 * X
+        w = Y + z
+        v = w ** 2.0
+        nrm = A.norm(w[n // 2:])
+        del X, Y, z, w
+        vg, ng = v.numpy(), float(nrm.numpy())
+        allocs = rt.stats()["allocations"] - a0
+    from oracle import ops
+    wo = ops.binary("ADD", y, ops.binary("MUL", 2.0, x, np.float64), np.float64)
+    vo = ops.binary("POW", wo, 2.0, np.float64)
+    assert np.max(np.abs(vg - vo) / np.maximum(vo, 1e-300)) <= 1e-15
+    want = np.sqrt(np.dot(wo[n // 2:], wo[n // 2:]))
+    assert abs(ng - want) <= 1e-13 * want
+    assert allocs == 3                           # w, v and the norm's 0-d result; z stays in registers
+
+
 # ------------------------------------------------------- runtime behaviour
 def test_temporaries_are_never_allocated():
     n = 1 << 16

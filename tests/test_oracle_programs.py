@@ -255,6 +255,40 @@ def test_jacobi_is_jacobi_not_gauss_seidel():
     assert np.array_equal(programs.jacobi(g, 1, np.float64), new)
 
 
+def test_jacobi3d_matches_explicit_loops_and_delta():
+    # an explicit double-buffered triple loop in the stated summation order
+    g = np.random.default_rng(5).uniform(0, 1, (5, 6, 7)).astype(np.float32)
+    new = g.copy()
+    sev = np.float32(1.0 / 7.0)
+    for a in range(1, 4):
+        for b in range(1, 5):
+            for c in range(1, 6):
+                acc = g[a, b, c]
+                for v in (g[a - 1, b, c], g[a + 1, b, c], g[a, b - 1, c], g[a, b + 1, c], g[a, b, c - 1],
+                          g[a, b, c + 1]):
+                    acc = np.float32(acc + v)
+                new[a, b, c] = np.float32(sev * acc)
+    assert np.array_equal(programs.jacobi3d(g, 1, np.float32), new)
+    # a unit delta spreads 1/7 onto itself and its six face neighbours only
+    d = np.zeros((5, 5, 5))
+    d[2, 2, 2] = 1.0
+    out = programs.jacobi3d(d, 1, np.float64)
+    want = np.zeros((5, 5, 5))
+    for (a, b, c) in ((2, 2, 2), (1, 2, 2), (3, 2, 2), (2, 1, 2), (2, 3, 2), (2, 2, 1), (2, 2, 3)):
+        want[a, b, c] = 1.0 / 7.0
+    assert np.allclose(out, want, atol=1e-16)
+
+
+def test_jacobi3d_affine_fixed_point_and_max_principle():
+    i, j, k = np.meshgrid(np.arange(6.0), np.arange(7.0), np.arange(8.0), indexing="ij")
+    g = 0.5 * i - 0.25 * j + 0.125 * k + 2.0
+    assert np.allclose(programs.jacobi3d(g, 3, np.float64), g, atol=1e-13)
+    g = np.ones((8, 8, 8), np.float32)
+    g[1:-1, 1:-1, 1:-1] = np.random.default_rng(6).uniform(0, 1, (6, 6, 6))
+    out = programs.jacobi3d(g, 10, np.float32)
+    assert out[1:-1, 1:-1, 1:-1].min() >= g[1:-1, 1:-1, 1:-1].min() and out.max() <= 1.0
+
+
 # --------------------------------------------------------------------- BiCGSTAB
 def test_bicgstab_manufactured_solution():
     rp, col, val = inputs.poisson3d_csr(8)
