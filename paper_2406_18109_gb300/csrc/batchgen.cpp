@@ -47,6 +47,7 @@ class BatchGen {
   std::map<int64_t, int> ptr_of;          // root -> pointer slot
   std::map<int64_t, int> sslot;           // 0-d root -> scalar slot
   std::map<std::string, int> vbase;       // akey -> first v slot (tile, off, vlo, vhi or vlo, vhi)
+  std::map<int, int> kbase;               // SpMV task -> slot of its lanes per row
   std::map<int64_t, bool> produced;       // 0-d root holds a kernel-produced value
   std::map<int64_t, std::string> local;   // 0-d root -> register inside the open scalar phase
   struct Pending { int slot; int64_t root; int dtype; int pslot; };
@@ -58,6 +59,7 @@ class BatchGen {
   const LaunchRoot& R(int64_t r) const { return S.roots[S.root_index.at(r)]; }
   std::string T(int dt) const { return dtype_cname(dt); }
   int vslots(const Task& t, size_t ai);
+  int kslot(const Task& t);
   std::string imm(int task, int arg, int dt);
   std::string zero_d_read(int64_t root, int dt, bool in_scalar);
   void vector_group(int g);
@@ -67,6 +69,19 @@ class BatchGen {
   void finals(const char* ind);
   void barrier();
 };
+
+// One descriptor slot holding the instance's lanes per row (spmv_lanes) of
+// an SpMV task's matrix.
+int BatchGen::kslot(const Task& t) {
+  const int task = (int)(&t - &S.tasks[0]);
+  auto it = kbase.find(task);
+  if (it != kbase.end()) return it->second;
+  const int b = bc.nv;
+  bc.v_src.push_back({task, 1, 4});
+  bc.nv += 1;
+  kbase[task] = b;
+  return b;
+}
 
 int BatchGen::vslots(const Task& t, size_t ai) {
   const Arg& a = t.args[ai];
@@ -285,6 +300,7 @@ void BatchGen::vector_group(int g) {
         zv[{k, (int)ai}] = nm;
       }
     }
+    std::map<int, std::string> spre;  // SpMV task -> value computed before the body
     auto body = [&](int w, const std::vector<std::string>& slots, const std::vector<std::string>& ef,
                     const std::string& pad) {
       const int ns = (int)slots.size();
@@ -324,6 +340,9 @@ void BatchGen::vector_group(int g) {
               if (t.args.size() == 3) o << ", " << val(1);
               o << ");\n";
               cur[akey(t.args.back())] = res;
+            } else if (t.op == DFS_OP_SPMV && spre.count(k)) {
+              o << pad << "const " << T(dt) << " " << res << " = " << spre.at(k) << ";\n";
+              cur[akey(t.args[4])] = res;
             } else if (t.op == DFS_OP_SPMV) {
               const Arg& y = t.args[4];
               const int yb = vslots(t, 4);
@@ -371,32 +390,62 @@ void BatchGen::vector_group(int g) {
         }
       }
     };
-    // block-stride loop over the point's n elements
-    o << ind << "  if (n > 0) {\n";
-    const std::string it = V > 1 ? "v" : "e";
-    const std::string lim = V > 1 ? "nv" : "n";
-    auto fe = [&](const std::string& x) { return V > 1 ? "(" + x + ") * " + std::to_string(V) : "(" + x + ")"; };
-    if (V > 1) o << ind << "    const i64 nv = n / " << V << ";\n";
-    o << ind << "    i64 " << it << " = threadIdx.x;\n";
-    if (U > 1) {
-      o << ind << "    for (; " << it << " + " << (U - 1) * BD << " < " << lim << "; " << it << " += " << U * BD << ") {\n";
-      std::vector<std::string> sl, ef;
-      for (int u = 0; u < U; ++u) {
-        sl.push_back("u" + std::to_string(u));
-        ef.push_back(fe(it + " + " + std::to_string(u * BD)));
+    bool has_spmv = false;
+    for (int k = i; k < j; ++k) has_spmv = has_spmv || S.tasks[k].op == DFS_OP_SPMV;
+    if (has_spmv) {
+      // SpMV rows shared by lanes (spmv_warp, lanes per row from the
+      // instance's descriptor): each warp takes 32 consecutive rows per trip
+      o << ind << "  const int lane_ = threadIdx.x & 31;\n";
+      o << ind << "  for (i64 wb = (i64)threadIdx.x - lane_; wb < n; wb += " << BD << ") {\n";
+      o << ind << "    const i64 e = wb + lane_;\n";
+      o << ind << "    const bool act_ = e < n;\n";
+      for (int k = i; k < j; ++k) {
+        const Task& t = S.tasks[k];
+        if (t.op != DFS_OP_SPMV) continue;
+        const Arg& y = t.args[4];
+        const int yb = vslots(t, 4);
+        const int dt = y.dtype;
+        const std::string nm = "sp" + std::to_string(k);
+        o << ind << "    const " << T(dt) << " " << nm << " = spmv_warp<" << T(dt) << ">(" << P_(t.args[0].root) << " + "
+          << base.at(akey(t.args[0])) << ", " << P_(t.args[1].root) << " + " << base.at(akey(t.args[1])) << ", "
+          << P_(t.args[2].root) << " + " << base.at(akey(t.args[2])) << ", " << P_(t.args[3].root) << " + "
+          << base.at(akey(t.args[3])) << ", (" << base.at(akey(y)) << " - D.v[" << yb + 2 << "] + e), act_, (int)D.v["
+          << kslot(t) << "]);\n";
+        spre[k] = nm;
       }
-      body(V, sl, ef, ind + "      ");
+      o << ind << "    if (act_) {\n";
+      body(1, {"r"}, {"e"}, ind + "      ");
       o << ind << "    }\n";
+      o << ind << "  }\n";
     }
-    o << ind << "    for (; " << it << " < " << lim << "; " << it << " += " << BD << ") {\n";
-    body(V, {"r"}, {fe(it)}, ind + "      ");
-    o << ind << "    }\n";
-    if (V > 1) {
-      o << ind << "    for (i64 e = nv * " << V << " + threadIdx.x; e < n; e += " << BD << ") {\n";
-      body(1, {"t"}, {"e"}, ind + "      ");
+    if (!has_spmv) {
+      // block-stride loop over the point's n elements
+      o << ind << "  if (n > 0) {\n";
+      const std::string it = V > 1 ? "v" : "e";
+      const std::string lim = V > 1 ? "nv" : "n";
+      auto fe = [&](const std::string& x) { return V > 1 ? "(" + x + ") * " + std::to_string(V) : "(" + x + ")"; };
+      if (V > 1) o << ind << "    const i64 nv = n / " << V << ";\n";
+      o << ind << "    i64 " << it << " = threadIdx.x;\n";
+      if (U > 1) {
+        o << ind << "    for (; " << it << " + " << (U - 1) * BD << " < " << lim << "; " << it << " += " << U * BD << ") {\n";
+        std::vector<std::string> sl, ef;
+        for (int u = 0; u < U; ++u) {
+          sl.push_back("u" + std::to_string(u));
+          ef.push_back(fe(it + " + " + std::to_string(u * BD)));
+        }
+        body(V, sl, ef, ind + "      ");
+        o << ind << "    }\n";
+      }
+      o << ind << "    for (; " << it << " < " << lim << "; " << it << " += " << BD << ") {\n";
+      body(V, {"r"}, {fe(it)}, ind + "      ");
       o << ind << "    }\n";
+      if (V > 1) {
+        o << ind << "    for (i64 e = nv * " << V << " + threadIdx.x; e < n; e += " << BD << ") {\n";
+        body(1, {"t"}, {"e"}, ind + "      ");
+        o << ind << "    }\n";
+      }
+      o << ind << "  }\n";
     }
-    o << ind << "  }\n";
     for (const Acc& ac : accs) {
       o << ind << "  { const " << T(ac.dt) << " tot = block_sum(" << ac.var << ", (" << T(ac.dt) << "*)red_buf);\n";
       o << ind << "    if (threadIdx.x == 0) ((" << T(ac.dt) << "*)P.partials)[" << ac.slot

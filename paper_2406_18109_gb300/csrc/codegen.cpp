@@ -88,7 +88,15 @@ struct Nest {
   int dims;         // 1 (flat) or 2 (row loop)
   int vec;          // elements per vector access
   int rank = 1;     // rank of the iteration space (rows of a 3-D space are (plane, row) pairs)
+  bool coop = false;  // an SpMV of the nest uses several lanes per row (spmv_warp)
 };
+
+// Lanes per row of an SpMV task's matrix (col and rowptr extents).
+int spmv_k(const Task& t) {
+  const NPart& c = t.args[1].part;
+  const NPart& r = t.args[0].part;
+  return spmv_lanes(c.vhi[0] - c.vlo[0], r.vhi[0] - r.vlo[0] - 1);
+}
 
 class Gen {
  public:
@@ -245,6 +253,9 @@ std::vector<Nest> Gen::nests_of(int g) {
       }
     }
     n.vec = aligned ? vec : 1;
+    for (int t = i; t < j; ++t)
+      if (S.tasks[t].op == DFS_OP_SPMV && spmv_k(S.tasks[t]) > 1) n.coop = true;
+    if (n.coop) n.vec = 1;  // lanes of a warp take consecutive rows
     v.push_back(n);
     i = j;
     while (i < G.end && S.tasks[i].scalar()) ++i;
@@ -472,6 +483,7 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
     }
   }
 
+  std::map<int, std::string> spre;  // SpMV task -> value computed before the body (warp-cooperative rows)
   // ---- body generator for one element group: `u` unroll slot, lanes V,
   // element offset expression `eoff` (flat) or (row, col) expressions
   auto addr = [&](const Arg& a, const std::string& e_flat, const std::string& row, const std::string& col) {
@@ -528,6 +540,9 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
             if (t.args.size() == 3) o << ", " << val(1);
             o << ");\n";
             cur[akey(t.args.back())] = res;
+          } else if (t.op == DFS_OP_SPMV && spre.count(i)) {
+            o << pad << "const " << T(dt) << " " << res << " = " << spre.at(i) << ";\n";
+            cur[akey(t.args[4])] = res;
           } else if (t.op == DFS_OP_SPMV) {
             const Arg& y = t.args[4];
             const std::string row = "(" + base.at(akey(y)) + " - " + std::to_string(y.part.vlo[0]) + "LL + " +
@@ -590,7 +605,34 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
   const std::string stp = flat ? "gs" : std::to_string(BD);
   if (flat) o << ind << "  const i64 gs = (i64)gridDim.x * " << BD << ";\n";
   auto slot_off = [&](int u) { return flat ? std::to_string(u) + " * gs" : std::to_string(u * BD); };
-  if (n.dims == 1) {
+  if (n.dims == 1 && n.coop) {
+    // SpMV rows shared by lanes (spmv_warp): each warp takes 32 consecutive
+    // rows per trip, so every lane of a warp runs the same trips
+    o << ind << "  const i64 n = ";
+    for (int d = 0; d < nd; ++d) o << (d ? " * " : "") << "ext" << d;
+    o << ";\n";
+    o << ind << "  const int lane_ = threadIdx.x & 31;\n";
+    o << ind << "  for (i64 wb = " << st0 << " - lane_; wb < n; wb += " << stp << ") {\n";
+    o << ind << "    const i64 e = wb + lane_;\n";
+    o << ind << "    const bool act_ = e < n;\n";
+    for (int i = n.first; i < n.last; ++i) {
+      const Task& t = S.tasks[i];
+      if (t.op != DFS_OP_SPMV) continue;
+      const Arg& y = t.args[4];
+      const int dt = y.dtype;
+      const std::string nm = "sp" + std::to_string(i);
+      o << ind << "    const " << T(dt) << " " << nm << " = spmv_warp<" << T(dt) << ">(" << ptr(t.args[0].root) << " + "
+        << base.at(akey(t.args[0])) << ", " << ptr(t.args[1].root) << " + " << base.at(akey(t.args[1])) << ", "
+        << ptr(t.args[2].root) << " + " << base.at(akey(t.args[2])) << ", " << ptr(t.args[3].root) << " + "
+        << base.at(akey(t.args[3])) << ", (" << base.at(akey(y)) << " - " << y.part.vlo[0] << "LL + e), act_, "
+        << spmv_k(t) << ");\n";
+      spre[i] = nm;
+    }
+    o << ind << "    if (act_) {\n";
+    body(1, {"r"}, {"e"}, {""}, {""}, ind + "      ");
+    o << ind << "    }\n";
+    o << ind << "  }\n";
+  } else if (n.dims == 1) {
     // n elements in one contiguous range; vectors of V; main loop unrolled U
     o << ind << "  const i64 n = ";
     for (int d = 0; d < nd; ++d) o << (d ? " * " : "") << "ext" << d;

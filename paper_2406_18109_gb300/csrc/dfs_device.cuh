@@ -134,6 +134,40 @@ __device__ __forceinline__ T spmv_row(const int* __restrict__ rowptr, const int*
   return acc;
 }
 
+// Rows of y = A x for the 32 lanes of a warp, K lanes per row (K a power of
+// two, 1..32).  In round t (0 <= t < K) the lanes of group g = lane / K
+// compute the row of lane t * (32 / K) + g: lane q of the group sums the
+// entries k0 + q, k0 + q + K, ... in order with fma, and the group combines
+// its K partial sums with a xor butterfly (every lane of the group ends with
+// the same bits, since each level adds the same two values).  Each round's
+// loads of col and val are K consecutive entries per row, so dense-ish rows
+// are read with few memory transactions per instruction.  Every lane of the
+// warp must call it with the same K (warp-uniform control flow); a lane with
+// act false owns no row and gets 0.  K = 1 is spmv_row on every lane.
+template <typename T>
+__device__ __forceinline__ T spmv_warp(const int* __restrict__ rowptr, const int* __restrict__ col,
+                                       const T* __restrict__ val, const T* x, i64 r, bool act, int K) {
+  if (K <= 1) return act ? spmv_row<T>(rowptr, col, val, x, r) : T(0);
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int rpr = 32 / K, g = lane / K, q = lane & (K - 1);
+  T mine = T(0);
+  for (int t = 0; t < K; ++t) {
+    const int src = t * rpr + g;
+    const i64 rr = __shfl_sync(full, r, src);
+    const int ra = __shfl_sync(full, act ? 1 : 0, src);
+    T acc = T(0);
+    if (ra) {
+      const int k0 = __ldg(rowptr + rr), k1 = __ldg(rowptr + rr + 1);
+      for (int k = k0 + q; k < k1; k += K) acc = red_fma(__ldg(val + k), ld(x + __ldg(col + k)), acc);
+    }
+    for (int m = 1; m < K; m <<= 1) acc = op_add(acc, __shfl_xor_sync(full, acc, m));
+    const T got = __shfl_sync(full, acc, (lane % rpr) * K);
+    if (t == lane / rpr) mine = got;
+  }
+  return act ? mine : T(0);
+}
+
 // ----------------------------------------------------------- control block
 // One per context, zero-initialised; every kernel leaves it zeroed on exit.
 struct Ctl {

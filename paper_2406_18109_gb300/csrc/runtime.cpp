@@ -961,7 +961,14 @@ int flush_batch(dfs_ctx* c) {
     }
     for (int k = 0; k < bc.nv; ++k) {
       const auto& src = bc.v_src[k];
-      const NPart& p = iw[i][src.task].args[src.arg].part;
+      const Task& tk = iw[i][src.task];
+      if (src.field == 4) {  // lanes per row of an SpMV task's matrix
+        const NPart& cp = tk.args[1].part;
+        const NPart& rp = tk.args[0].part;
+        d[NP + NIm + k] = spmv_lanes(cp.vhi[0] - cp.vlo[0], rp.vhi[0] - rp.vlo[0] - 1);
+        continue;
+      }
+      const NPart& p = tk.args[src.arg].part;
       const int64_t vals[] = {p.tile[0], p.off[0], p.vlo[0], p.vhi[0]};
       d[NP + NIm + k] = vals[src.field];
     }

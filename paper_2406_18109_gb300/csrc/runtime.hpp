@@ -207,11 +207,23 @@ struct BatchCode {
   std::vector<int64_t> ptr_roots;              // instance-0 root of each pointer slot
   std::vector<std::pair<int, int>> imm_src;    // (task, arg) of each immediate slot
   struct VSrc {
-    int task, arg, field;                      // field: 0 tile, 1 off, 2 vlo, 3 vhi
+    int task, arg, field;                      // field: 0 tile, 1 off, 2 vlo, 3 vhi, 4 SpMV lanes per row
   };
   std::vector<VSrc> v_src;
   std::vector<int> prefix_task;                // first task of the group each prefix array serves
 };
+
+// Lanes per row of the warp-cooperative SpMV (spmv_warp) for a CSR matrix
+// of nnz entries over nrows rows: the largest power of two K <= 32 with
+// 3 K <= nnz / nrows, so that every lane of a group sums about three or more
+// entries; 1 (one row per lane) for sparser rows.  A property of the matrix
+// alone, so every path that multiplies by it sums its rows in one order.
+inline int spmv_lanes(int64_t nnz, int64_t nrows) {
+  const int64_t avg = nrows > 0 ? nnz / nrows : 0;
+  int k = 1;
+  while (k < 32 && 3 * (2 * k) <= avg) k *= 2;
+  return k;
+}
 
 // Returns false (with a reason) when the launch cannot be batched.
 bool generate_batch(const LaunchSpec& spec, int vec, BatchCode& out, std::string& why);

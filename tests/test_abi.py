@@ -226,7 +226,7 @@ def test_spmv_output_temporary_compiles():
             rt.batch_end() if batched else rt.flush()
         assert e.value.code == -2
         assert rt.stats()["batch_fallbacks"] == 0
-        assert "spmv_row" in rt.kernel_source()
+        assert "spmv_warp" in rt.kernel_source()    # 16 entries per row: lanes share rows
 
 
 def test_capture_api_needs_a_device_and_checks_state():
@@ -333,3 +333,27 @@ def test_fig6_temporary_example_plan():
     p = rt.plan()
     assert p["groups"][0] == [0, 1, 2] and [3] in p["groups"]
     assert p["temporaries"] == [zh] and wh not in p["temporaries"]
+
+
+@pytest.mark.parametrize("per_row,lanes", [(5, 1), (7, 2), (16, 4), (27, 8), (100, 32)])
+def test_spmv_lanes_follow_the_mean_row_length(per_row, lanes):
+    """Rows of 3 or more entries per lane are shared by a power-of-two group
+    of lanes (one warp-cooperative row product, spmv_warp); sparser rows keep
+    one row per lane (spmv_row)."""
+    rt = rt0(tile=512)
+    n = 3000
+    Am = A.CSR.__new__(A.CSR)
+    Am.rt, Am.nrows, Am.ncols, Am.nnz = rt, n, n, per_row * n
+    Am.rowptr = rt.empty((n + 1,), np.int32)
+    Am.col = rt.empty((per_row * n,), np.int32)
+    Am.val = rt.empty((per_row * n,), np.float64)
+    Am.dtype = np.dtype(np.float64)
+    y = Am @ rt.empty((n,))
+    _ = A.dot(y, y)
+    with pytest.raises(B.DfsError):
+        rt.flush()
+    src = rt.kernel_source()
+    if lanes == 1:
+        assert "spmv_row" in src and "spmv_warp" not in src
+    else:
+        assert f"act_, {lanes});" in src
