@@ -341,7 +341,7 @@ void BatchGen::vector_group(int g) {
               o << ");\n";
               cur[akey(t.args.back())] = res;
             } else if (t.op == DFS_OP_SPMV && spre.count(k)) {
-              o << pad << "const " << T(dt) << " " << res << " = " << spre.at(k) << ";\n";
+              o << pad << "const " << T(dt) << " " << res << " = " << spre.at(k) << "_" << l << ";\n";
               cur[akey(t.args[4])] = res;
             } else if (t.op == DFS_OP_SPMV) {
               const Arg& y = t.args[4];
@@ -394,27 +394,46 @@ void BatchGen::vector_group(int g) {
     for (int k = i; k < j; ++k) has_spmv = has_spmv || S.tasks[k].op == DFS_OP_SPMV;
     if (has_spmv) {
       // SpMV rows shared by lanes (spmv_warp, lanes per row from the
-      // instance's descriptor): each warp takes 32 consecutive rows per trip
+      // instance's descriptor).  Elements are dealt to threads as in the
+      // plain loops (vectors of V, then the scalar tail), so fused reductions
+      // sum in the same order; a warp takes 32 consecutive vectors per trip
       o << ind << "  const int lane_ = threadIdx.x & 31;\n";
-      o << ind << "  for (i64 wb = (i64)threadIdx.x - lane_; wb < n; wb += " << BD << ") {\n";
-      o << ind << "    const i64 e = wb + lane_;\n";
-      o << ind << "    const bool act_ = e < n;\n";
-      for (int k = i; k < j; ++k) {
-        const Task& t = S.tasks[k];
-        if (t.op != DFS_OP_SPMV) continue;
-        const Arg& y = t.args[4];
-        const int yb = vslots(t, 4);
-        const int dt = y.dtype;
-        const std::string nm = "sp" + std::to_string(k);
-        o << ind << "    const " << T(dt) << " " << nm << " = spmv_warp<" << T(dt) << ">(" << P_(t.args[0].root) << " + "
-          << base.at(akey(t.args[0])) << ", " << P_(t.args[1].root) << " + " << base.at(akey(t.args[1])) << ", "
-          << P_(t.args[2].root) << " + " << base.at(akey(t.args[2])) << ", " << P_(t.args[3].root) << " + "
-          << base.at(akey(t.args[3])) << ", (" << base.at(akey(y)) << " - D.v[" << yb + 2 << "] + e), act_, (int)D.v["
-          << kslot(t) << "]);\n";
-        spre[k] = nm;
+      auto coop_spmv = [&](int w, const std::string& first, const std::string& pad) {
+        for (int k = i; k < j; ++k) {
+          const Task& t = S.tasks[k];
+          if (t.op != DFS_OP_SPMV) continue;
+          const Arg& y = t.args[4];
+          const int yb = vslots(t, 4);
+          const int dt = y.dtype;
+          for (int l = 0; l < w; ++l)
+            o << pad << "const " << T(dt) << " sp" << k << "_" << l << " = spmv_warp<" << T(dt) << ">("
+              << P_(t.args[0].root) << " + " << base.at(akey(t.args[0])) << ", " << P_(t.args[1].root) << " + "
+              << base.at(akey(t.args[1])) << ", " << P_(t.args[2].root) << " + " << base.at(akey(t.args[2])) << ", "
+              << P_(t.args[3].root) << " + " << base.at(akey(t.args[3])) << ", (" << base.at(akey(y)) << " - D.v["
+              << yb + 2 << "] + " << first << " + " << l << "), act_, (int)D.v[" << kslot(t) << "]);\n";
+          spre[k] = "sp" + std::to_string(k);
+        }
+      };
+      if (V > 1) {
+        o << ind << "  const i64 nv = n / " << V << ";\n";
+        o << ind << "  for (i64 wb = (i64)threadIdx.x - lane_; wb < nv; wb += " << BD << ") {\n";
+        o << ind << "    const i64 v = wb + lane_;\n";
+        o << ind << "    const bool act_ = v < nv;\n";
+        coop_spmv(V, "v * " + std::to_string(V), ind + "    ");
+        o << ind << "    if (act_) {\n";
+        body(V, {"r"}, {"(v) * " + std::to_string(V)}, ind + "      ");
+        o << ind << "    }\n";
+        o << ind << "  }\n";
+        o << ind << "  for (i64 wb = (i64)threadIdx.x - lane_; nv * " << V << " + wb < n; wb += " << BD << ") {\n";
+        o << ind << "    const i64 e = nv * " << V << " + wb + lane_;\n";
+      } else {
+        o << ind << "  for (i64 wb = (i64)threadIdx.x - lane_; wb < n; wb += " << BD << ") {\n";
+        o << ind << "    const i64 e = wb + lane_;\n";
       }
+      o << ind << "    const bool act_ = e < n;\n";
+      coop_spmv(1, "e", ind + "    ");
       o << ind << "    if (act_) {\n";
-      body(1, {"r"}, {"e"}, ind + "      ");
+      body(1, {"t"}, {"e"}, ind + "      ");
       o << ind << "    }\n";
       o << ind << "  }\n";
     }

@@ -255,7 +255,6 @@ std::vector<Nest> Gen::nests_of(int g) {
     n.vec = aligned ? vec : 1;
     for (int t = i; t < j; ++t)
       if (S.tasks[t].op == DFS_OP_SPMV && spmv_k(S.tasks[t]) > 1) n.coop = true;
-    if (n.coop) n.vec = 1;  // lanes of a warp take consecutive rows
     v.push_back(n);
     i = j;
     while (i < G.end && S.tasks[i].scalar()) ++i;
@@ -541,7 +540,7 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
             o << ");\n";
             cur[akey(t.args.back())] = res;
           } else if (t.op == DFS_OP_SPMV && spre.count(i)) {
-            o << pad << "const " << T(dt) << " " << res << " = " << spre.at(i) << ";\n";
+            o << pad << "const " << T(dt) << " " << res << " = " << spre.at(i) << "_" << l << ";\n";
             cur[akey(t.args[4])] = res;
           } else if (t.op == DFS_OP_SPMV) {
             const Arg& y = t.args[4];
@@ -606,30 +605,49 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
   if (flat) o << ind << "  const i64 gs = (i64)gridDim.x * " << BD << ";\n";
   auto slot_off = [&](int u) { return flat ? std::to_string(u) + " * gs" : std::to_string(u * BD); };
   if (n.dims == 1 && n.coop) {
-    // SpMV rows shared by lanes (spmv_warp): each warp takes 32 consecutive
-    // rows per trip, so every lane of a warp runs the same trips
+    // SpMV rows shared by lanes (spmv_warp).  Elements are dealt to threads
+    // exactly as in the plain loops (vectors of V in thread order, then the
+    // scalar tail), so reductions fused here sum in the same order; each trip
+    // a warp takes 32 consecutive vectors, so all its lanes run the same trips
     o << ind << "  const i64 n = ";
     for (int d = 0; d < nd; ++d) o << (d ? " * " : "") << "ext" << d;
     o << ";\n";
     o << ind << "  const int lane_ = threadIdx.x & 31;\n";
-    o << ind << "  for (i64 wb = " << st0 << " - lane_; wb < n; wb += " << stp << ") {\n";
-    o << ind << "    const i64 e = wb + lane_;\n";
-    o << ind << "    const bool act_ = e < n;\n";
-    for (int i = n.first; i < n.last; ++i) {
-      const Task& t = S.tasks[i];
-      if (t.op != DFS_OP_SPMV) continue;
-      const Arg& y = t.args[4];
-      const int dt = y.dtype;
-      const std::string nm = "sp" + std::to_string(i);
-      o << ind << "    const " << T(dt) << " " << nm << " = spmv_warp<" << T(dt) << ">(" << ptr(t.args[0].root) << " + "
-        << base.at(akey(t.args[0])) << ", " << ptr(t.args[1].root) << " + " << base.at(akey(t.args[1])) << ", "
-        << ptr(t.args[2].root) << " + " << base.at(akey(t.args[2])) << ", " << ptr(t.args[3].root) << " + "
-        << base.at(akey(t.args[3])) << ", (" << base.at(akey(y)) << " - " << y.part.vlo[0] << "LL + e), act_, "
-        << spmv_k(t) << ");\n";
-      spre[i] = nm;
+    auto coop_spmv = [&](int w, const std::string& first, const std::string& pad) {
+      for (int i = n.first; i < n.last; ++i) {
+        const Task& t = S.tasks[i];
+        if (t.op != DFS_OP_SPMV) continue;
+        const Arg& y = t.args[4];
+        const int dt = y.dtype;
+        for (int l = 0; l < w; ++l)
+          o << pad << "const " << T(dt) << " sp" << i << "_" << l << " = spmv_warp<" << T(dt) << ">("
+            << ptr(t.args[0].root) << " + " << base.at(akey(t.args[0])) << ", " << ptr(t.args[1].root) << " + "
+            << base.at(akey(t.args[1])) << ", " << ptr(t.args[2].root) << " + " << base.at(akey(t.args[2])) << ", "
+            << ptr(t.args[3].root) << " + " << base.at(akey(t.args[3])) << ", (" << base.at(akey(y)) << " - "
+            << y.part.vlo[0] << "LL + " << first << " + " << l << "), act_, " << spmv_k(t) << ");\n";
+        spre[i] = "sp" + std::to_string(i);
+      }
+    };
+    if (V > 1) {
+      o << ind << "  const i64 nv = n / " << V << ";\n";
+      o << ind << "  for (i64 wb = " << st0 << " - lane_; wb < nv; wb += " << stp << ") {\n";
+      o << ind << "    const i64 v = wb + lane_;\n";
+      o << ind << "    const bool act_ = v < nv;\n";
+      coop_spmv(V, "v * " + std::to_string(V), ind + "    ");
+      o << ind << "    if (act_) {\n";
+      body(V, {"r"}, {"(v) * " + std::to_string(V)}, {""}, {""}, ind + "      ");
+      o << ind << "    }\n";
+      o << ind << "  }\n";
+      o << ind << "  for (i64 wb = " << st0 << " - lane_; nv * " << V << " + wb < n; wb += " << stp << ") {\n";
+      o << ind << "    const i64 e = nv * " << V << " + wb + lane_;\n";
+    } else {
+      o << ind << "  for (i64 wb = " << st0 << " - lane_; wb < n; wb += " << stp << ") {\n";
+      o << ind << "    const i64 e = wb + lane_;\n";
     }
+    o << ind << "    const bool act_ = e < n;\n";
+    coop_spmv(1, "e", ind + "    ");
     o << ind << "    if (act_) {\n";
-    body(1, {"r"}, {"e"}, {""}, {""}, ind + "      ");
+    body(1, {"t"}, {"e"}, {""}, {""}, ind + "      ");
     o << ind << "    }\n";
     o << ind << "  }\n";
   } else if (n.dims == 1) {
