@@ -36,12 +36,13 @@ std::string akey(const Arg& a) { return std::to_string(a.root) + "@" + a.part.ke
 
 class BatchGen {
  public:
-  BatchGen(const LaunchSpec& s, int vec) : S(s), V(vec) {}
+  BatchGen(const LaunchSpec& s, int vec, bool co) : S(s), V(vec), coop(co) {}
   bool run(BatchCode& out, std::string& why);
 
  private:
   const LaunchSpec& S;
   const int V;
+  const bool coop;  // some instance's SpMV shares rows between lanes
   std::ostringstream o;
   BatchCode bc;
   std::map<int64_t, int> ptr_of;          // root -> pointer slot
@@ -391,7 +392,7 @@ void BatchGen::vector_group(int g) {
       }
     };
     bool has_spmv = false;
-    for (int k = i; k < j; ++k) has_spmv = has_spmv || S.tasks[k].op == DFS_OP_SPMV;
+    for (int k = i; k < j; ++k) has_spmv = has_spmv || (coop && S.tasks[k].op == DFS_OP_SPMV);
     if (has_spmv) {
       // SpMV rows shared by lanes (spmv_warp, lanes per row from the
       // instance's descriptor).  Elements are dealt to threads as in the
@@ -582,8 +583,8 @@ bool BatchGen::run(BatchCode& out, std::string& why) {
 
 }  // namespace
 
-bool generate_batch(const LaunchSpec& spec, int vec, BatchCode& out, std::string& why) {
-  BatchGen g(spec, vec);
+bool generate_batch(const LaunchSpec& spec, int vec, bool coop, BatchCode& out, std::string& why) {
+  BatchGen g(spec, vec, coop);
   return g.run(out, why);
 }
 

@@ -899,9 +899,18 @@ int flush_batch(dfs_ctx* c) {
         if ((r.ptr && (uintptr_t)r.ptr % 16) || a.part.tile[0] % vec || a.part.off[0] % vec || a.part.vlo[0] % vec)
           vec = 1;
       }
+  // does some instance's SpMV share rows between lanes?
+  bool lanes = false;
+  for (int i = 0; i < K && !lanes; ++i)
+    for (const Task& t : iw[i])
+      if (t.op == DFS_OP_SPMV) {
+        const NPart& cp = t.args[1].part;
+        const NPart& rp = t.args[0].part;
+        if (spmv_lanes(cp.vhi[0] - cp.vlo[0], rp.vhi[0] - rp.vlo[0] - 1) > 1) lanes = true;
+      }
   // memoised kernel of this structure
   std::string ckey = key0;
-  const int64_t cfgk[] = {vec, c->cfg.block_threads, c->cfg.unroll, c->cfg.debug_skip_arrival};
+  const int64_t cfgk[] = {vec, c->cfg.block_threads, c->cfg.unroll, c->cfg.debug_skip_arrival, lanes ? 1 : 0};
   ckey.append(reinterpret_cast<const char*>(cfgk), sizeof cfgk);
   auto bit = c->bcache.find(ckey);
   dfs_ctx::BatchEntry* be = nullptr;
@@ -912,7 +921,7 @@ int flush_batch(dfs_ctx* c) {
     c->st.plan_misses += 1;
     auto ne = std::make_unique<dfs_ctx::BatchEntry>();
     std::string why;
-    if (!generate_batch(spec, vec, ne->code, why)) return fallback(why);
+    if (!generate_batch(spec, vec, lanes, ne->code, why)) return fallback(why);
     std::string err;
     c->last_source = ne->code.source;
     if (!c->device) {

@@ -215,17 +215,21 @@ struct BatchCode {
 
 // Lanes per row of the warp-cooperative SpMV (spmv_warp) for a CSR matrix
 // of nnz entries over nrows rows: the largest power of two K <= 32 with
-// 3 K <= nnz / nrows, so that every lane of a group sums about three or more
-// entries; 1 (one row per lane) for sparser rows.  A property of the matrix
-// alone, so every path that multiplies by it sums its rows in one order.
+// 16 K <= nnz / nrows, so rows share lanes only from 32 entries on (measured
+// on GB300: 7-entry rows ran 30 % slower on two lanes than on one, 16-entry
+// random rows 7 % faster on four); 1 (one row per lane) below.  A property of
+// the matrix alone, so every path that multiplies by it sums its rows in one
+// order.
 inline int spmv_lanes(int64_t nnz, int64_t nrows) {
   const int64_t avg = nrows > 0 ? nnz / nrows : 0;
   int k = 1;
-  while (k < 32 && 3 * (2 * k) <= avg) k *= 2;
+  while (k < 32 && 16 * (2 * k) <= avg) k *= 2;
   return k;
 }
 
 // Returns false (with a reason) when the launch cannot be batched.
-bool generate_batch(const LaunchSpec& spec, int vec, BatchCode& out, std::string& why);
+// coop: some instance's SpMV shares rows between lanes (spmv_lanes > 1);
+// without it SpMV nests keep one row per lane and the unrolled loops.
+bool generate_batch(const LaunchSpec& spec, int vec, bool coop, BatchCode& out, std::string& why);
 
 }  // namespace dfs

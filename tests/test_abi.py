@@ -226,7 +226,7 @@ def test_spmv_output_temporary_compiles():
             rt.batch_end() if batched else rt.flush()
         assert e.value.code == -2
         assert rt.stats()["batch_fallbacks"] == 0
-        assert "spmv_warp" in rt.kernel_source()    # 16 entries per row: lanes share rows
+        assert "spmv_row" in rt.kernel_source()
 
 
 def test_capture_api_needs_a_device_and_checks_state():
@@ -335,11 +335,11 @@ def test_fig6_temporary_example_plan():
     assert p["temporaries"] == [zh] and wh not in p["temporaries"]
 
 
-@pytest.mark.parametrize("per_row,lanes", [(5, 1), (7, 2), (16, 4), (27, 8), (100, 32)])
+@pytest.mark.parametrize("per_row,lanes", [(5, 1), (16, 1), (31, 1), (32, 2), (100, 4), (700, 32)])
 def test_spmv_lanes_follow_the_mean_row_length(per_row, lanes):
-    """Rows of 3 or more entries per lane are shared by a power-of-two group
-    of lanes (one warp-cooperative row product, spmv_warp); sparser rows keep
-    one row per lane (spmv_row)."""
+    """Rows of 32 or more entries are shared by a power-of-two group of lanes
+    (16 or more entries per lane; one warp-cooperative row product,
+    spmv_warp); shorter rows keep one row per lane (spmv_row)."""
     rt = rt0(tile=512)
     n = 3000
     Am = A.CSR.__new__(A.CSR)

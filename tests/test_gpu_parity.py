@@ -264,6 +264,55 @@ def test_spmv_random_spd(dtype):
     assert np.max(np.abs(y - want)) <= tol * np.max(np.abs(want))
 
 
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_spmv_long_rows_share_lanes(dtype):
+    """Rows of ~90 entries are summed by groups of 4 lanes (spmv_warp): 3000
+    rows over 12 tiles of 256 with a ragged tail, against the oracle."""
+    rp, col, val = inputs.random_spd_csr(3000, seed=7, kmin=30, kmax=60)
+    assert len(col) // 3000 >= 64
+    x = inputs.uniform(8, -1, 1, 3000, dtype)
+    with gpu_runtime("persistent", tile=256) as rt:
+        Am = A.CSR(rt, rp, col, val.astype(dtype))
+        y = (Am @ rt.array(x)).numpy()
+        assert "spmv_warp" in rt.kernel_source() and "act_, 4);" in rt.kernel_source()
+    want = programs.spmv(rp, col, val, x.astype(np.float64))
+    tol = 1e-13 if dtype == np.float64 else 1e-5
+    assert np.max(np.abs(y - want)) <= tol * np.max(np.abs(want))
+
+
+def test_cg_long_rows_fused_unfused_batched_agree():
+    """CG on long-row matrices: fused, unfused and batched (mixed with Poisson
+    problems, whose rows stay one per lane) are bit-identical, and match the
+    oracle to 1e-12."""
+    iters = 12
+    mats = [inputs.random_spd_csr(2500, seed=9, kmin=30, kmax=60), inputs.poisson2d_csr(40),
+            inputs.random_spd_csr(1200, seed=10, kmin=30, kmax=60)]
+    xs = [inputs.uniform(20 + i, -1, 1, len(m[0]) - 1) for i, m in enumerate(mats)]
+
+    def run(mode, batched):
+        with gpu_runtime(mode, tile=256) as rt:
+            probs = []
+            for (rp, col, val), x in zip(mats, xs):
+                Am = A.CSR(rt, rp, col, val)
+                probs.append((Am, W.cg_start_inplace(Am @ rt.array(x))))
+            rt.flush()
+            for _ in range(iters):
+                if batched:
+                    W.batched_cg_iteration(rt, probs)
+                else:
+                    for Am, s in probs:
+                        W.cg_iteration_inplace(Am, s)
+                    rt.flush()
+            assert rt.stats()["batch_fallbacks"] == 0
+            return [s.x.numpy() for _, s in probs]
+    fused, unfused, batched = run("persistent", False), run("unfused", False), run("persistent", True)
+    for i, (rp, col, val) in enumerate(mats):
+        assert np.array_equal(fused[i].view(np.uint64), unfused[i].view(np.uint64)), i
+        assert np.array_equal(fused[i].view(np.uint64), batched[i].view(np.uint64)), i
+        xo, _, _ = programs.cg(rp, col, val, programs.spmv(rp, col, val, xs[i]), iters)
+        assert np.linalg.norm(fused[i] - xo) / np.linalg.norm(xo) < 1e-12, i
+
+
 @pytest.mark.parametrize("mode", ["persistent", "unfused"])
 def test_spmv_output_as_temporary(mode):
     """y = A x dies inside its window (Def. 4): read straight from registers
