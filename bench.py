@@ -259,16 +259,20 @@ class Arm:
             self.step = self._cg
             if graph:
                 # the whole solve (reset + 50 in-place iterations) captured once
-                # after one normally issued iteration, then replayed per step
+                # after one normally issued window, then replayed per step;
+                # iters_per_flush iterations share one window (one launch)
+                ipf = cfg.get("iters_per_flush", 1)
                 self.s = W.cg_start_inplace(self.b)
-                W.cg_iteration_inplace(self.Am, self.s)
+                for _ in range(ipf):
+                    W.cg_iteration_inplace(self.Am, self.s)
                 self.rt.flush()
                 self.rt.capture_begin()
                 W.cg_reset_inplace(self.s, self.b)
                 self.rt.flush()
-                for _ in range(cfg["iters"]):
+                for it in range(cfg["iters"]):
                     W.cg_iteration_inplace(self.Am, self.s)
-                    self.rt.flush()
+                    if (it + 1) % ipf == 0 or it + 1 == cfg["iters"]:
+                        self.rt.flush()
                 self.graph = self.rt.capture_end()
                 self.step = self._cg_graph
         elif workload == "batched":
@@ -576,6 +580,7 @@ def main():
     ap.add_argument("--sweeps", type=int, default=0, help="Jacobi sweeps per step (profiling)")
     for k in ("block", "unroll", "tile", "rows"):
         ap.add_argument(f"--{k}", type=int, default=0, help=f"override the workload's {k} (tuning)")
+    ap.add_argument("--ipf", type=int, default=0, help="CG: iterations per flush window (tuning)")
     ap.add_argument("--no-autotune", action="store_true", help="batched CG: keep the configured tile/launch shape")
     ap.add_argument("--compile-report", action="store_true",
                     help="print the warm-up/compilation cost table instead of the bench line")
@@ -586,6 +591,8 @@ def main():
         configs.JACOBI["N"] = args.jac_n
     if args.sweeps:
         configs.JACOBI["sweeps"] = args.sweeps
+    if args.ipf:
+        configs.CG["iters_per_flush"] = args.ipf
     if args.fp32:
         configs.BATCHED_CG["dtype"] = "f32"
         METRIC["batched"] = (METRIC["batched"][0], "iterations/s", "f32")
@@ -637,7 +644,7 @@ def main():
     cfg = {"bs": configs.BLACK_SCHOLES, "cg": configs.CG, "jacobi": configs.JACOBI,
            "batched": configs.BATCHED_CG}[args.workload]
     base = dict(block=cfg["block"], unroll=cfg["unroll"], sms=sms, cache_dir=cache)
-    for k in ("tile", "tile_max", "min_points"):
+    for k in ("tile", "tile_max", "min_points", "window_size"):
         if k in cfg:
             base[k] = cfg[k]
     if "rows" in cfg:

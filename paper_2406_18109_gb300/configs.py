@@ -12,8 +12,9 @@ BLACK_SCHOLES = dict(n=1 << 26, seed=1, r=0.02, sigma=0.3, tile=16384, block=512
                      inst_per_option=187.0)
 
 # CG: 2-D 5-point Poisson on a 256x256 grid, 50 iterations, FP64 values,
-# int32 indices, x* ~ U[-1,1] (seed 0), b = A x*, x0 = 0
-CG = dict(m=256, iters=50, seed=0, tile=512, block=256, unroll=2)
+# int32 indices, x* ~ U[-1,1] (seed 0), b = A x*, x0 = 0; five iterations
+# share one flush window (one persistent launch) in the captured solve
+CG = dict(m=256, iters=50, seed=0, tile=512, block=256, unroll=2, iters_per_flush=5, window_size=1024)
 
 # Batched CG: 256 independent solves of uneven size (half 2-D Poisson with m
 # log-uniform in [32, 1024], half random diagonally dominant SPD with n
