@@ -23,7 +23,7 @@ CG = dict(m=256, iters=50, seed=0, tile=512, block=256, unroll=2, iters_per_flus
 # for the FP32 variant).  Tiles follow the size-dependent policy (at least two
 # points per problem, at most tile_max elements); the bench autotunes
 # tile_max and the launch shape before capturing.
-BATCHED_CG = dict(count=256, seed=4, iters=100, dtype="f64", tile_max=512, min_points=2, block=256, unroll=2)
+BATCHED_CG = dict(count=256, seed=4, iters=100, dtype="f64", tile_max=2048, min_points=2, block=256, unroll=2)
 
 # Jacobi: Fig. 1 stencil on an 8192x8192 FP32 grid (8190^2 interior),
 # 200 sweeps, interior U[0,1] (seed 2), boundary 1.0

@@ -146,6 +146,38 @@ def test_cg_full_size():
     assert st["plan_hits"] >= cfg["iters"] - 1
 
 
+def test_cg_full_size_as_benchmarked():
+    """The benchmark's launch configuration: the whole 256^2 solve captured
+    in a CUDA graph with five iterations per flush window, replayed."""
+    cfg = configs.CG
+    ipf = cfg["iters_per_flush"]
+    rp, col, val, xs = inputs.cg_inputs(m=cfg["m"], seed=cfg["seed"])
+    with gpu_runtime("persistent", tile=cfg["tile"], block=cfg["block"], unroll=cfg["unroll"],
+                     window_size=cfg["window_size"]) as rt:
+        Am = A.CSR(rt, rp, col, val)
+        b = Am @ rt.array(xs)
+        s = W.cg_start_inplace(b)
+        for _ in range(ipf):
+            W.cg_iteration_inplace(Am, s)
+        rt.flush()
+        rt.capture_begin()
+        W.cg_reset_inplace(s, b)
+        rt.flush()
+        for it in range(cfg["iters"]):
+            W.cg_iteration_inplace(Am, s)
+            if (it + 1) % ipf == 0:
+                rt.flush()
+        g = rt.capture_end()
+        for _ in range(2):
+            rt.graph_launch(g)
+        x = s.x.numpy()
+        launches = rt.stats()["launches"]
+        rt.graph_destroy(g)
+    xo, _, _, _ = _cg_oracle(cfg["m"], cfg["iters"])
+    assert _rel(x, xo) < 1e-12
+    assert launches >= 2 * (1 + cfg["iters"] // ipf)
+
+
 # ------------------------------------------------------------------ Jacobi
 def _jacobi_gpu(mode, grid, sweeps, rows, per_flush=1, **kw):
     with gpu_runtime(mode, rows=rows, **kw) as rt:
