@@ -49,6 +49,7 @@ class BatchGen {
   std::map<int64_t, int> sslot;           // 0-d root -> scalar slot
   std::map<std::string, int> vbase;       // akey -> first v slot (tile, off, vlo, vhi or vlo, vhi)
   std::map<int, int> kbase;               // SpMV task -> slot of its lanes per row
+  int nticket = 0;                        // dynamically dealt phases so far
   std::map<int64_t, bool> produced;       // 0-d root holds a kernel-produced value
   std::map<int64_t, std::string> local;   // 0-d root -> register inside the open scalar phase
   struct Pending { int slot; int64_t root; int dtype; int pslot; };
@@ -194,7 +195,15 @@ void BatchGen::vector_group(int g) {
   o << "    { // group " << g << ": tasks " << G.begin << ".." << G.end - 1 << ", points of every instance\n";
   o << "      const i64* pf = P.prefix + " << ps << "LL * (NI + 1);\n";
   o << "      const i64 tot = pf[NI];\n";
-  o << "      for (i64 gp = blockIdx.x; gp < tot; gp += gridDim.x) {\n";
+  // points are dealt dynamically (one ticket counter per phase, up to
+  // kTickets phases): uneven points finish their phase together
+  if (nticket < 16) {
+    const int q = nticket++;
+    o << "      for (i64 gp = take_ticket(ctl, " << q << ", &s_ticket); gp < tot; gp = take_ticket(ctl, " << q
+      << ", &s_ticket)) {\n";
+  } else {
+    o << "      for (i64 gp = blockIdx.x; gp < tot; gp += gridDim.x) {\n";
+  }
   o << "        const i64 inst = find_inst(pf, NI, gp);\n";
   o << "        const i64 q0 = gp - pf[inst];\n";
   o << "        const Inst& D = P.insts[inst];\n";
@@ -506,6 +515,7 @@ bool BatchGen::run(BatchCode& out, std::string& why) {
   for (const LaunchRoot& r : S.roots) produced[r.root] = false;
 
   o << "  __shared__ double red_buf[" << S.block / 32 << "];\n";
+  o << "  __shared__ i64 s_ticket;\n";
   o << "  Ctl* ctl = P.ctl;\n  const i64 NI = P.ninst;\n";
   o << "  do {\n";
   bool in_scalar = false, first = true;

@@ -170,12 +170,14 @@ __device__ __forceinline__ T spmv_warp(const int* __restrict__ rowptr, const int
 
 // ----------------------------------------------------------- control block
 // One per context, zero-initialised; every kernel leaves it zeroed on exit.
+constexpr int kTickets = 16;
 struct Ctl {
   u32 bar_arrive;   // grid-barrier arrivals (monotone within a launch)
   u32 exit_arrive;  // CTAs that finished the launch
   int err;          // first device error (0 = none)
   int err_where;    // barrier index that timed out
   u64 pad[2];
+  u64 ticket[kTickets];  // work-queue counters, one per dynamically dealt phase
 };
 
 __device__ __forceinline__ u64 globaltimer_ns() {
@@ -246,8 +248,20 @@ __device__ __forceinline__ void ctl_reset(Ctl* ctl) {
   if (threadIdx.x == 0) {
     ctl->bar_arrive = 0;
     ctl->exit_arrive = 0;
+    for (int i = 0; i < kTickets; ++i) ctl->ticket[i] = 0;
     __threadfence();
   }
+}
+
+// Next point of a dynamically dealt phase: thread 0 takes a ticket from the
+// phase's counter and the block reads it.  Which CTA runs a point does not
+// change any result (reductions keep one partial per point).
+__device__ __forceinline__ i64 take_ticket(Ctl* ctl, int q, i64* s_ticket) {
+  if (threadIdx.x == 0) *s_ticket = (i64)atomicAdd((unsigned long long*)&ctl->ticket[q], 1ull);
+  __syncthreads();
+  const i64 t = *s_ticket;
+  __syncthreads();
+  return t;
 }
 
 // --------------------------------------------------------------- reductions

@@ -102,6 +102,7 @@ struct Ctl {
   int32_t err;
   int32_t err_where;
   uint64_t pad[2];
+  uint64_t ticket[16];
 };
 
 // ------------------------------------------------------------------ analysis
