@@ -321,7 +321,7 @@ class Arm:
                 import tempfile
                 from paper_2406_18109_gb300 import autotune as AT
                 space = {"tile_max": [512, 1024, 2048, 4096, 8192], "block": [128, 256, 512], "unroll": [1, 2],
-                         "ctas_per_sm": [0, 2]}
+                         "ctas_per_sm": [0, 5, 6]}
                 best, trials = AT.tune(rt, one_iteration, space=space, warmup=1, reps=3,
                                        key=f"batched-cg-{cfg['count']}-{cfg['seed']}-{cfg['dtype']}",
                                        cache_path=os.path.join(tempfile.gettempdir(), "dfs_autotune.json"),

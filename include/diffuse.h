@@ -143,7 +143,9 @@ typedef struct {
   int32_t window_size;       /* tasks buffered before the window is analysed (>= 1) */
   void *stream;              /* cudaStream_t to use; NULL = the context creates one */
   int32_t block_threads;     /* threads per CTA: 128, 256, 512 or 1024 (0 = 256) */
-  int32_t ctas_per_sm;       /* CTAs per SM for grid sizing (0 = occupancy limit) */
+  int32_t ctas_per_sm;       /* CTAs per SM (0 = as many as fit): sizes the grid and, when
+                              * > 0, is the kernels' minimum resident CTAs per SM, which
+                              * caps their registers per thread */
   int32_t unroll;            /* vectors per thread per loop trip, 1..8 (0 = 2) */
   double barrier_timeout_s;  /* grid-barrier spin limit in seconds (0 = 2.0) */
   const char *cache_dir;     /* on-disk cubin cache directory, or NULL */
@@ -336,7 +338,8 @@ int dfs_read_scalars(dfs_ctx *ctx, int32_t n, const dfs_store *stores, double *h
 /*
  * dfs_set_launch_config -- changes the launch parameters of a live context
  * (block_threads: 128, 256, 512 or 1024; unroll: 1..8; ctas_per_sm: 0 =
- * as many as fit, else at most that many), as an autotuner does between
+ * as many as fit, else that many, with registers capped to fit them; see
+ * dfs_config), as an autotuner does between
  * timed trials.  Flushes the pending window first.  Kernels already
  * generated for other parameters stay cached.  Block size changes the
  * per-thread order of reductions inside a point, so reduction results may

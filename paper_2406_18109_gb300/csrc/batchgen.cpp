@@ -584,7 +584,7 @@ bool BatchGen::run(BatchCode& out, std::string& why) {
   char nm[64];
   snprintf(nm, sizeof nm, "dfs_b%016zx", std::hash<std::string>{}(body));
   bc.name = nm;
-  src << "extern \"C\" __global__ void __launch_bounds__(" << S.block << ") " << bc.name
+  src << "extern \"C\" __global__ void __launch_bounds__(" << S.block << (S.min_blocks > 0 ? ", " + std::to_string(S.min_blocks) : std::string()) << ") " << bc.name
       << "(const __grid_constant__ BP P) {\n" << body << "}\n";
   bc.source = src.str();
   out = bc;

@@ -816,7 +816,7 @@ KernelCode Gen::run() {
   char nm[64];
   snprintf(nm, sizeof nm, "dfs_k%016zx", h);
   kc.name = nm;
-  src << "extern \"C\" __global__ void __launch_bounds__(" << S.block << ") " << kc.name
+  src << "extern \"C\" __global__ void __launch_bounds__(" << S.block << (S.min_blocks > 0 ? ", " + std::to_string(S.min_blocks) : std::string()) << ") " << kc.name
       << "(const __grid_constant__ Params P) {\n"
       << body_s << "}\n";
   kc.source = src.str();

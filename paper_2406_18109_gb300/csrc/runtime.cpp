@@ -395,6 +395,7 @@ LaunchSpec make_spec(dfs_ctx* c, const std::vector<Task>& w, const std::map<int6
   const int t0 = P.groups[g0].begin, t1 = P.groups[g1 - 1].end;
   LaunchSpec spec;
   spec.block = c->cfg.block_threads;
+  spec.min_blocks = c->cfg.ctas_per_sm;
   spec.unroll = c->cfg.unroll;
   spec.persistent = (g1 - g0) > 1;
   spec.debug_skip = c->cfg.debug_skip_arrival;
@@ -910,7 +911,7 @@ int flush_batch(dfs_ctx* c) {
       }
   // memoised kernel of this structure
   std::string ckey = key0;
-  const int64_t cfgk[] = {vec, c->cfg.block_threads, c->cfg.unroll, c->cfg.debug_skip_arrival, lanes ? 1 : 0};
+  const int64_t cfgk[] = {vec, c->cfg.block_threads, c->cfg.unroll, c->cfg.debug_skip_arrival, lanes ? 1 : 0, c->cfg.ctas_per_sm};
   ckey.append(reinterpret_cast<const char*>(cfgk), sizeof cfgk);
   auto bit = c->bcache.find(ckey);
   dfs_ctx::BatchEntry* be = nullptr;

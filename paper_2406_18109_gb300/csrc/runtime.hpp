@@ -170,6 +170,7 @@ struct LaunchSpec {
   int unroll = 2;
   bool persistent = false;
   int debug_skip = 0;  // test hook: CTA 0 withholds its arrival at this barrier
+  int min_blocks = 0;  // > 0: __launch_bounds__ minimum resident CTAs per SM (caps registers)
 };
 
 struct KernelCode {
