@@ -275,6 +275,13 @@ class Arm:
                         self.rt.flush()
                 self.graph = self.rt.capture_end()
                 self.step = self._cg_graph
+                if e2e:
+                    # end to end: b uploaded from pinned host memory, x read back, every step
+                    pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+                    self.hb = pin(self.b.numpy())
+                    self.hx = pin(np.empty(self.hb.shape, self.hb.dtype))
+                    self.h2d = self.d2h = self.hb.nbytes
+                    self.e2e_io = ([(self.b, self.hb)], [(self.s.x, self.hx)])
         elif workload == "batched":
             cfg = self.cfg = configs.BATCHED_CG
             dt = np.float64 if cfg["dtype"] == "f64" else np.float32
@@ -337,6 +344,16 @@ class Arm:
             self.graph = rt.capture_end()
             self.units = cfg["count"] * cfg["iters"]
             self.step = self._cg_graph
+            if e2e:
+                pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+                ups, downs = [], []
+                for _, s, b in self.probs:
+                    hb = pin(b.numpy())
+                    ups.append((b, hb))
+                    downs.append((s.x, pin(np.empty(hb.shape, hb.dtype))))
+                self.h2d = sum(h.nbytes for _, h in ups)
+                self.d2h = sum(h.nbytes for _, h in downs)
+                self.e2e_io = (ups, downs)
         else:
             cfg = self.cfg = configs.JACOBI
             grid = inputs.jacobi_grid(cfg["N"], seed=cfg["seed"])
@@ -344,6 +361,11 @@ class Arm:
             self.views = W.jacobi_views(self.g)
             self.units = cfg["sweeps"]
             self.step = self._jacobi
+            if e2e:
+                pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+                hg = pin(grid)
+                self.h2d = self.d2h = hg.nbytes
+                self.e2e_io = ([(self.g, hg)], [(self.g, pin(np.empty_like(grid)))])
         self.rt.sync()
         self.keep = None
 
@@ -369,15 +391,25 @@ class Arm:
         self.keep = st
 
     def _cg_graph(self):
+        if self.e2e:
+            for dev, host in self.e2e_io[0]:
+                dev.write(host)
         self.rt.graph_launch(self.graph)
+        if self.e2e:
+            for dev, host in self.e2e_io[1]:
+                dev.read_into(host)
 
     def _jacobi(self):
+        if self.e2e:
+            self.g.write(self.e2e_io[0][0][1])
         per = self.cfg["sweeps_per_flush"]
         for s in range(self.cfg["sweeps"]):
             self.W.jacobi_sweep(self.views)
             if (s + 1) % per == 0:
                 self.rt.flush()
         self.rt.flush()
+        if self.e2e:
+            self.g.read_into(self.e2e_io[1][0][1])
 
     def run(self, steps, warmup):
         torch, stream, rt = self.torch, self.stream, self.rt
@@ -708,10 +740,17 @@ def main():
                 "fused": {"value": nf["units"] / (nf["ms"] / 1e3), "ms_per_step": nf["ms"] / k2},
                 "unfused": {"value": nu["units"] / (nu["ms"] / 1e3), "ms_per_step": nu["ms"] / k2},
                 "note": "each iteration issued from Python (11 tasks + flush); host-bound"}
-        if args.workload == "bs":
-            e = arm(dict(base, fusion=True, launch="persistent"), k2, 2, e2e=True)
+    if not args.quick:
+        # end to end through the public API: inputs from pinned host memory
+        # and results back to it inside every timed step
+        k3 = max(2, args.steps // 4)
+        ea = Arm(args.workload, dict(base, fusion=True, launch="persistent"), torch, stream, e2e=True, graph=graph)
+        try:
+            e = ea.run(k3, 2)
             extra["e2e"] = {"value": e["units"] / (e["ms"] / 1e3), "unit": unit,
-                            "h2d_bytes_per_step": 3 * cfg["n"] * 4, "d2h_bytes_per_step": 2 * cfg["n"] * 4}
+                            "h2d_bytes_per_step": ea.h2d, "d2h_bytes_per_step": ea.d2h}
+        finally:
+            ea.close()
 
     peaks = load_peaks()
     if args.workload == "bs":
@@ -719,7 +758,7 @@ def main():
     elif args.workload == "cg":
         m = cfg["m"]
         nn, nnz = m * m, 5 * m * m - 4 * m
-        alg_bytes = 12 * nnz + 4 * (nn + 1) + 96 * nn     # one CG iteration (one launch)
+        alg_bytes = 12 * nnz + 4 * (nn + 1) + 96 * nn     # one CG iteration
     elif args.workload == "batched":
         nnz, rows = batch_sizes
         esz = 8 if cfg["dtype"] == "f64" else 4
