@@ -787,8 +787,10 @@ def main():
         sm_max = clk.get("sm_max_mhz") or 2070.0
         peak_ti = sms * 4 * 32 * sm_max * 1e6 / 1e12
         ach_ti = cfg["inst_per_option"] * cfg["n"] / (kern_ms / 1e3) / 1e12 if kern_ms > 0 else 0.0
+        # measured DRAM traffic of this kernel at the default size (ncu), else unknown
+        traffic = cfg["dram_bytes_per_launch"] if cfg["n"] == 1 << 26 else None
         roofline = {"bound": "alu", "achieved": ach_ti, "peak": peak_ti, "unit": "T thread-inst/s",
-                    "frac": ach_ti / peak_ti, "traffic": None,
+                    "frac": ach_ti / peak_ti, "traffic": traffic,
                     "peak_source": f"derived: {sms} SMs x 4 SMSPs x 32 lanes x {sm_max:.0f} MHz",
                     "inst_per_option": cfg["inst_per_option"], "kernel": fused["dominant"],
                     "kernel_ms": kern_ms, "launches": fused["dominant_launches"],

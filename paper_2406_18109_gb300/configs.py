@@ -9,7 +9,10 @@ BLACK_SCHOLES = dict(n=1 << 26, seed=1, r=0.02, sigma=0.3, tile=16384, block=512
                      # thread instructions per option of the fused kernel (ncu
                      # smsp__inst_executed x 32 / options); the kernel is bound
                      # by instruction issue, see profiles/
-                     inst_per_option=187.0)
+                     inst_per_option=187.0,
+                     # DRAM bytes (read + write) of one launch at n = 2^26, from
+                     # an ncu capture of this kernel (profiles/)
+                     dram_bytes_per_launch=1307.45e6)
 
 # CG: 2-D 5-point Poisson on a 256x256 grid, 50 iterations, FP64 values,
 # int32 indices, x* ~ U[-1,1] (seed 0), b = A x*, x0 = 0; five iterations
