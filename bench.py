@@ -361,6 +361,20 @@ class Arm:
             self.views = W.jacobi_views(self.g)
             self.units = cfg["sweeps"]
             self.step = self._jacobi
+            if autotune:
+                # rows per point and launch shape of the sweep, by timing it
+                import tempfile
+                from paper_2406_18109_gb300 import autotune as AT
+                rt = self.rt
+
+                def sweep():
+                    W.jacobi_sweep(self.views)
+                    rt.flush()
+                space = {"rows": [8, 16, 32], "block": [256, 512], "unroll": [4, 8], "ctas_per_sm": [0, 4, 6]}
+                best, trials = AT.tune(rt, sweep, space=space, warmup=1, reps=3, key=f"jacobi-{cfg['N']}",
+                                       cache_path=os.path.join(tempfile.gettempdir(), "dfs_autotune.json"),
+                                       gpu=torch.cuda.get_device_name())
+                self.tuned = {"config": best, "trials": [{"config": c, "ms_per_sweep": m} for c, m in trials]}
             if e2e:
                 pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
                 hg = pin(grid)
@@ -613,7 +627,8 @@ def main():
     for k in ("block", "unroll", "tile", "rows"):
         ap.add_argument(f"--{k}", type=int, default=0, help=f"override the workload's {k} (tuning)")
     ap.add_argument("--ipf", type=int, default=0, help="CG: iterations per flush window (tuning)")
-    ap.add_argument("--no-autotune", action="store_true", help="batched CG: keep the configured tile/launch shape")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batched CG / Jacobi: keep the configured tiling and launch shape")
     ap.add_argument("--compile-report", action="store_true",
                     help="print the warm-up/compilation cost table instead of the bench line")
     args = ap.parse_args()
@@ -697,7 +712,7 @@ def main():
             a.close()
 
     fused_arm = Arm(args.workload, dict(base, fusion=True, launch="persistent"), torch, stream, graph=graph,
-                    autotune=args.workload == "batched" and not args.no_autotune)
+                    autotune=args.workload in ("batched", "jacobi") and not args.no_autotune)
     batch_sizes = (fused_arm.nnz, fused_arm.rows) if args.workload == "batched" else None
     tuned = fused_arm.tuned
     if tuned:

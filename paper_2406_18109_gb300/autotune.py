@@ -25,8 +25,9 @@ import time
 from .binding import DfsError
 
 # search order; a space names any subset.  tile: a fixed tile for every
-# vector; tile_max: the cap of the size-dependent tile policy (tile None)
-PARAMS = ("tile", "tile_max", "block", "unroll", "ctas_per_sm")
+# vector; tile_max: the cap of the size-dependent tile policy (tile None);
+# rows: rows per point of 2-D and 3-D arrays
+PARAMS = ("tile", "tile_max", "rows", "block", "unroll", "ctas_per_sm")
 DEFAULT_SPACE = {"tile": [256, 512, 1024, 2048], "block": [128, 256, 512], "unroll": [1, 2, 4],
                  "ctas_per_sm": [0, 1, 2]}
 
@@ -36,8 +37,9 @@ def current(rt, params=("tile", "block", "unroll", "ctas_per_sm")) -> dict:
 
 
 def apply(rt, cfg: dict) -> None:
-    if ("tile" in cfg and cfg["tile"] != rt.tile) or ("tile_max" in cfg and cfg["tile_max"] != rt.tile_max):
-        rt.set_tiling(cfg.get("tile", rt.tile), rt.rows, tile_max=cfg.get("tile_max"))
+    if (("tile" in cfg and cfg["tile"] != rt.tile) or ("tile_max" in cfg and cfg["tile_max"] != rt.tile_max)
+            or ("rows" in cfg and cfg["rows"] != rt.rows)):
+        rt.set_tiling(cfg.get("tile", rt.tile), cfg.get("rows", rt.rows), tile_max=cfg.get("tile_max"))
     rt.set_launch(cfg.get("block", rt.block), cfg.get("unroll", rt.unroll), cfg.get("ctas_per_sm", rt.ctas_per_sm))
 
 

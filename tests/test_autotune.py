@@ -8,8 +8,9 @@ from paper_2406_18109_gb300.binding import DfsError
 
 class FakeRuntime:
     def __init__(self, cost, fallback=lambda cfg: False, fails=lambda cfg: False):
-        self.tile, self.rows, self.block, self.unroll, self.ctas_per_sm = 512, None, 256, 2, 0
+        self.tile, self.block, self.unroll, self.ctas_per_sm = 512, 256, 2, 0
         self.tile_max = 16384
+        self.rows = 16
         self.cost, self.fallback, self.fails = cost, fallback, fails
         self.ms = 0.0
         self.fallbacks = 0
@@ -89,3 +90,9 @@ def test_subset_space_and_tile_policy_cap():
                                                                "block": [128, 256]})
     assert best == {"tile_max": 4096, "block": 128} and len(trials) == 1 + 4 + 1
     assert rt.tile is None and rt.tile_max == 4096
+
+
+def test_rows_parameter():
+    rt = FakeRuntime(lambda cfg: abs(cfg["rows"] - 32) + (cfg["unroll"] != 8))
+    best, _ = autotune.tune(rt, rt.step, space={"rows": [8, 16, 32, 64], "unroll": [4, 8]})
+    assert best == {"rows": 32, "unroll": 8} and rt.rows == 32
