@@ -176,7 +176,11 @@ int dfs_shutdown(dfs_ctx *ctx);
 
 /* Creates a store of `ndim` (0..3) dimensions.  Device memory is owned by the
  * library and allocated lazily, at the first flush that must materialise the
- * store; a store that the fusion pass proves temporary is never allocated. */
+ * store; a store that the fusion pass proves temporary is never allocated.
+ * Stores of 2 or 3 dimensions are pitched in device memory: each row (run of
+ * the last dimension) starts on a 16-byte boundary, so row-wise kernels use
+ * 16-byte accesses whatever the row length.  Host copies (dfs_store_write,
+ * dfs_store_read) take and give densely packed rows. */
 int dfs_store_create(dfs_ctx *ctx, int32_t dtype, int32_t ndim, const int64_t *shape,
                      dfs_store *out);
 
@@ -204,7 +208,9 @@ int dfs_store_write(dfs_ctx *ctx, dfs_store s, const void *host_src, size_t byte
 int dfs_store_read(dfs_ctx *ctx, dfs_store s, void *host_dst, size_t bytes);
 
 /* Flushes, materialises the store's root and returns the device address of
- * the store's first element (for interoperation with other CUDA code). */
+ * the store's first element (for interoperation with other CUDA code).  Rows
+ * of a created 2-D or 3-D store are pitched (see dfs_store_create): the row
+ * pitch is the row length rounded up to 16 bytes. */
 int dfs_store_device_ptr(dfs_ctx *ctx, dfs_store s, void **out);
 
 /* The None partition: every point of the launch domain sees the whole store. */

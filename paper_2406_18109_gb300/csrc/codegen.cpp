@@ -89,6 +89,12 @@ struct Nest {
   int vec;          // elements per vector access
   int rank = 1;     // rank of the iteration space (rows of a 3-D space are (plane, row) pairs)
   bool coop = false;  // an SpMV of the nest uses several lanes per row (spmv_warp)
+  // realigned rows: vectors in the frame of the written views (`head` scalar
+  // columns first); a read view whose column origin is `shift` elements past
+  // that frame is loaded as two aligned vectors
+  bool realign = false;
+  int head = 0;
+  std::map<std::string, int> shift;
 };
 
 // Lanes per row of an SpMV task's matrix (col and rowptr extents).
@@ -127,6 +133,7 @@ class Gen {
   void emit_vector_group(int g);
   void emit_nest(int g, const Nest& n, const std::string& red_pt, bool flat);
   void emit_finalise(const char* indent);
+  void realign(Nest& n, int vec);
   std::vector<Nest> nests_of(int g);
   std::string imm_expr(int task, int arg, int dt);
 };
@@ -178,6 +185,48 @@ void Gen::emit_prologue() {
   }
 }
 
+// Row nests whose views start at different column offsets (the shifted
+// views of a stencil) still use vector accesses when every root row is a
+// whole number of aligned vectors and no reduction's summation order would
+// change: the nest iterates in the vector frame of its written views.
+void Gen::realign(Nest& n, int vec) {
+  int mw = -1, mr = -1;
+  size_t esz = 0;
+  std::map<std::string, int> phase;
+  for (int t = n.first; t < n.last; ++t) {
+    const Task& tk = S.tasks[t];
+    if (tk.scalar()) continue;
+    if (is_reduction(tk.op) || tk.op == DFS_OP_SPMV) return;
+    for (size_t ai = 0; ai < tk.args.size(); ++ai) {
+      const Arg& a = tk.args[ai];
+      if (a.imm || a.nd == 0) continue;
+      const LaunchRoot& r = R(a.root);
+      if (r.temp) continue;  // lives in registers
+      if (esz && esz != dtype_size(a.dtype)) return;
+      esz = dtype_size(a.dtype);
+      const int cd = a.nd - 1;
+      if (!r.aligned16 || a.part.kind != 1 || tk.dom[a.part.proj[cd]] != 1) return;
+      for (int d = 0; d < cd; ++d)
+        if (r.stride[d] % vec) return;
+      const int64_t c0 = std::max(a.part.off[cd], a.part.vlo[cd]);
+      const int ph = (int)(((c0 % vec) + vec) % vec);
+      phase[akey(a)] = ph;
+      const bool out = is_elementwise(tk.op) && ai + 1 == tk.args.size();
+      if (out) {
+        if (mw >= 0 && mw != ph) return;
+        mw = ph;
+      } else if (mr < 0) {
+        mr = ph;
+      }
+    }
+  }
+  if (!esz || (int)(16 / esz) != vec) return;
+  n.realign = true;
+  n.vec = vec;
+  n.head = (vec - (mw >= 0 ? mw : std::max(mr, 0))) % vec;
+  for (const auto& kv : phase) n.shift[kv.first] = (kv.second + n.head) % vec;
+}
+
 std::vector<Nest> Gen::nests_of(int g) {
   const Group& G = S.groups[g];
   std::vector<Nest> v;
@@ -206,7 +255,7 @@ std::vector<Nest> Gen::nests_of(int g) {
           if (a.part.kind != 1) flat = false;
           for (int d = 1; d < nd && flat; ++d)
             if (a.part.vlo[d] != 0 || a.part.vhi[d] != r.shape[d] || a.part.off[d] > 0 ||
-                a.part.tile[d] < r.shape[d])
+                a.part.tile[d] < r.shape[d] || r.stride[d - 1] != r.shape[d] * r.stride[d])  // no row padding
               flat = false;
         }
     }
@@ -253,6 +302,7 @@ std::vector<Nest> Gen::nests_of(int g) {
       }
     }
     n.vec = aligned ? vec : 1;
+    if (!aligned && vec > 1 && n.dims == 2) realign(n, vec);
     for (int t = i; t < j; ++t)
       if (S.tasks[t].op == DFS_OP_SPMV && spmv_k(S.tasks[t]) > 1) n.coop = true;
     v.push_back(n);
@@ -504,7 +554,14 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
         const Arg& a = *rd.a;
         const std::string ad = addr(a, eflat[s], erow[s], ecol[s]);
         const std::string v = rd.var + "_" + slots[s];
-        if (w == 4 && a.dtype == DFS_F32) {
+        const int sh = (w > 1 && n.realign) ? n.shift.at(rd.key) : 0;
+        if (sh && w == 4 && a.dtype == DFS_F32) {
+          o << pad << "const f32x4 " << v << " = " << (rd.ro ? "ld4sro<" : "ld4s<") << sh << ">(" << ad << " - " << sh
+            << ");\n";
+        } else if (sh && w == 2 && a.dtype == DFS_F64) {
+          o << pad << "const f64x2 " << v << " = " << (rd.ro ? "ld2sro<" : "ld2s<") << sh << ">(" << ad << " - " << sh
+            << ");\n";
+        } else if (w == 4 && a.dtype == DFS_F32) {
           o << pad << "const f32x4 " << v << " = " << (rd.ro ? "ld4ro(" : "ld4(") << ad << ");\n";
         } else if (w == 2 && a.dtype == DFS_F64) {
           o << pad << "const f64x2 " << v << " = " << (rd.ro ? "ld2ro(" : "ld2(") << ad << ");\n";
@@ -685,10 +742,12 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
     o << ind << "  }\n";
   } else if (flat) {
     // a rectangle of nrows rows x ncols columns swept as one range of
-    // (row, vector) cells with a grid stride
+    // (row, vector) cells with a grid stride; realigned rows start their
+    // vectors after `hd` scalar columns and end with a scalar tail
     o << ind << "  const i64 nrows = " << (n.rank == 3 ? "ext0 * ext1" : "ext0") << ";\n";
     o << ind << "  const i64 ncols = " << (n.rank == 3 ? "ext2" : "ext1") << ";\n";
-    o << ind << "  const i64 nvr = ncols / " << V << ";\n";
+    o << ind << "  const i64 hd = " << (n.realign ? "min((i64)" + std::to_string(n.head) + ", ncols)" : "0") << ";\n";
+    o << ind << "  const i64 nvr = (ncols - hd) / " << V << ";\n";
     o << ind << "  const i64 ncell = nrows * nvr;\n";
     o << ind << "  i64 c = " << st0 << ";\n";
     // 32-bit division by the constant row length when the range allows it
@@ -698,7 +757,7 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
         o << ind << "      const i64 i" << sfx << " = (i64)((u32)(" << cv << ") / (u32)nvr);\n";
       else
         o << ind << "      const i64 i" << sfx << " = (" << cv << ") / nvr;\n";
-      o << ind << "      const i64 j" << sfx << " = ((" << cv << ") - i" << sfx << " * nvr) * " << V << ";\n";
+      o << ind << "      const i64 j" << sfx << " = hd + ((" << cv << ") - i" << sfx << " * nvr) * " << V << ";\n";
     };
     if (U > 1) {
       o << ind << "  for (; c + " << slot_off(U - 1) << " < ncell; c += " << U << " * gs) {\n";
@@ -717,12 +776,34 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
     cell("c", "r");
     body(V, {"r"}, {""}, {"ir"}, {"jr"}, ind + "      ");
     o << ind << "  }\n";
+    if (n.realign) {
+      // the scalar head and tail columns of every row
+      o << ind << "  const i64 nrem = ncols - nvr * " << V << ";\n";
+      o << ind << "  if (nrem > 0) {\n";
+      o << ind << "    for (i64 c2 = " << st0 << "; c2 < nrows * nrem; c2 += gs) {\n";
+      o << ind << "      const i64 is = c2 / nrem;\n";
+      o << ind << "      const i64 ks = c2 - is * nrem;\n";
+      o << ind << "      const i64 js = ks < hd ? ks : hd + nvr * " << V << " + (ks - hd);\n";
+      body(1, {"s"}, {""}, {"is"}, {"js"}, ind + "      ");
+      o << ind << "    }\n";
+      o << ind << "  }\n";
+    }
   } else {
     // rows: each row of ncols elements is swept by the whole block
     o << ind << "  const i64 nrows = " << (n.rank == 3 ? "ext0 * ext1" : "ext0") << ";\n";
     o << ind << "  const i64 ncols = " << (n.rank == 3 ? "ext2" : "ext1") << ";\n";
     o << ind << "  for (i64 i = 0; i < nrows; ++i) {\n";
-    if (V > 1) {
+    if (V > 1 && n.realign) {
+      o << ind << "    const i64 hd = min((i64)" << n.head << ", ncols);\n";
+      o << ind << "    const i64 nv = (ncols - hd) / " << V << ";\n";
+      o << ind << "    for (i64 v = threadIdx.x; v < nv; v += " << BD << ") {\n";
+      body(V, {"r"}, {""}, {"i"}, {"hd + v * " + std::to_string(V)}, ind + "      ");
+      o << ind << "    }\n";
+      o << ind << "    for (i64 k = threadIdx.x; k < ncols - nv * " << V << "; k += " << BD << ") {\n";
+      o << ind << "      const i64 js = k < hd ? k : hd + nv * " << V << " + (k - hd);\n";
+      body(1, {"t"}, {""}, {"i"}, {"js"}, ind + "      ");
+      o << ind << "    }\n";
+    } else if (V > 1) {
       o << ind << "    const i64 nv = ncols / " << V << ";\n";
       o << ind << "    for (i64 v = threadIdx.x; v < nv; v += " << BD << ") {\n";
       body(V, {"r"}, {""}, {"i"}, {"v * " + std::to_string(V)}, ind + "      ");

@@ -108,6 +108,39 @@ __device__ __forceinline__ f64x2 ld2cs(const double* p) {
   double2 t = __ldcs(reinterpret_cast<const double2*>(p));
   f64x2 r; r.v[0] = t.x; r.v[1] = t.y; return r;
 }
+// Vectors that start S elements past a 16-byte boundary: p is that
+// boundary; two aligned vector loads, the wanted elements picked in
+// registers.  Used for views whose column origin is not vector-aligned (the
+// shifted views of a stencil) when every root row is a whole number of
+// vectors, so both aligned loads stay inside the row of the used elements.
+template <int S> __device__ __forceinline__ f32x4 ld4s(const float* p) {
+  const f32x4 a = ld4(p), b = ld4(p + 4);
+  f32x4 r;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) r.v[k] = (S + k < 4) ? a.v[S + k] : b.v[S + k - 4];
+  return r;
+}
+template <int S> __device__ __forceinline__ f32x4 ld4sro(const float* p) {
+  const f32x4 a = ld4ro(p), b = ld4ro(p + 4);
+  f32x4 r;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) r.v[k] = (S + k < 4) ? a.v[S + k] : b.v[S + k - 4];
+  return r;
+}
+template <int S> __device__ __forceinline__ f64x2 ld2s(const double* p) {
+  const f64x2 a = ld2(p), b = ld2(p + 2);
+  f64x2 r;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) r.v[k] = (S + k < 2) ? a.v[S + k] : b.v[S + k - 2];
+  return r;
+}
+template <int S> __device__ __forceinline__ f64x2 ld2sro(const double* p) {
+  const f64x2 a = ld2ro(p), b = ld2ro(p + 2);
+  f64x2 r;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) r.v[k] = (S + k < 2) ? a.v[S + k] : b.v[S + k - 2];
+  return r;
+}
 __device__ __forceinline__ void st2(double* p, const f64x2& r) {
   *reinterpret_cast<double2*>(p) = make_double2(r.v[0], r.v[1]);
 }

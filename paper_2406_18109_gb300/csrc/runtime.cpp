@@ -1232,7 +1232,12 @@ int dfs_shutdown(dfs_ctx* c) {
   }
 }
 
-static int new_store(dfs_ctx* c, int32_t dtype, int32_t ndim, const int64_t* shape, dfs_store* out) {
+// Library-owned roots of rank >= 2 are pitched: every row (last dimension)
+// starts on a 16-byte boundary, so row nests can use vector accesses even
+// when the row length is not a multiple of the vector; wrapped memory keeps
+// the caller's contiguous layout.
+static int new_store(dfs_ctx* c, int32_t dtype, int32_t ndim, const int64_t* shape, dfs_store* out,
+                     bool pitched) {
   if (!c || !out) return DFS_ERR_INVALID;
   if (dtype < DFS_F32 || dtype > DFS_I64) return fail(c, DFS_ERR_INVALID, "bad dtype");
   if (ndim < 0 || ndim > MAXD || (ndim > 0 && !shape)) return fail(c, DFS_ERR_INVALID, "bad ndim");
@@ -1249,8 +1254,12 @@ static int new_store(dfs_ctx* c, int32_t dtype, int32_t ndim, const int64_t* sha
   for (int d = ndim - 1; d >= 0; --d) {
     r.stride[d] = s;
     s *= r.shape[d];
+    if (pitched && d == ndim - 1 && ndim >= 2) {
+      const int64_t v = (int64_t)(16 / dtype_size(dtype));
+      s = (r.shape[d] + v - 1) / v * v;  // row pitch in elements
+    }
   }
-  r.nbytes = (size_t)r.nelem() * dtype_size(dtype);
+  r.nbytes = r.nelem() ? (size_t)(ndim ? r.shape[0] * r.stride[0] : 1) * dtype_size(dtype) : 0;
   r.app_refs = 1;
   c->stores[r.handle] = r;
   *out = r.handle;
@@ -1259,7 +1268,7 @@ static int new_store(dfs_ctx* c, int32_t dtype, int32_t ndim, const int64_t* sha
 
 int dfs_store_create(dfs_ctx* c, int32_t dtype, int32_t ndim, const int64_t* shape, dfs_store* out) {
   try {
-    return new_store(c, dtype, ndim, shape, out);
+    return new_store(c, dtype, ndim, shape, out, true);
   } catch (const std::exception& e_) {
     return internal_error(c, e_.what());
   } catch (...) {
@@ -1271,7 +1280,7 @@ int dfs_store_wrap(dfs_ctx* c, int32_t dtype, int32_t ndim, const int64_t* shape
   try {
     if (!c) return DFS_ERR_INVALID;
     if (!dev_ptr) return fail(c, DFS_ERR_INVALID, "null device pointer");
-    int rc = new_store(c, dtype, ndim, shape, out);
+    int rc = new_store(c, dtype, ndim, shape, out, false);
     if (rc) return rc;
     StoreRec& r = c->stores.at(*out);
     r.ptr = dev_ptr;
@@ -1339,13 +1348,23 @@ int dfs_store_write(dfs_ctx* c, dfs_store s, const void* host_src, size_t bytes)
     StoreRec* r = find_store(c, s);
     if (!r) return fail(c, DFS_ERR_STATE, "unknown or released store");
     if (r->root != r->handle) return fail(c, DFS_ERR_INVALID, "write a root store, not a view");
-    if (bytes != r->nbytes) return fail(c, DFS_ERR_INVALID, "byte count does not match the store");
+    const size_t es = dtype_size(r->dtype);
+    if (bytes != (size_t)r->nelem() * es) return fail(c, DFS_ERR_INVALID, "byte count does not match the store");
     if (!c->device) return fail(c, DFS_ERR_NO_DEVICE, "analysis-only context");
     int rc = flush(c);
     if (rc) return rc;
     rc = materialise(c, *r);
     if (rc) return rc;
-    CUDA_OK(cudaMemcpyAsync(r->ptr, host_src, bytes, cudaMemcpyHostToDevice, c->stream));
+    const int nd = r->ndim;
+    if (nd >= 2 && r->stride[nd - 2] != r->shape[nd - 1]) {
+      // pitched rows: one 2-D copy over every row of every plane
+      const size_t w = (size_t)r->shape[nd - 1] * es;
+      const size_t h = bytes ? bytes / w : 0;
+      if (h) CUDA_OK(cudaMemcpy2DAsync(r->ptr, (size_t)r->stride[nd - 2] * es, host_src, w, w, h,
+                                       cudaMemcpyHostToDevice, c->stream));
+    } else if (bytes) {
+      CUDA_OK(cudaMemcpyAsync(r->ptr, host_src, bytes, cudaMemcpyHostToDevice, c->stream));
+    }
     r->valid = true;
     return DFS_OK;
   } catch (const std::exception& e_) {
