@@ -30,7 +30,7 @@ BATCHED_CG = dict(count=256, seed=4, iters=100, dtype="f64", tile_max=2048, min_
 
 # Jacobi: Fig. 1 stencil on an 8192x8192 FP32 grid (8190^2 interior),
 # 200 sweeps, interior U[0,1] (seed 2), boundary 1.0
-JACOBI = dict(N=8190, sweeps=200, seed=2, rows=16, block=256, unroll=8, sweeps_per_flush=1)
+JACOBI = dict(N=8190, sweeps=200, seed=2, rows=8, block=512, unroll=8, sweeps_per_flush=1)
 
 # Serving: Poisson arrivals (exponential gaps, mean 2 ms, seed 3) of CG and
 # BiCGSTAB solves on 3-D 7-point Poisson operators (m from a log-spaced
