@@ -116,6 +116,31 @@ class Clocks:
 
 
 # ------------------------------------------------------------------ oracle
+def _bs_oracle_worker(job):
+    """One host core pricing 2^20-option batches with the oracle for budget_s."""
+    seed, budget_s = job
+    from oracle import programs
+    cfg = configs.BLACK_SCHOLES
+    m = 1 << 20
+    S, K, T = inputs.bs_inputs(m, seed=seed)
+    done, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        programs.black_scholes(S, K, T, cfg["r"], cfg["sigma"], np.float32)
+        done += m
+    return done, time.perf_counter() - t0
+
+
+def oracle_rate_all_cores(budget_s: float = 8.0):
+    """The Black-Scholes oracle on every host core at once (independent
+    batches in spawned processes; BLAS single-threaded in each)."""
+    import multiprocessing as mp
+    n = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(n) as pool:
+        res = pool.map(_bs_oracle_worker, [(1000 + i, budget_s) for i in range(n)])
+    done = sum(d for d, _ in res)
+    return done / max(t for _, t in res), n
+
+
 def oracle_rate(workload: str, budget_s: float = 10.0):
     """CPU oracle throughput on a bounded sample (the reference / cpu_baseline)."""
     from oracle import programs
@@ -432,21 +457,25 @@ class Arm:
         rt.sync()
         s0 = rt.stats()
         torch.cuda.synchronize()
-        start = torch.cuda.Event(enable_timing=True)
-        end = torch.cuda.Event(enable_timing=True)
-        start.record(stream)
+        # an event at every step boundary: the whole region and each step
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        ev[0].record(stream)
         t0 = time.perf_counter()
-        for _ in range(steps):
+        for k in range(steps):
             self.step()
-        end.record(stream)
+            ev[k + 1].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         rt.sync()
         s1 = rt.stats()
-        ms = start.elapsed_time(end)
+        ms = ev[0].elapsed_time(ev[-1])
+        per = sorted(ev[k].elapsed_time(ev[k + 1]) for k in range(steps))
+        trimmed = per[1:-1] if len(per) > 2 else per
         kd = kernel_delta(s0["kernel_times"], s1["kernel_times"])
         dom = max(kd.items(), key=lambda kv: kv[1]["ms"]) if kd else (None, {"ms": 0.0, "launches": 1})
         out = {"ms": ms, "wall_s": wall, "launches": s1["launches"] - s0["launches"],
+               "step_ms": {"p50": statistics.median(per), "min": per[0], "max": per[-1],
+                           "trimmed_mean": sum(trimmed) / len(trimmed)},
                "units": self.units * steps, "kernels": kd, "dominant": dom[0],
                "dominant_ms": dom[1]["ms"] / max(1, dom[1]["launches"]),
                "dominant_launches": dom[1]["launches"], "stats": s1}
@@ -817,6 +846,10 @@ def main():
     if rank == 0 and world == 1 and not args.quick:
         v, u, sample = oracle_rate(args.workload, budget_s=10.0)
         cpu = {"value": v, "unit": u, "cores": 1, "kind": "oracle", "sample": sample}
+        if args.workload == "bs":
+            va, nc = oracle_rate_all_cores()
+            cpu["all_cores"] = {"value": va, "unit": u, "cores": nc,
+                                "sample": "independent 2^20-option batches, one process per host core, 8 s"}
 
     line = {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -828,6 +861,7 @@ def main():
                                                         "iteration windows" if graph else ""),
                        "parallelism": f"replicas x{world}"},
             "e2e": extra.pop("e2e", None), "gpu_launches": fused["launches"], "roofline": roofline,
+            "step_ms": fused["step_ms"],
             "cpu_baseline": cpu, "clocks": clk}
     line.update(extra)
     if tuned:
