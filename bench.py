@@ -288,6 +288,22 @@ class Arm:
                 # iters_per_flush iterations share one window (one launch)
                 ipf = cfg.get("iters_per_flush", 1)
                 self.s = W.cg_start_inplace(self.b)
+                if autotune:
+                    # tile and launch shape of the iteration window, by timing it
+                    import tempfile
+                    from paper_2406_18109_gb300 import autotune as AT
+                    rt = self.rt
+
+                    def window():
+                        for _ in range(ipf):
+                            W.cg_iteration_inplace(self.Am, self.s)
+                        rt.flush()
+                    space = {"tile": [256, 512, 1024, 2048], "block": [128, 256, 512], "unroll": [1, 2]}
+                    best, trials = AT.tune(rt, window, space=space, warmup=1, reps=5,
+                                           key=f"cg-{cfg['m']}-{ipf}",
+                                           cache_path=os.path.join(tempfile.gettempdir(), "dfs_autotune.json"),
+                                           gpu=torch.cuda.get_device_name())
+                    self.tuned = {"config": best, "trials": [{"config": c, "ms_per_window": m} for c, m in trials]}
                 for _ in range(ipf):
                     W.cg_iteration_inplace(self.Am, self.s)
                 self.rt.flush()
@@ -657,7 +673,7 @@ def main():
         ap.add_argument(f"--{k}", type=int, default=0, help=f"override the workload's {k} (tuning)")
     ap.add_argument("--ipf", type=int, default=0, help="CG: iterations per flush window (tuning)")
     ap.add_argument("--no-autotune", action="store_true",
-                    help="batched CG / Jacobi: keep the configured tiling and launch shape")
+                    help="CG / batched CG / Jacobi: keep the configured tiling and launch shape")
     ap.add_argument("--compile-report", action="store_true",
                     help="print the warm-up/compilation cost table instead of the bench line")
     args = ap.parse_args()
@@ -741,7 +757,7 @@ def main():
             a.close()
 
     fused_arm = Arm(args.workload, dict(base, fusion=True, launch="persistent"), torch, stream, graph=graph,
-                    autotune=args.workload in ("batched", "jacobi") and not args.no_autotune)
+                    autotune=args.workload in ("batched", "jacobi", "cg") and not args.no_autotune)
     batch_sizes = (fused_arm.nnz, fused_arm.rows) if args.workload == "batched" else None
     tuned = fused_arm.tuned
     if tuned:
