@@ -194,3 +194,44 @@ def test_autotuned_batch_matches_fresh_run_and_oracle():
         rp, col, val, xs = inputs.batched_cg_matrix(spec)
         xo, _, _ = programs.cg(rp, col, val, programs.spmv(rp, col, val, xs), iters)
         assert np.linalg.norm(tuned[i] - xo) / np.linalg.norm(xo) < 1e-12, spec
+
+
+def test_batched_full_size_sampled():
+    """The full batch the benchmark times (256 uneven solves, 22.3 M unknowns,
+    its tile policy and launch shape): after 10 batched iterations, the
+    largest and smallest problem of each family and two random ones agree
+    with the oracle one by one (1e-12 norm-wise)."""
+    from paper_2406_18109_gb300 import configs
+    cfg = configs.BATCHED_CG
+    specs = inputs.batched_cg_problems(cfg["count"], cfg["seed"])
+    iters = 10
+    with gpu_runtime("persistent", tile_max=cfg["tile_max"], min_points=cfg["min_points"], block=cfg["block"],
+                     unroll=cfg["unroll"]) as rt:
+        mats = []
+        for spec in specs:
+            rp, col, val, xs = inputs.batched_cg_matrix(spec)
+            mats.append((A.CSR(rt, rp, col, val), rt.array(xs)))
+        probs = []
+        rt.batch_begin()
+        for Am, xs_d in mats:
+            b = Am @ xs_d
+            probs.append((Am, W.cg_start_inplace(b), b))
+            rt.batch_next()
+        rt.batch_end()
+        for _ in range(iters):
+            W.batched_cg_iteration(rt, [(Am, s) for Am, s, _ in probs])
+        st = rt.stats()
+        assert st["batch_fallbacks"] == 0 and st["batches"] == iters + 1
+        sizes = [(spec[0], spec[1]) for spec in specs]
+        pick = set()
+        for fam in ("poisson", "spd"):
+            idx = [i for i, s in enumerate(sizes) if s[0] == fam]
+            pick.add(max(idx, key=lambda i: sizes[i][1]))
+            pick.add(min(idx, key=lambda i: sizes[i][1]))
+        rng = np.random.default_rng(11)
+        pick.update(int(i) for i in rng.choice(len(specs), 2, replace=False))
+        got = {i: probs[i][1].x.numpy() for i in sorted(pick)}
+    for i, x in got.items():
+        rp, col, val, xs = inputs.batched_cg_matrix(specs[i])
+        xo, _, _ = programs.cg(rp, col, val, programs.spmv(rp, col, val, xs), iters)
+        assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-12, specs[i]

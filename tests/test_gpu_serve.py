@@ -147,3 +147,35 @@ def test_read_scalars_matches_single_reads():
         vals = rt.read_scalars(ss)
         for v, s in zip(vals, ss):
             assert v == float(s.numpy())
+
+
+def test_serving_full_size_requests():
+    """Eight requests drawn from the benchmark's serving distribution (3-D
+    Poisson 64^3..256^3, options 2^16..2^24) in its launch configuration:
+    every solve converged, its true residual ||b - A x|| (oracle SpMV) within
+    1.5 tol ||b||; option prices on a sample of 4096 options per batch
+    within 1e-5 (S + K)."""
+    from paper_2406_18109_gb300 import configs
+    cfg = configs.SERVING
+    reqs = inputs.serving_requests(8, seed=cfg["seed"], mean_gap_s=cfg["mean_gap_ms"] * 1e-3)
+    with gpu_runtime("persistent", tile=cfg["tile"], block=cfg["block"], unroll=cfg["unroll"]) as rt:
+        srv = serve.Server(rt, inputs.poisson3d_csr, budget_bytes=int(cfg["budget_gb"] * 1e9), tol=cfg["tol"],
+                           iters_per_tick=cfg["iters_per_tick"], max_active=cfg["max_active"])
+        out = {r.rid: r for r in srv.run(reqs, inputs.serving_payload)}
+    assert sorted(out) == [r["rid"] for r in reqs]
+    prm = inputs.bs_params()
+    rng = np.random.default_rng(5)
+    for req in reqs:
+        r = out[req["rid"]]
+        if req["kind"] == "bs":
+            S, K, T = inputs.serving_payload(req)
+            idx = np.sort(rng.choice(len(S), 4096, replace=False))
+            c, p = programs.black_scholes(S[idx], K[idx], T[idx], prm["r"], prm["sigma"], np.float32)
+            tol = 1e-5 * (S[idx].astype(np.float64) + K[idx])
+            assert np.all(np.abs(r.output[0][idx] - c) <= tol) and np.all(np.abs(r.output[1][idx] - p) <= tol)
+            continue
+        assert r.converged and r.iterations % cfg["iters_per_tick"] == 0, req
+        rp, col, val = inputs.poisson3d_csr(req["size"])
+        b = programs.spmv(rp, col, val, inputs.serving_payload(req))
+        res = np.linalg.norm(b - programs.spmv(rp, col, val, r.output))
+        assert res <= 1.5 * cfg["tol"] * np.linalg.norm(b), (req, res / np.linalg.norm(b))
