@@ -269,11 +269,19 @@ class Arm:
             self.dS, self.dK, self.dT = self.rt.array(S), self.rt.array(K), self.rt.array(T)
             self.units = n
             if e2e:
+                # end to end: S, K, T from pinned host memory, call and put
+                # back to it, chunks pipelined over several contexts' streams
+                from paper_2406_18109_gb300 import pipeline as PL
                 pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
                 self.hS, self.hK, self.hT = pin(S), pin(K), pin(T)
                 self.hc = torch.empty(n, dtype=torch.float32).pin_memory().numpy()
                 self.hp = torch.empty(n, dtype=torch.float32).pin_memory().numpy()
                 self.h2d, self.d2h = 3 * n * 4, 2 * n * 4
+                self.pipe_rts = PL.pipelined_runtimes(cfg["e2e_contexts"], torch.cuda.current_device(),
+                                                      **rt_kwargs)
+                r, sg = cfg["r"], cfg["sigma"]
+                self.pipe = PL.ChunkPipeline(self.pipe_rts, lambda S_, K_, T_: W.black_scholes(S_, K_, T_, r, sg),
+                                             cfg["e2e_chunk"], [np.float32] * 3)
             self.step = self._bs
         elif workload == "cg":
             cfg = self.cfg = configs.CG
@@ -427,14 +435,10 @@ class Arm:
     def _bs(self):
         c = self.cfg
         if self.e2e:
-            self.dS.write(self.hS)
-            self.dK.write(self.hK)
-            self.dT.write(self.hT)
+            self.pipe.run([self.hS, self.hK, self.hT], [self.hc, self.hp])
+            return
         call, put = self.W.black_scholes(self.dS, self.dK, self.dT, c["r"], c["sigma"])
         self.rt.flush()
-        if self.e2e:
-            call.read_into(self.hc)
-            put.read_into(self.hp)
         self.keep = (call, put)
 
     def _cg(self):
@@ -499,6 +503,9 @@ class Arm:
 
     def close(self):
         self.keep = None
+        self.pipe = None
+        for r in getattr(self, "pipe_rts", []):
+            r.close()
         self.rt.close()
 
 
@@ -672,6 +679,8 @@ def main():
     for k in ("block", "unroll", "tile", "rows"):
         ap.add_argument(f"--{k}", type=int, default=0, help=f"override the workload's {k} (tuning)")
     ap.add_argument("--ipf", type=int, default=0, help="CG: iterations per flush window (tuning)")
+    ap.add_argument("--e2e-chunk", type=int, default=0, help="Black-Scholes end to end: options per chunk (tuning)")
+    ap.add_argument("--e2e-contexts", type=int, default=0, help="Black-Scholes end to end: streams (tuning)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="CG / batched CG / Jacobi: keep the configured tiling and launch shape")
     ap.add_argument("--compile-report", action="store_true",
@@ -685,6 +694,10 @@ def main():
         configs.JACOBI["sweeps"] = args.sweeps
     if args.ipf:
         configs.CG["iters_per_flush"] = args.ipf
+    if args.e2e_chunk:
+        configs.BLACK_SCHOLES["e2e_chunk"] = args.e2e_chunk
+    if args.e2e_contexts:
+        configs.BLACK_SCHOLES["e2e_contexts"] = args.e2e_contexts
     if args.fp32:
         configs.BATCHED_CG["dtype"] = "f32"
         METRIC["batched"] = (METRIC["batched"][0], "iterations/s", "f32")

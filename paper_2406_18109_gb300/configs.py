@@ -12,7 +12,9 @@ BLACK_SCHOLES = dict(n=1 << 26, seed=1, r=0.02, sigma=0.3, tile=16384, block=512
                      inst_per_option=187.0,
                      # DRAM bytes (read + write) of one launch at n = 2^26, from
                      # an ncu capture of this kernel (profiles/)
-                     dram_bytes_per_launch=1307.45e6)
+                     dram_bytes_per_launch=1307.45e6,
+                     # end to end (host arrays): chunks pipelined over contexts
+                     e2e_chunk=1 << 23, e2e_contexts=3)
 
 # CG: 2-D 5-point Poisson on a 256x256 grid, 50 iterations, FP64 values,
 # int32 indices, x* ~ U[-1,1] (seed 0), b = A x*, x0 = 0; five iterations

@@ -433,3 +433,30 @@ def test_barrier_timeout_is_reported_and_context_survives():
     x, *_ = _cg_gpu("persistent", 32, 5, tile=256)
     xo, *_ = _cg_oracle(32, 5)
     assert _rel(x, xo) < 1e-12
+
+
+def test_chunk_pipeline_equals_one_window():
+    """Host arrays priced in chunks over three contexts (ragged last chunk)
+    give exactly the single-window results."""
+    from paper_2406_18109_gb300 import pipeline as PL
+    import torch
+    n = 300_001
+    S, K, T = inputs.bs_inputs(n, seed=6)
+    prm = inputs.bs_params()
+    pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+    hS, hK, hT = pin(S), pin(K), pin(T)
+    hc, hp = pin(np.zeros(n, np.float32)), pin(np.zeros(n, np.float32))
+    rts = PL.pipelined_runtimes(3, 0, tile=4096)
+    try:
+        pipe = PL.ChunkPipeline(rts, lambda a, b, c: W.black_scholes(a, b, c, prm["r"], prm["sigma"]), 65536,
+                                [np.float32] * 3)
+        for _ in range(2):
+            pipe.run([hS, hK, hT], [hc, hp])
+    finally:
+        for r in rts:
+            r.close()
+    with gpu_runtime("persistent", tile=4096) as rt:
+        c, p = W.black_scholes(rt.array(S), rt.array(K), rt.array(T), prm["r"], prm["sigma"])
+        cw, pw = c.numpy(), p.numpy()
+    assert np.array_equal(hc.view(np.uint32), cw.view(np.uint32))
+    assert np.array_equal(hp.view(np.uint32), pw.view(np.uint32))
