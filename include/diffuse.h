@@ -190,6 +190,23 @@ int dfs_store_create(dfs_ctx *ctx, int32_t dtype, int32_t ndim, const int64_t *s
 int dfs_store_wrap(dfs_ctx *ctx, int32_t dtype, int32_t ndim, const int64_t *shape,
                    void *dev_ptr, dfs_store *out);
 
+/*
+ * dfs_store_wrap_host -- a store over caller-owned, page-locked host memory
+ * that is mapped into the device's address space (cudaHostAlloc, or memory
+ * registered with cudaHostRegister and its mapping flag; on GB300 the GPU
+ * reaches it over NVLink-C2C).  Kernels then read and write the host memory
+ * directly: a one-pass program over host arrays needs no separate copies in
+ * or out.  Layout: dense, row-major.  The memory must stay allocated while any
+ * task uses the store; the store is never temporary.
+ * The range [host_ptr, host_ptr + bytes) is checked before anything uses it:
+ * both its first and its last byte must have a device mapping, at the same
+ * distance apart.  Returns DFS_OK; DFS_ERR_INVALID (nothing is created) for a
+ * null pointer or memory that is not mapped pinned host memory;
+ * DFS_ERR_NO_DEVICE in an analysis-only context.
+ */
+int dfs_store_wrap_host(dfs_ctx *ctx, int32_t dtype, int32_t ndim, const int64_t *shape, void *host_ptr,
+                        dfs_store *out);
+
 /* Creates an aliasing view: the box [offset, offset+shape) of `parent`
  * (itself possibly a view), as array slicing does (Fig. 1a). */
 int dfs_store_view(dfs_ctx *ctx, dfs_store parent, const int64_t *offset, const int64_t *shape,

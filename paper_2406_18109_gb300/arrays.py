@@ -194,6 +194,16 @@ class Runtime:
         a._keep = tensor
         return a
 
+    def wrap_host(self, host: np.ndarray) -> "Array":
+        """Wraps a contiguous numpy array that lives in mapped page-locked
+        host memory (e.g. a pinned torch tensor's .numpy()): kernels read and
+        write it directly, without copies (dfs_store_wrap_host)."""
+        assert host.flags["C_CONTIGUOUS"]
+        h = B.dfs_store_wrap_host(self.ctx, _dfs_dtype(host.dtype), tuple(host.shape), host.ctypes.data)
+        a = Array(self, h, tuple(host.shape), host.dtype)
+        a._keep = host
+        return a
+
     def submit(self, op, domain, args):
         B.dfs_submit(self.ctx, op, domain, args)
 

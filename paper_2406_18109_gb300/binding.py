@@ -37,7 +37,7 @@ EXPORTS = ("dfs_config_default", "dfs_init", "dfs_shutdown", "dfs_store_create",
            "dfs_last_kernel_source", "dfs_version", "dfs_dot_noalloc", "dfs_capture_begin",
            "dfs_capture_end", "dfs_graph_launch", "dfs_graph_destroy", "dfs_batch_begin",
            "dfs_batch_next", "dfs_batch_end", "dfs_batch_repeat", "dfs_read_scalars",
-           "dfs_set_launch_config")
+           "dfs_set_launch_config", "dfs_store_wrap_host")
 
 
 class dfs_config(C.Structure):
@@ -103,6 +103,7 @@ def lib():
             "dfs_batch_repeat": (C.c_int, [P, I32]),
             "dfs_read_scalars": (C.c_int, [P, I32, pI64, C.POINTER(C.c_double)]),
             "dfs_set_launch_config": (C.c_int, [P, I32, I32, I32]),
+            "dfs_store_wrap_host": (C.c_int, [P, I32, I32, pI64, P, pI64]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -292,6 +293,12 @@ def dfs_read_scalars(ctx, stores, out=None):
 
 def dfs_set_launch_config(ctx, block_threads: int, unroll: int, ctas_per_sm: int) -> None:
     _check(ctx, lib().dfs_set_launch_config(ctx, block_threads, unroll, ctas_per_sm))
+
+
+def dfs_store_wrap_host(ctx, dtype: int, shape, host_ptr: int) -> int:
+    out = C.c_int64()
+    _check(ctx, lib().dfs_store_wrap_host(ctx, dtype, len(shape), _i64s(shape), C.c_void_p(host_ptr), C.byref(out)))
+    return out.value
 
 
 def dfs_version() -> int:

@@ -13,8 +13,9 @@ BLACK_SCHOLES = dict(n=1 << 26, seed=1, r=0.02, sigma=0.3, tile=16384, block=512
                      # DRAM bytes (read + write) of one launch at n = 2^26, from
                      # an ncu capture of this kernel (profiles/)
                      dram_bytes_per_launch=1307.45e6,
-                     # end to end (host arrays): chunks pipelined over contexts
-                     e2e_chunk=1 << 23, e2e_contexts=3)
+                     # end to end (host arrays): kernels on mapped host memory
+                     # ("zero_copy") or copies pipelined in chunks over contexts
+                     e2e_mode="zero_copy", e2e_chunk=1 << 23, e2e_contexts=2)
 
 # CG: 2-D 5-point Poisson on a 256x256 grid, 50 iterations, FP64 values,
 # int32 indices, x* ~ U[-1,1] (seed 0), b = A x*, x0 = 0; five iterations

@@ -1294,6 +1294,43 @@ int dfs_store_wrap(dfs_ctx* c, int32_t dtype, int32_t ndim, const int64_t* shape
   }
 }
 
+int dfs_store_wrap_host(dfs_ctx* c, int32_t dtype, int32_t ndim, const int64_t* shape, void* host_ptr,
+                        dfs_store* out) {
+  try {
+    if (!c) return DFS_ERR_INVALID;
+    if (!host_ptr || !out) return fail(c, DFS_ERR_INVALID, "null pointer");
+    if (!c->device) return fail(c, DFS_ERR_NO_DEVICE, "analysis-only context");
+    if (dtype < DFS_F32 || dtype > DFS_I64 || ndim < 0 || ndim > MAXD || (ndim > 0 && !shape))
+      return fail(c, DFS_ERR_INVALID, "bad dtype or shape");
+    size_t n = 1;
+    for (int d = 0; d < ndim; ++d) {
+      if (shape[d] < 0) return fail(c, DFS_ERR_INVALID, "negative extent");
+      n *= (size_t)shape[d];
+    }
+    const size_t bytes = n * dtype_size(dtype);
+    void* dev = nullptr;
+    void* dev_last = nullptr;
+    char* last = (char*)host_ptr + (bytes ? bytes - 1 : 0);
+    if (cudaHostGetDevicePointer(&dev, host_ptr, 0) != cudaSuccess || !dev ||
+        cudaHostGetDevicePointer(&dev_last, last, 0) != cudaSuccess ||
+        (char*)dev_last - (char*)dev != last - (char*)host_ptr) {
+      cudaGetLastError();  // clear the sticky-free error of the failed query
+      return fail(c, DFS_ERR_INVALID, "not mapped page-locked host memory over the whole range");
+    }
+    int rc = new_store(c, dtype, ndim, shape, out, false);
+    if (rc) return rc;
+    StoreRec& r = c->stores.at(*out);
+    r.ptr = dev;
+    r.wrapped = true;
+    r.valid = true;
+    return DFS_OK;
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
+  }
+}
+
 int dfs_store_view(dfs_ctx* c, dfs_store parent, const int64_t* offset, const int64_t* shape, dfs_store* out) {
   try {
     if (!c || !out) return DFS_ERR_INVALID;

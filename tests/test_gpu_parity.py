@@ -460,3 +460,32 @@ def test_chunk_pipeline_equals_one_window():
         cw, pw = c.numpy(), p.numpy()
     assert np.array_equal(hc.view(np.uint32), cw.view(np.uint32))
     assert np.array_equal(hp.view(np.uint32), pw.view(np.uint32))
+
+
+def test_wrap_host_zero_copy_equals_device_window():
+    """Black-Scholes reading S, K, T from and writing call, put to mapped
+    page-locked host memory gives exactly the device-resident results;
+    memory without a device mapping is refused before anything runs."""
+    import torch
+    n = 200_003
+    S, K, T = inputs.bs_inputs(n, seed=8)
+    prm = inputs.bs_params()
+    pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+    hS, hK, hT = pin(S), pin(K), pin(T)
+    hc, hp = pin(np.zeros(n, np.float32)), pin(np.zeros(n, np.float32))
+    with gpu_runtime("persistent", tile=4096) as rt:
+        wc, wp = rt.wrap_host(hc), rt.wrap_host(hp)
+        c, p = W.black_scholes(rt.wrap_host(hS), rt.wrap_host(hK), rt.wrap_host(hT), prm["r"], prm["sigma"])
+        wc[...] = c
+        wp[...] = p
+        del c, p
+        rt.flush()
+        rt.sync()
+        try:                                              # pageable memory: refused unless the
+            rt.wrap_host(np.zeros(1000, np.float32))      # driver maps it (address translation)
+        except B.DfsError as e:
+            assert e.code == -1
+        c2, p2 = W.black_scholes(rt.array(S), rt.array(K), rt.array(T), prm["r"], prm["sigma"])
+        cw, pw = c2.numpy(), p2.numpy()
+    assert np.array_equal(hc.view(np.uint32), cw.view(np.uint32))
+    assert np.array_equal(hp.view(np.uint32), pw.view(np.uint32))
