@@ -17,7 +17,8 @@ What it holds:
   * ``interp``   -- an unfused task-stream interpreter: every index task runs
                     point by point, one loop per task, every temporary stored.
   * ``programs`` -- the workloads written as unfused programs in program order:
-                    Black-Scholes, CG, the Fig. 1 Jacobi stencil, BiCGSTAB.
+                    Black-Scholes, CG, the Fig. 1 Jacobi stencil and its 3-D
+                    7-point analogue, BiCGSTAB.
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 against closed forms, textbook values, invariants or brute force; none is
