@@ -123,7 +123,9 @@ std::string BatchGen::zero_d_read(int64_t root, int dt, bool in_scalar) {
 
 void BatchGen::barrier() {
   ++nbar;
-  o << "    if (!grid_barrier(ctl, " << nbar << "u, P.timeout_ns)) break;\n";
+  // test hook: CTA 0 withholds its arrival at barrier number debug_skip
+  o << "    if (!grid_barrier(ctl, " << nbar << "u, P.timeout_ns" << (S.debug_skip == nbar ? ", blockIdx.x != 0" : "")
+    << ")) break;\n";
 }
 
 void BatchGen::open_scalar(const char* ind) {

@@ -235,3 +235,24 @@ def test_batched_full_size_sampled():
         rp, col, val, xs = inputs.batched_cg_matrix(specs[i])
         xo, _, _ = programs.cg(rp, col, val, programs.spmv(rp, col, val, xs), iters)
         assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-12, specs[i]
+
+
+def test_batched_barrier_timeout_is_reported_and_next_batch_is_right():
+    """A batched launch whose grid barrier runs out of time (CTA 0 withholds
+    its arrival at barrier 2) ends instead of hanging and reports
+    DFS_ERR_BARRIER_TIMEOUT at the next sync; the context stays usable, and
+    batched launches on the same device afterwards deal every point."""
+    from paper_2406_18109_gb300.binding import DfsError
+    specs = SPECS[:3]
+    with gpu_runtime("persistent", tile=512, timeout_s=0.05, debug_skip_arrival=2) as rt:
+        probs = _problems(rt, specs)
+        W.batched_cg_iteration(rt, probs)
+        with pytest.raises(DfsError) as e:
+            rt.sync()
+        assert e.value.code == -6
+        rt.sync()                                  # error consumed; context usable
+    # a fresh context on the same device: the batched kernels deal every point
+    xb, st = _run(specs, 6, batched=True)
+    xa, _ = _run(specs, 6, batched=False)
+    for i in range(len(specs)):
+        assert np.array_equal(xb[i].view(np.uint64), xa[i].view(np.uint64))
