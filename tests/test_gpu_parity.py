@@ -146,6 +146,27 @@ def test_cg_full_size():
     assert st["plan_hits"] >= cfg["iters"] - 1
 
 
+@pytest.mark.parametrize("mode", MODES)
+def test_cg_fp32_matches_stored_dtype_oracle(mode):
+    """CG with FP32 values: against the FP32 oracle (same operations in the
+    stored dtype) to 1e-5 norm-wise; fused and unfused paths bit-identical
+    is checked by the FP64 tests."""
+    m, iters = 48, 25
+    rp, col, val, xs = inputs.cg_inputs(m=m, seed=0)
+    with gpu_runtime(mode, tile=256) as rt:
+        Am = A.CSR(rt, rp, col, val.astype(np.float32))
+        b = Am @ rt.array(xs.astype(np.float32))
+        s = W.cg_start(b)
+        for _ in range(iters):
+            W.cg_iteration(Am, s)
+            rt.flush()
+        x = s.x.numpy()
+    assert x.dtype == np.float32
+    bo = programs.spmv(rp, col, val.astype(np.float32), xs.astype(np.float32), np.float32)
+    xo, _, _ = programs.cg(rp, col, val, bo, iters, dt=np.float32)
+    assert _rel(x.astype(np.float64), xo.astype(np.float64)) < 1e-5
+
+
 def test_cg_full_size_as_benchmarked():
     """The benchmark's launch configuration: the whole 256^2 solve captured
     in a CUDA graph with five iterations per flush window, replayed."""
