@@ -596,7 +596,8 @@ def run_serving(args, torch, stream, sms, cache, dev):
 
     def server():
         return SV.Server(rt, inputs.poisson3d_csr, budget_bytes=int(cfg["budget_gb"] * 1e9), tol=cfg["tol"],
-                         iters_per_tick=cfg["iters_per_tick"], max_active=cfg["max_active"], keep_outputs=False)
+                         iters_per_tick=cfg["iters_per_tick"], max_active=cfg["max_active"], keep_outputs=False,
+                         overlap=not args.no_overlap)
 
     # resident operators (every rung of the ladder), loaded before serving
     t_load = time.perf_counter()
@@ -687,6 +688,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bs", choices=["bs", "cg", "jacobi", "batched", "serve"])
     ap.add_argument("--requests", type=int, default=0, help="serving: requests per run (default: the config's)")
+    ap.add_argument("--no-overlap", action="store_true", help="serving: set new solves up before the tick's iterations")
     ap.add_argument("--fp32", action="store_true", help="batched CG in FP32 instead of FP64")
     ap.add_argument("--quick", action="store_true", help="skip the comparison arms (for profiling)")
     ap.add_argument("--bs-n", type=int, default=0, help="Black-Scholes batch size (profiling a smaller case)")

@@ -6,9 +6,10 @@ Black-Scholes option batches) arrive over time.  The loop runs in ticks:
   1. admit, in arrival order, the requests that have arrived while the
      device-memory budget and the per-kind slot limit allow it (an idle
      operator is evicted, least recently used first, when the budget is
-     short); upload their data and set them up as one batched window per kind
-     (b = A x*, the solver's start state; a Black-Scholes batch is priced at
-     once and completes in the tick that admits it);
+     short); a Black-Scholes batch is priced at once and completes in the tick
+     that admits it; new solves have their data uploaded and are set up as one
+     batched window per kind (b = A x*, the solver's start state) after the
+     tick's iterations are launched, so that host work overlaps GPU work;
   2. advance every active solve by `iters_per_tick` iterations: all solves of
      one kind form the instances of one batched launch (their uneven sizes
      share one persistent kernel), repeated with dfs_batch_repeat while the
@@ -137,12 +138,14 @@ class Server:
     operator(m): host CSR arrays (rowptr, col, val) of the m^3 Poisson matrix;
     clock: None for wall-clock arrivals, else a callable giving the time in
     seconds (a virtual clock: when idle the loop jumps to the next arrival);
-    bs_rate, bs_sigma: the market's r and sigma for option batches.
+    bs_rate, bs_sigma: the market's r and sigma for option batches; overlap:
+    set new solves up after the tick's iterations are launched, so the
+    uploads and set-up overlap GPU work (they start iterating a tick later).
     """
 
     def __init__(self, rt: A.Runtime, operator, *, budget_bytes: int = 120 * 10 ** 9, tol: float = 1e-8,
                  iters_per_tick: int = 8, max_iters: int = 20000, max_active: int = 64, clock=None,
-                 keep_outputs: bool = True, bs_rate: float = 0.02, bs_sigma: float = 0.3):
+                 keep_outputs: bool = True, bs_rate: float = 0.02, bs_sigma: float = 0.3, overlap: bool = True):
         self.rt = rt
         self.operator_fn = operator
         self.budget = int(budget_bytes)
@@ -153,6 +156,7 @@ class Server:
         self.clock = clock
         self.keep = keep_outputs
         self.bs_rate, self.bs_sigma = bs_rate, bs_sigma
+        self.overlap = overlap
         self.ops: OrderedDict[int, A.CSR] = OrderedDict()   # resident operators, LRU order
         self.op_users: dict[int, int] = {}
         self.used = 0
@@ -284,14 +288,18 @@ class Server:
             qi += len(adm)
             if add:
                 self._evict_for(add)
-            # admission: set-up windows (solves) and pricing (option batches)
-            for kind in SOLVERS:
-                reqs = [r for r in adm if r["kind"] == kind]
-                if reqs:
-                    sols = self._setup_solves(kind, reqs, payloads, now)
-                    for s in sols:
-                        self.used += s.nbytes
-                    active[kind].extend(sols)
+            def setup_new():
+                for kind in SOLVERS:
+                    reqs = [r for r in adm if r["kind"] == kind]
+                    if reqs:
+                        sols = self._setup_solves(kind, reqs, payloads, now)
+                        for s in sols:
+                            self.used += s.nbytes
+                        active[kind].extend(sols)
+            # admission: set-up windows of new solves (now, or after this
+            # tick's iterations are launched) and pricing of option batches
+            if not self.overlap:
+                setup_new()
             bs = [r for r in adm if r["kind"] == "bs"]
             if bs:
                 self.used += sum(request_bytes("bs", r["size"]) for r in bs)
@@ -310,10 +318,12 @@ class Server:
                     self._iterate(kind, active[kind])
                     for s in active[kind]:
                         s.it += self.C
+            if self.overlap:
+                setup_new()                      # host work while the GPU iterates; they join next tick
             self.stats.ticks += 1
             self._advance(0.0)
-            # convergence test of every active solve, one gather
-            sols = active["cg"] + active["bicgstab"]
+            # convergence test of every solve that iterated, one gather
+            sols = [s for s in active["cg"] + active["bicgstab"] if s.it > 0]
             if sols:
                 arrs = []
                 for s in sols:
