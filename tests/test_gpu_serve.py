@@ -179,3 +179,36 @@ def test_serving_full_size_requests():
         b = programs.spmv(rp, col, val, inputs.serving_payload(req))
         res = np.linalg.norm(b - programs.spmv(rp, col, val, r.output))
         assert res <= 1.5 * cfg["tol"] * np.linalg.norm(b), (req, res / np.linalg.norm(b))
+
+
+def test_scalar_gather_and_repeat_refuse_bad_state():
+    """dfs_read_scalars refuses a store that is not 0-d or holds no value;
+    dfs_batch_repeat refuses a batch that was not steady (it created the
+    stores it wrote) and works once the batch only updates stores in place."""
+    with gpu_runtime("persistent", tile=256) as rt:
+        v = rt.array(np.ones(300))
+        with pytest.raises(A.B.DfsError) as e:
+            rt.read_scalars([v])
+        assert e.value.code == -1
+        with pytest.raises(A.B.DfsError) as e:
+            rt.read_scalars([rt.empty(())])
+        assert e.value.code == -7
+        xs = [rt.array(inputs.uniform(i, -1, 1, 700 + 300 * i)) for i in range(2)]
+        rt.batch_begin()
+        outs = []
+        for x in xs:
+            outs.append(x * 2.0)                 # creates its output: not steady
+            rt.batch_next()
+        rt.batch_end()
+        with pytest.raises(A.B.DfsError) as e:
+            rt.batch_repeat(1)
+        assert e.value.code == -7
+        rt.batch_begin()
+        for x in xs:
+            x *= 0.5                             # in place: steady
+            rt.batch_next()
+        rt.batch_end()
+        rt.batch_repeat(3)
+        for i, x in enumerate(xs):
+            want = inputs.uniform(i, -1, 1, 700 + 300 * i) * 0.5 ** 4
+            assert np.array_equal(x.numpy(), want)
