@@ -251,195 +251,191 @@ class Arm:
 
     def __init__(self, workload, rt_kwargs, torch, stream, e2e=False, graph=False, per_solve=False,
                  autotune=False):
-        self.per_solve = per_solve
-        self.tuned = None
         from paper_2406_18109_gb300 import arrays as A
-        from paper_2406_18109_gb300 import dist as D
         from paper_2406_18109_gb300 import workloads as W
-        self.W, self.torch, self.stream, self.e2e = W, torch, stream, e2e
+        self.A, self.W, self.torch, self.stream, self.e2e = A, W, torch, stream, e2e
+        self.per_solve, self.graph_mode, self.autotune, self.rt_kwargs = per_solve, graph, autotune, rt_kwargs
+        self.tuned = None
         self.rt = A.Runtime(device=torch.cuda.current_device(), stream=stream.cuda_stream,
                             time_launches=True, **rt_kwargs)
         self.h2d = self.d2h = 0
-        rank = int(os.environ.get("RANK", "0"))
-        if workload == "bs":
-            cfg = self.cfg = configs.BLACK_SCHOLES
-            n = cfg["n"]
-            # weak scaling: every rank prices its own, independent batch
-            S, K, T = inputs.bs_inputs(n, seed=D.rank_seed(cfg["seed"], rank))
-            self.dS, self.dK, self.dT = self.rt.array(S), self.rt.array(K), self.rt.array(T)
-            self.units = n
-            if e2e:
-                # end to end: S, K, T from pinned host memory, call and put
-                # back to it, chunks pipelined over several contexts' streams
-                from paper_2406_18109_gb300 import pipeline as PL
-                pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
-                self.hS, self.hK, self.hT = pin(S), pin(K), pin(T)
-                self.hc = torch.empty(n, dtype=torch.float32).pin_memory().numpy()
-                self.hp = torch.empty(n, dtype=torch.float32).pin_memory().numpy()
-                self.h2d, self.d2h = 3 * n * 4, 2 * n * 4
-                self.e2e_mode = cfg["e2e_mode"]
-                if self.e2e_mode == "zero_copy":
-                    # the kernel reads S, K, T from and writes call, put to the
-                    # host buffers themselves (mapped page-locked memory)
-                    self.wS, self.wK, self.wT = (self.rt.wrap_host(h) for h in (self.hS, self.hK, self.hT))
-                    self.wc, self.wp = self.rt.wrap_host(self.hc), self.rt.wrap_host(self.hp)
-                else:
-                    self.pipe_rts = PL.pipelined_runtimes(cfg["e2e_contexts"], torch.cuda.current_device(),
-                                                          **rt_kwargs)
-                    r, sg = cfg["r"], cfg["sigma"]
-                    self.pipe = PL.ChunkPipeline(self.pipe_rts,
-                                                 lambda S_, K_, T_: W.black_scholes(S_, K_, T_, r, sg),
-                                                 cfg["e2e_chunk"], [np.float32] * 3)
-            self.step = self._bs
-        elif workload == "cg":
-            cfg = self.cfg = configs.CG
-            rp, col, val, xs = inputs.cg_inputs(m=cfg["m"], seed=cfg["seed"])
-            self.Am = A.CSR(self.rt, rp, col, val)
-            self.b = self.Am @ self.rt.array(xs)
-            self.units = cfg["iters"]
-            self.step = self._cg
-            if graph:
-                # the whole solve (reset + 50 in-place iterations) captured once
-                # after one normally issued window, then replayed per step;
-                # iters_per_flush iterations share one window (one launch)
-                ipf = cfg.get("iters_per_flush", 1)
-                self.s = W.cg_start_inplace(self.b)
-                if autotune:
-                    # tile and launch shape of the iteration window, by timing it
-                    import tempfile
-                    from paper_2406_18109_gb300 import autotune as AT
-                    rt = self.rt
-
-                    def window():
-                        for _ in range(ipf):
-                            W.cg_iteration_inplace(self.Am, self.s)
-                        rt.flush()
-                    space = {"tile": [256, 512, 1024, 2048], "block": [128, 256, 512], "unroll": [1, 2]}
-                    best, trials = AT.tune(rt, window, space=space, warmup=1, reps=5,
-                                           key=f"cg-{cfg['m']}-{ipf}",
-                                           cache_path=os.path.join(tempfile.gettempdir(), "dfs_autotune.json"),
-                                           gpu=torch.cuda.get_device_name())
-                    self.tuned = {"config": best, "trials": [{"config": c, "ms_per_window": m} for c, m in trials]}
-                for _ in range(ipf):
-                    W.cg_iteration_inplace(self.Am, self.s)
-                self.rt.flush()
-                self.rt.capture_begin()
-                W.cg_reset_inplace(self.s, self.b)
-                self.rt.flush()
-                for it in range(cfg["iters"]):
-                    W.cg_iteration_inplace(self.Am, self.s)
-                    if (it + 1) % ipf == 0 or it + 1 == cfg["iters"]:
-                        self.rt.flush()
-                self.graph = self.rt.capture_end()
-                self.step = self._cg_graph
-                if e2e:
-                    # end to end: b uploaded from pinned host memory, x read back, every step
-                    pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
-                    self.hb = pin(self.b.numpy())
-                    self.hx = pin(np.empty(self.hb.shape, self.hb.dtype))
-                    self.h2d = self.d2h = self.hb.nbytes
-                    self.e2e_io = ([(self.b, self.hb)], [(self.s.x, self.hx)])
-        elif workload == "batched":
-            cfg = self.cfg = configs.BATCHED_CG
-            dt = np.float64 if cfg["dtype"] == "f64" else np.float32
-            self.probs, self.nnz, self.rows = [], 0, 0
-            mats = []
-            for spec in inputs.batched_cg_problems(cfg["count"], cfg["seed"]):
-                rp, col, val, xs = inputs.batched_cg_matrix(spec)
-                mats.append((A.CSR(self.rt, rp, col, val.astype(dt)), self.rt.array(xs.astype(dt))))
-                self.nnz += len(col)
-                self.rows += len(rp) - 1
-            # b = A x* and the CG start of every problem, as one batch
-            self.rt.batch_begin()
-            for Am, xs_d in mats:
-                b = Am @ xs_d
-                self.probs.append((Am, W.cg_start_inplace(b), b))
-                self.rt.batch_next()
-            self.rt.batch_end()
-            del mats
-            pairs = [(Am, s) for Am, s, _ in self.probs]
-            rt = self.rt
-
-            def one_iteration():
-                if self.per_solve:
-                    for Am, s in pairs:
-                        W.cg_iteration_inplace(Am, s)
-                        rt.flush()
-                else:
-                    W.batched_cg_iteration(rt, pairs)
-
-            def reset():
-                if self.per_solve:
-                    for _, s, b in self.probs:
-                        W.cg_reset_inplace(s, b)
-                        rt.flush()
-                else:
-                    rt.batch_begin()
-                    for _, s, b in self.probs:
-                        W.cg_reset_inplace(s, b)
-                        rt.batch_next()
-                    rt.batch_end()
-            if autotune:
-                # tile and launch shape of the batched iteration, by timing it
-                # (coordinate descent; the choice is cached per GPU and dtype)
-                import tempfile
-                from paper_2406_18109_gb300 import autotune as AT
-                space = {"tile_max": [512, 1024, 2048, 4096, 8192], "block": [128, 256, 512], "unroll": [1, 2],
-                         "ctas_per_sm": [0, 5, 6]}
-                best, trials = AT.tune(rt, one_iteration, space=space, warmup=1, reps=3,
-                                       key=f"batched-cg-{cfg['count']}-{cfg['seed']}-{cfg['dtype']}",
-                                       cache_path=os.path.join(tempfile.gettempdir(), "dfs_autotune.json"),
-                                       gpu=torch.cuda.get_device_name())
-                self.tuned = {"config": best, "trials": [{"config": c, "ms_per_iteration": m} for c, m in trials]}
-            # one normal pass of each window (compiles kernels, uploads descriptors), then capture
-            reset()
-            one_iteration()
-            rt.capture_begin()
-            reset()
-            for _ in range(cfg["iters"]):
-                one_iteration()
-            self.graph = rt.capture_end()
-            self.units = cfg["count"] * cfg["iters"]
-            self.step = self._cg_graph
-            if e2e:
-                pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
-                ups, downs = [], []
-                for _, s, b in self.probs:
-                    hb = pin(b.numpy())
-                    ups.append((b, hb))
-                    downs.append((s.x, pin(np.empty(hb.shape, hb.dtype))))
-                self.h2d = sum(h.nbytes for _, h in ups)
-                self.d2h = sum(h.nbytes for _, h in downs)
-                self.e2e_io = (ups, downs)
-        else:
-            cfg = self.cfg = configs.JACOBI
-            grid = inputs.jacobi_grid(cfg["N"], seed=cfg["seed"])
-            self.g = self.rt.array(grid)
-            self.views = W.jacobi_views(self.g)
-            self.units = cfg["sweeps"]
-            self.step = self._jacobi
-            if autotune:
-                # rows per point and launch shape of the sweep, by timing it
-                import tempfile
-                from paper_2406_18109_gb300 import autotune as AT
-                rt = self.rt
-
-                def sweep():
-                    W.jacobi_sweep(self.views)
-                    rt.flush()
-                space = {"rows": [8, 16, 32], "block": [256, 512], "unroll": [4, 8], "ctas_per_sm": [0, 4, 6]}
-                best, trials = AT.tune(rt, sweep, space=space, warmup=1, reps=3, key=f"jacobi-{cfg['N']}",
-                                       cache_path=os.path.join(tempfile.gettempdir(), "dfs_autotune.json"),
-                                       gpu=torch.cuda.get_device_name())
-                self.tuned = {"config": best, "trials": [{"config": c, "ms_per_sweep": m} for c, m in trials]}
-            if e2e:
-                pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
-                hg = pin(grid)
-                self.h2d = self.d2h = hg.nbytes
-                self.e2e_io = ([(self.g, hg)], [(self.g, pin(np.empty_like(grid)))])
+        {"bs": self._setup_bs, "cg": self._setup_cg, "batched": self._setup_batched,
+         "jacobi": self._setup_jacobi}[workload]()
         self.rt.sync()
         self.keep = None
 
+    # ------------------------------------------------------------- helpers
+    def _pin(self, a):
+        return self.torch.from_numpy(a).pin_memory().numpy()
+
+    def _tune(self, step, space, key, reps, what):
+        """Autotunes the context for `step`, caching the choice per GPU and key."""
+        import tempfile
+        from paper_2406_18109_gb300 import autotune as AT
+        best, trials = AT.tune(self.rt, step, space=space, warmup=1, reps=reps, key=key,
+                               cache_path=os.path.join(tempfile.gettempdir(), "dfs_autotune.json"),
+                               gpu=self.torch.cuda.get_device_name())
+        self.tuned = {"config": best, "trials": [{"config": c, what: m} for c, m in trials]}
+
+    # ------------------------------------------------------------ workloads
+    def _setup_bs(self):
+        from paper_2406_18109_gb300 import dist as D
+        W = self.W
+        cfg = self.cfg = configs.BLACK_SCHOLES
+        n = cfg["n"]
+        # weak scaling: every rank prices its own, independent batch
+        S, K, T = inputs.bs_inputs(n, seed=D.rank_seed(cfg["seed"], int(os.environ.get("RANK", "0"))))
+        self.dS, self.dK, self.dT = self.rt.array(S), self.rt.array(K), self.rt.array(T)
+        self.units = n
+        self.step = self._bs
+        if not self.e2e:
+            return
+        # end to end: S, K, T from pinned host memory, call and put back to it
+        self.hS, self.hK, self.hT = self._pin(S), self._pin(K), self._pin(T)
+        self.hc = self._pin(np.empty(n, np.float32))
+        self.hp = self._pin(np.empty(n, np.float32))
+        self.h2d, self.d2h = 3 * n * 4, 2 * n * 4
+        self.e2e_mode = cfg["e2e_mode"]
+        if self.e2e_mode == "zero_copy":
+            # the kernel reads S, K, T from and writes call, put to the host
+            # buffers themselves (mapped page-locked memory)
+            self.wS, self.wK, self.wT = (self.rt.wrap_host(h) for h in (self.hS, self.hK, self.hT))
+            self.wc, self.wp = self.rt.wrap_host(self.hc), self.rt.wrap_host(self.hp)
+        else:
+            # chunks pipelined over several contexts' streams
+            from paper_2406_18109_gb300 import pipeline as PL
+            self.pipe_rts = PL.pipelined_runtimes(cfg["e2e_contexts"], self.torch.cuda.current_device(),
+                                                  **self.rt_kwargs)
+            r, sg = cfg["r"], cfg["sigma"]
+            self.pipe = PL.ChunkPipeline(self.pipe_rts, lambda S_, K_, T_: W.black_scholes(S_, K_, T_, r, sg),
+                                         cfg["e2e_chunk"], [np.float32] * 3)
+
+    def _setup_cg(self):
+        A, W, rt = self.A, self.W, self.rt
+        cfg = self.cfg = configs.CG
+        rp, col, val, xs = inputs.cg_inputs(m=cfg["m"], seed=cfg["seed"])
+        self.Am = A.CSR(rt, rp, col, val)
+        self.b = self.Am @ rt.array(xs)
+        self.units = cfg["iters"]
+        self.step = self._cg
+        if not self.graph_mode:
+            return
+        # the whole solve (reset + 50 in-place iterations) captured once after
+        # one normally issued window, then replayed per step; iters_per_flush
+        # iterations share one window (one launch)
+        ipf = cfg.get("iters_per_flush", 1)
+        self.s = W.cg_start_inplace(self.b)
+
+        def window():
+            for _ in range(ipf):
+                W.cg_iteration_inplace(self.Am, self.s)
+            rt.flush()
+        if self.autotune:
+            self._tune(window, {"tile": [256, 512, 1024, 2048], "block": [128, 256, 512], "unroll": [1, 2]},
+                       f"cg-{cfg['m']}-{ipf}", 5, "ms_per_window")
+        window()
+        rt.capture_begin()
+        W.cg_reset_inplace(self.s, self.b)
+        rt.flush()
+        for it in range(cfg["iters"]):
+            W.cg_iteration_inplace(self.Am, self.s)
+            if (it + 1) % ipf == 0 or it + 1 == cfg["iters"]:
+                rt.flush()
+        self.graph = rt.capture_end()
+        self.step = self._cg_graph
+        if self.e2e:
+            # end to end: b uploaded from pinned host memory, x read back, every step
+            self.hb = self._pin(self.b.numpy())
+            self.hx = self._pin(np.empty(self.hb.shape, self.hb.dtype))
+            self.h2d = self.d2h = self.hb.nbytes
+            self.e2e_io = ([(self.b, self.hb)], [(self.s.x, self.hx)])
+
+    def _setup_batched(self):
+        A, W, rt = self.A, self.W, self.rt
+        cfg = self.cfg = configs.BATCHED_CG
+        dt = np.float64 if cfg["dtype"] == "f64" else np.float32
+        self.probs, self.nnz, self.rows = [], 0, 0
+        mats = []
+        for spec in inputs.batched_cg_problems(cfg["count"], cfg["seed"]):
+            rp, col, val, xs = inputs.batched_cg_matrix(spec)
+            mats.append((A.CSR(rt, rp, col, val.astype(dt)), rt.array(xs.astype(dt))))
+            self.nnz += len(col)
+            self.rows += len(rp) - 1
+        # b = A x* and the CG start of every problem, as one batch
+        rt.batch_begin()
+        for Am, xs_d in mats:
+            b = Am @ xs_d
+            self.probs.append((Am, W.cg_start_inplace(b), b))
+            rt.batch_next()
+        rt.batch_end()
+        del mats
+        pairs = [(Am, s) for Am, s, _ in self.probs]
+
+        def one_iteration():
+            if self.per_solve:
+                for Am, s in pairs:
+                    W.cg_iteration_inplace(Am, s)
+                    rt.flush()
+            else:
+                W.batched_cg_iteration(rt, pairs)
+
+        def reset():
+            if self.per_solve:
+                for _, s, b in self.probs:
+                    W.cg_reset_inplace(s, b)
+                    rt.flush()
+            else:
+                rt.batch_begin()
+                for _, s, b in self.probs:
+                    W.cg_reset_inplace(s, b)
+                    rt.batch_next()
+                rt.batch_end()
+        if self.autotune:
+            # tile cap and launch shape of the batched iteration (coordinate descent)
+            self._tune(one_iteration, {"tile_max": [512, 1024, 2048, 4096, 8192], "block": [128, 256, 512],
+                                       "unroll": [1, 2], "ctas_per_sm": [0, 5, 6]},
+                       f"batched-cg-{cfg['count']}-{cfg['seed']}-{cfg['dtype']}", 3, "ms_per_iteration")
+        # one normal pass of each window (compiles kernels, uploads descriptors), then capture
+        reset()
+        one_iteration()
+        rt.capture_begin()
+        reset()
+        for _ in range(cfg["iters"]):
+            one_iteration()
+        self.graph = rt.capture_end()
+        self.units = cfg["count"] * cfg["iters"]
+        self.step = self._cg_graph
+        if self.e2e:
+            ups, downs = [], []
+            for _, s, b in self.probs:
+                hb = self._pin(b.numpy())
+                ups.append((b, hb))
+                downs.append((s.x, self._pin(np.empty(hb.shape, hb.dtype))))
+            self.h2d = sum(h.nbytes for _, h in ups)
+            self.d2h = sum(h.nbytes for _, h in downs)
+            self.e2e_io = (ups, downs)
+
+    def _setup_jacobi(self):
+        W, rt = self.W, self.rt
+        cfg = self.cfg = configs.JACOBI
+        grid = inputs.jacobi_grid(cfg["N"], seed=cfg["seed"])
+        self.g = rt.array(grid)
+        self.views = W.jacobi_views(self.g)
+        self.units = cfg["sweeps"]
+        self.step = self._jacobi
+        if self.autotune:
+            # rows per point and launch shape of the sweep
+            def sweep():
+                W.jacobi_sweep(self.views)
+                rt.flush()
+            self._tune(sweep, {"rows": [8, 16, 32], "block": [256, 512], "unroll": [4, 8], "ctas_per_sm": [0, 4, 6]},
+                       f"jacobi-{cfg['N']}", 3, "ms_per_sweep")
+        if self.e2e:
+            hg = self._pin(grid)
+            self.h2d = self.d2h = hg.nbytes
+            self.e2e_io = ([(self.g, hg)], [(self.g, self._pin(np.empty_like(grid)))])
+
+    # ---------------------------------------------------------------- steps
     def _bs(self):
         c = self.cfg
         if self.e2e and self.e2e_mode == "zero_copy":
