@@ -12,7 +12,7 @@ S, K, T and D2H of call, put every step), and the CPU oracle on a bounded
 sample.  Kernel durations come from CUDA events the runtime records
 immediately around each launch on the launching stream.
 
-  python bench.py [--steps K] [--warmup W] [--workload bs|cg|jacobi|batched] [--fp32]
+  python bench.py [--steps K] [--warmup W] [--workload bs|cg|jacobi|batched|serve] [--fp32]
   python bench.py --impl reference     # the CPU oracle as the reference arm
 Prints one JSON line.
 """
@@ -679,7 +679,8 @@ def run_serving(args, torch, stream, sms, cache, dev):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=0,
+                    help="timed steps (default 50 for the sub-millisecond Black-Scholes step, else 20)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bs", choices=["bs", "cg", "jacobi", "batched", "serve"])
@@ -702,6 +703,8 @@ def main():
     ap.add_argument("--compile-report", action="store_true",
                     help="print the warm-up/compilation cost table instead of the bench line")
     args = ap.parse_args()
+    if not args.steps:
+        args.steps = 50 if args.workload == "bs" else 20
     if args.bs_n:
         configs.BLACK_SCHOLES["n"] = args.bs_n
     if args.jac_n:
@@ -727,7 +730,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        v, u, sample = oracle_rate(args.workload, budget_s=max(5.0, min(60.0, 2.0 * args.steps)))
+        v, u, sample = oracle_rate(args.workload, budget_s=max(5.0, min(30.0, 2.0 * args.steps)))
         line = {"metric": metric, "value": v, "unit": unit, "n_gpus": args.gpus, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": dtype, "data": "synthetic", "impl": "reference",
