@@ -207,6 +207,16 @@ int dfs_store_wrap(dfs_ctx *ctx, int32_t dtype, int32_t ndim, const int64_t *sha
 int dfs_store_wrap_host(dfs_ctx *ctx, int32_t dtype, int32_t ndim, const int64_t *shape, void *host_ptr,
                         dfs_store *out);
 
+/*
+ * dfs_host_alloc / dfs_host_free -- page-locked host memory mapped into the
+ * address space of every device (cudaHostAlloc, mapped and portable), for
+ * dfs_store_wrap_host and for fast copies.  *out receives the host address
+ * (NULL for bytes == 0).  Returns DFS_OK, DFS_ERR_INVALID for a null `out`,
+ * DFS_ERR_OOM when the allocation fails.  dfs_host_free(NULL) is a no-op.
+ */
+int dfs_host_alloc(size_t bytes, void **out);
+int dfs_host_free(void *p);
+
 /* Creates an aliasing view: the box [offset, offset+shape) of `parent`
  * (itself possibly a view), as array slicing does (Fig. 1a). */
 int dfs_store_view(dfs_ctx *ctx, dfs_store parent, const int64_t *offset, const int64_t *shape,

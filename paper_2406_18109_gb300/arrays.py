@@ -194,6 +194,21 @@ class Runtime:
         a._keep = tensor
         return a
 
+    @staticmethod
+    def host_empty(shape, dtype=np.float64) -> np.ndarray:
+        """A numpy array in mapped page-locked host memory (dfs_host_alloc),
+        freed with the array; wrap it with wrap_host for kernels to read or
+        write it in place."""
+        import weakref
+        dt = np.dtype(dtype)
+        shape = tuple(int(d) for d in shape) if isinstance(shape, (tuple, list)) else (int(shape),)
+        nbytes = max(1, int(np.prod(shape)) * dt.itemsize)
+        ptr = B.dfs_host_alloc(nbytes)
+        buf = (C.c_char * nbytes).from_address(ptr)
+        arr = np.frombuffer(buf, dtype=dt, count=int(np.prod(shape))).reshape(shape)
+        weakref.finalize(buf, B.dfs_host_free, ptr)
+        return arr
+
     def wrap_host(self, host: np.ndarray) -> "Array":
         """Wraps a contiguous numpy array that lives in mapped page-locked
         host memory (e.g. a pinned torch tensor's .numpy()): kernels read and

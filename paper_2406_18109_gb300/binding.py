@@ -37,7 +37,7 @@ EXPORTS = ("dfs_config_default", "dfs_init", "dfs_shutdown", "dfs_store_create",
            "dfs_last_kernel_source", "dfs_version", "dfs_dot_noalloc", "dfs_capture_begin",
            "dfs_capture_end", "dfs_graph_launch", "dfs_graph_destroy", "dfs_batch_begin",
            "dfs_batch_next", "dfs_batch_end", "dfs_batch_repeat", "dfs_read_scalars",
-           "dfs_set_launch_config", "dfs_store_wrap_host")
+           "dfs_set_launch_config", "dfs_store_wrap_host", "dfs_host_alloc", "dfs_host_free")
 
 
 class dfs_config(C.Structure):
@@ -104,6 +104,8 @@ def lib():
             "dfs_read_scalars": (C.c_int, [P, I32, pI64, C.POINTER(C.c_double)]),
             "dfs_set_launch_config": (C.c_int, [P, I32, I32, I32]),
             "dfs_store_wrap_host": (C.c_int, [P, I32, I32, pI64, P, pI64]),
+            "dfs_host_alloc": (C.c_int, [C.c_size_t, C.POINTER(P)]),
+            "dfs_host_free": (C.c_int, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -299,6 +301,16 @@ def dfs_store_wrap_host(ctx, dtype: int, shape, host_ptr: int) -> int:
     out = C.c_int64()
     _check(ctx, lib().dfs_store_wrap_host(ctx, dtype, len(shape), _i64s(shape), C.c_void_p(host_ptr), C.byref(out)))
     return out.value
+
+
+def dfs_host_alloc(nbytes: int) -> int:
+    out = C.c_void_p()
+    _check(None, lib().dfs_host_alloc(nbytes, C.byref(out)))
+    return out.value or 0
+
+
+def dfs_host_free(ptr: int) -> None:
+    _check(None, lib().dfs_host_free(C.c_void_p(ptr)))
 
 
 def dfs_version() -> int:

@@ -1331,6 +1331,26 @@ int dfs_store_wrap_host(dfs_ctx* c, int32_t dtype, int32_t ndim, const int64_t* 
   }
 }
 
+int dfs_host_alloc(size_t bytes, void** out) {
+  if (!out) return DFS_ERR_INVALID;
+  *out = nullptr;
+  if (!bytes) return DFS_OK;
+  if (cudaHostAlloc(out, bytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess || !*out) {
+    cudaGetLastError();
+    *out = nullptr;
+    return DFS_ERR_OOM;
+  }
+  return DFS_OK;
+}
+
+int dfs_host_free(void* p) {
+  if (p && cudaFreeHost(p) != cudaSuccess) {
+    cudaGetLastError();
+    return DFS_ERR_CUDA;
+  }
+  return DFS_OK;
+}
+
 int dfs_store_view(dfs_ctx* c, dfs_store parent, const int64_t* offset, const int64_t* shape, dfs_store* out) {
   try {
     if (!c || !out) return DFS_ERR_INVALID;

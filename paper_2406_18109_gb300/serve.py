@@ -248,18 +248,25 @@ class Server:
         for req in reqs:
             S, K, T = payloads(req)
             data.append((req, rt.array(S), rt.array(K), rt.array(T)))
-        outs = []
+        # one batched launch; the prices go straight from the kernel into
+        # mapped page-locked host buffers (call and put become temporaries)
+        results, hold = [], []
         rt.batch_begin()
         for req, S, K, T in data:
-            outs.append(W.black_scholes(S, K, T, self.bs_rate, self.bs_sigma))
+            hc = A.Runtime.host_empty((req["size"],), np.float32)
+            hp = A.Runtime.host_empty((req["size"],), np.float32)
+            wc, wp = rt.wrap_host(hc), rt.wrap_host(hp)
+            call, put = W.black_scholes(S, K, T, self.bs_rate, self.bs_sigma)
+            wc[...] = call
+            wp[...] = put
+            del call, put
+            hold.append((wc, wp))
+            res = Result(req["rid"], "bs", req["size"], req["arrival"], admitted=now)
+            res.output = (hc, hp) if self.keep else None
+            results.append(res)
             rt.batch_next()
         rt.batch_end()
-        results = []
-        for (req, *_), (call, put) in zip(data, outs):
-            c, p = call.numpy(), put.numpy()
-            res = Result(req["rid"], "bs", req["size"], req["arrival"], admitted=now)
-            res.output = (c, p) if self.keep else None
-            results.append(res)
+        rt.sync()
         return results
 
     # ------------------------------------------------------------------ run
@@ -337,16 +344,31 @@ class Server:
                         s.res.rel_residual = rel
                         s.res.converged = rel <= self.tol
                         retire.append(s)
+                # solutions go from one batched copy kernel straight into
+                # mapped page-locked host buffers, one sync for all of them
+                hold = []
+                if retire:
+                    self.rt.batch_begin()
                 for s in retire:
-                    x = s.st.x.numpy()
+                    hx = A.Runtime.host_empty(s.st.x.shape, s.st.x.dtype)
+                    w = self.rt.wrap_host(hx)
+                    w[...] = s.st.x
+                    hold.append(w)
+                    self.rt.batch_next()
                     s.res.iterations = s.it
-                    s.res.output = x if self.keep else None
-                    s.res.done = self._now(t0)
-                    finished.append(s.res)
+                    s.res.output = hx if self.keep else None
                     active[s.res.kind].remove(s)
                     self.used -= s.nbytes
                     self.op_users[s.m] -= 1
                     s.st = s.bb = None
+                if retire:
+                    self.rt.batch_end()
+                    self.rt.sync()
+                    t = self._now(t0)
+                    for s in retire:
+                        s.res.done = t
+                        finished.append(s.res)
+                del hold
         return finished
 
     def _advance(self, dt: float) -> None:
