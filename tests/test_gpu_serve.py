@@ -212,3 +212,26 @@ def test_scalar_gather_and_repeat_refuse_bad_state():
         for i, x in enumerate(xs):
             want = inputs.uniform(i, -1, 1, 700 + 300 * i) * 0.5 ** 4
             assert np.array_equal(x.numpy(), want)
+
+
+def test_payloads_in_mapped_host_memory_give_the_same_results():
+    """Request data in mapped page-locked buffers are read in place (x*
+    streamed into a device copy; option inputs read directly) with the same
+    results, bit for bit, as uploaded pageable data."""
+    reqs = _requests()
+
+    def pinned(req):
+        p = inputs.serving_payload(req)
+        out = []
+        for a in (p if isinstance(p, tuple) else (p,)):
+            h = A.Runtime.host_empty(a.shape, a.dtype)
+            h[...] = a
+            out.append(h)
+        return tuple(out) if isinstance(p, tuple) else out[0]
+    with gpu_runtime("persistent", tile=256) as rt:
+        srv = serve.Server(rt, inputs.poisson3d_csr, tol=1e-8, iters_per_tick=4, clock=serve.TickClock(1e-3))
+        got = {r.rid: r for r in srv.run(reqs, pinned)}
+        assert rt.stats()["batch_fallbacks"] == 0
+    ref, _, _ = _serve(reqs)
+    for rid, r in ref.items():
+        assert got[rid].iterations == r.iterations and _same(got[rid].output, r.output), rid
