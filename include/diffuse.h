@@ -199,8 +199,12 @@ int dfs_store_wrap(dfs_ctx *ctx, int32_t dtype, int32_t ndim, const int64_t *sha
  * or out.  Layout: dense, row-major.  The memory must stay allocated while any
  * task uses the store; the store is never temporary.
  * The range [host_ptr, host_ptr + bytes) is checked before anything uses it:
- * both its first and its last byte must have a device mapping, at the same
- * distance apart.  Returns DFS_OK; DFS_ERR_INVALID (nothing is created) for a
+ * CUDA must report both its first and its last byte as page-locked host
+ * memory (pageable memory is refused even where the device could reach it,
+ * since its pages can be unmapped under a running kernel), with device
+ * mappings at the same distance apart.  The caller keeps the memory
+ * allocated until every task that uses the store has completed (a
+ * dfs_sync after its flush).  Returns DFS_OK; DFS_ERR_INVALID (nothing is created) for a
  * null pointer or memory that is not mapped pinned host memory;
  * DFS_ERR_NO_DEVICE in an analysis-only context.
  */

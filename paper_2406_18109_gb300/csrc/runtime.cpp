@@ -1311,6 +1311,14 @@ int dfs_store_wrap_host(dfs_ctx* c, int32_t dtype, int32_t ndim, const int64_t* 
     void* dev = nullptr;
     void* dev_last = nullptr;
     char* last = (char*)host_ptr + (bytes ? bytes - 1 : 0);
+    // only page-locked host memory (cudaHostAlloc / cudaHostRegister): its
+    // pages stay resident; pageable memory can be unmapped under a kernel
+    cudaPointerAttributes a0{}, a1{};
+    if (cudaPointerGetAttributes(&a0, host_ptr) != cudaSuccess || a0.type != cudaMemoryTypeHost ||
+        cudaPointerGetAttributes(&a1, last) != cudaSuccess || a1.type != cudaMemoryTypeHost) {
+      cudaGetLastError();
+      return fail(c, DFS_ERR_INVALID, "not page-locked host memory");
+    }
     if (cudaHostGetDevicePointer(&dev, host_ptr, 0) != cudaSuccess || !dev ||
         cudaHostGetDevicePointer(&dev_last, last, 0) != cudaSuccess ||
         (char*)dev_last - (char*)dev != last - (char*)host_ptr) {

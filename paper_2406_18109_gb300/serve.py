@@ -161,6 +161,7 @@ class Server:
         self.op_users: dict[int, int] = {}
         self.used = 0
         self.stats = Stats()
+        self._inflight = []   # host buffers read by work not yet synchronised
 
     # ----------------------------------------------------------- operators
     def _need(self, req, admitted_now) -> int:
@@ -231,7 +232,9 @@ class Server:
                                nbytes=request_bytes(kind, req["size"])))
             rt.batch_next()
         rt.batch_end()
-        del items, xs_all               # x* of every new solve
+        # the set-up runs asynchronously: keep the host data it reads (and
+        # their stores) until the next synchronisation of the stream
+        self._inflight.append((items, xs_all))
         return sols
 
     def _iterate(self, kind, sols) -> None:
@@ -347,7 +350,8 @@ class Server:
                 arrs = []
                 for s in sols:
                     arrs += [s.bb, s.st.rho if s.res.kind == "cg" else s.st.rr]
-                vals = self.rt.read_scalars(arrs)
+                vals = self.rt.read_scalars(arrs)  # synchronises the stream
+                self._inflight.clear()
                 retire = []
                 for i, s in enumerate(sols):
                     bb, rr = vals[2 * i], vals[2 * i + 1]
@@ -381,6 +385,8 @@ class Server:
                         s.res.done = t
                         finished.append(s.res)
                 del hold
+        self.rt.sync()
+        self._inflight.clear()
         return finished
 
     def _advance(self, dt: float) -> None:
