@@ -581,10 +581,16 @@ def serving_alg_bytes(results) -> int:
 
 def run_serving(args, torch, stream, sms, cache, dev):
     """The serving loop under its Poisson arrival stream, then again at a
-    fraction of the throughput it sustained; one JSON line."""
+    fraction of the throughput it sustained; one JSON line.  With N GPUs every
+    rank serves its own stream (replicas; seeds differ by rank) and the value
+    is the requests of all ranks over the slowest rank's time."""
     from paper_2406_18109_gb300 import arrays as A
+    from paper_2406_18109_gb300 import dist as D
     from paper_2406_18109_gb300 import serve as SV
     cfg = configs.SERVING
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    seed = D.rank_seed(cfg["seed"], rank)
     count = args.requests or cfg["count"]
     peaks = load_peaks()
     rt = A.Runtime(device=dev, stream=stream.cuda_stream, time_launches=True, tile=cfg["tile"],
@@ -607,7 +613,7 @@ def run_serving(args, torch, stream, sms, cache, dev):
     srv.run(warm, inputs.serving_payload)
 
     def one_run(mean_gap_s):
-        reqs = inputs.serving_requests(count, seed=cfg["seed"], mean_gap_s=mean_gap_s)
+        reqs = inputs.serving_requests(count, seed=seed, mean_gap_s=mean_gap_s)
         # request data arrive with the requests, in mapped page-locked host
         # buffers the server reads in place: generated (in parallel, the
         # generators release the GIL) before the clock starts
@@ -651,7 +657,13 @@ def run_serving(args, torch, stream, sms, cache, dev):
         summ["dominant_kernel"] = {"name": top[0], "ms": top[1]["ms"], "launches": top[1]["launches"]}
         return summ, clk
 
+    if world > 1:
+        torch.distributed.barrier()
     offered, clk = one_run(cfg["mean_gap_ms"] * 1e-3)
+    if world > 1:
+        # whole-job throughput: every rank's requests over the slowest rank's time
+        v, ms, _ = D.combine(offered["wall_s"] * 1e3, offered["requests"], device="cuda")
+        offered["sustained_rps_all_ranks"] = v
     cap = offered["sustained_rps"]
     at_load = None
     if not args.quick and cap > 0:
@@ -663,27 +675,29 @@ def run_serving(args, torch, stream, sms, cache, dev):
                 "kernel_ms": offered["kernel_ms"], "launches": offered["launches"],
                 "algorithmic_bytes_per_launch": offered["algorithmic_bytes"] / max(1, offered["launches"])}
     cpu = None
-    if not args.quick:
+    if not args.quick and rank == 0:
         v, u, sample = oracle_rate("serve", budget_s=10.0)
         cpu = {"value": v, "unit": u, "cores": 1, "kind": "oracle", "sample": sample}
     n = offered["requests"]
-    line = {"metric": METRIC["serve"][0], "value": offered["sustained_rps"], "unit": "requests/s", "n_gpus": 1,
+    value = offered.get("sustained_rps_all_ranks", offered["sustained_rps"])
+    line = {"metric": METRIC["serve"][0], "value": value, "unit": "requests/s", "n_gpus": world,
             "steps": n, "warmup": len(warm), "ms_per_step": offered["wall_s"] * 1e3 / max(1, n),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
             "data": "synthetic (seeded generators of synth/inputs.py)",
             "config": {"workload": WORKLOAD["serve"], "requests": n, "l2": "inputs larger than L2",
                        "launch": "continuous batching: one batched persistent launch per solver kind per "
                                  "iteration, dfs_batch_repeat within a tick",
-                       "parallelism": "replicas x1"},
+                       "parallelism": f"replicas x{world}"},
             "p50_ms": offered["p50_ms"], "p99_ms": offered["p99_ms"],
-            "e2e": {"value": offered["sustained_rps"], "unit": "requests/s",
+            "e2e": {"value": value, "unit": "requests/s",
                     "h2d_bytes_per_step": offered["h2d_bytes"] / max(1, n),
                     "d2h_bytes_per_step": offered["d2h_bytes"] / max(1, n),
                     "note": "a step is one request; payload upload and result download are inside the loop"},
             "gpu_launches": offered["launches"], "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
             "serving": {"offered_load": offered, "at_fraction_of_capacity": at_load,
                         "load_fraction": cfg["load_fraction"], "operator_load_s": t_load}}
-    print(json.dumps(line))
+    if rank == 0:
+        print(json.dumps(line))
 
 
 def main():
@@ -774,6 +788,8 @@ def main():
         return
     if args.workload == "serve":
         run_serving(args, torch, stream, sms, cache, dev)
+        if world > 1:
+            torch.distributed.destroy_process_group()
         return
 
     metric, unit, dtype = METRIC[args.workload]

@@ -10,6 +10,7 @@ a GPU driver (the analysis-only context and symbol checks still work there).
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import hashlib
 import os
 import shutil
@@ -60,10 +61,21 @@ def _inputs_digest() -> str:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compiles libdiffuse.so if its sources changed; returns its path."""
+    """Compiles libdiffuse.so if its sources changed; returns its path.
+    Processes that build at once (one per rank) take turns on a file lock, so
+    the later ones find the library up to date."""
+    os.makedirs(LIBDIR, exist_ok=True)
+    with open(os.path.join(LIBDIR, ".build.lock"), "w") as lk:
+        fcntl.flock(lk, fcntl.LOCK_EX)
+        try:
+            return _build_locked(force, verbose)
+        finally:
+            fcntl.flock(lk, fcntl.LOCK_UN)
+
+
+def _build_locked(force: bool, verbose: bool) -> str:
     cuda = cuda_home()
     nvcc = os.path.join(cuda, "bin", "nvcc")
-    os.makedirs(LIBDIR, exist_ok=True)
     os.makedirs(OBJDIR, exist_ok=True)
     _embed_device_header()
     digest = _inputs_digest()
