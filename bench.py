@@ -331,7 +331,7 @@ class Arm:
                 W.cg_iteration_inplace(self.Am, self.s)
             rt.flush()
         if self.autotune:
-            self._tune(window, {"tile": [256, 512, 1024, 2048], "block": [128, 256, 512], "unroll": [1, 2]},
+            self._tune(window, {"tile": [256, 432, 512, 864, 1024, 2048], "block": [128, 256, 512], "unroll": [1, 2]},
                        f"cg-{cfg['m']}-{ipf}", 5, "ms_per_window")
         window()
         rt.capture_begin()

@@ -120,6 +120,7 @@ class Gen {
   struct Red { int slot; int64_t root; int dtype; int64_t points; };
   std::vector<Red> pending_red;           // reductions awaiting finalisation
   int nbar = 0;
+  int nbc = 0;  // shared broadcast slots of finished reductions
 
   const LaunchRoot& R(int64_t root) const { return S.roots[S.root_index.at(root)]; }
   bool temp_in(int g, int64_t root) const;
@@ -133,6 +134,7 @@ class Gen {
   void emit_vector_group(int g);
   void emit_nest(int g, const Nest& n, const std::string& red_pt, bool flat);
   void emit_finalise(const char* indent);
+  int emit_warp0_scalars(int g);
   void realign(Nest& n, int vec);
   std::vector<Nest> nests_of(int g);
   std::string imm_expr(int task, int arg, int dt);
@@ -319,11 +321,12 @@ void Gen::emit_group(int g) {
     emit_vector_group(g);
 }
 
-// A group of scalar tasks: every thread of every CTA evaluates it on the
-// register copies of the 0-d stores.
+// A group of scalar tasks, evaluated on the register copies of the 0-d
+// stores: by every thread at the start of a launch, by warp 0 after a grid
+// barrier (emit_warp0_scalars).
 void Gen::emit_scalar_group(int g) {
   const Group& G = S.groups[g];
-  o << "    { // group " << g << " (scalar, replicated)\n";
+  o << "    { // group " << g << " (scalar)\n";
   for (int i = G.begin; i < G.end; ++i) {
     const Task& t = S.tasks[i];
     const Arg& out = t.args.back();
@@ -839,19 +842,81 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
 }
 
 // Finishes every pending reduction: sum of the per-point partials in point
-// order, folded into the register copy of the target.
+// order, folded into the register copy of the target.  Warp 0 sums (the
+// order of sum_partials) and hands the totals to the CTA through shared
+// memory: FP64 arithmetic is scarce on GB300 (about two lane operations per
+// SM and clock), and every warp repeating the same sum cost about 0.5 us per
+// reduction in an L2-resident CG iteration.  Called where every thread of the
+// CTA arrives (after a grid barrier, or in the last CTA).
 void Gen::emit_finalise(const char* ind) {
+  if (pending_red.empty()) return;
+  std::vector<std::string> bc;
   for (const Red& r : pending_red) {
+    bc.push_back("bc" + std::to_string(nbc++));
+    o << ind << "__shared__ " << T(r.dtype) << " " << bc.back() << ";\n";
+  }
+  o << ind << "if (threadIdx.x < 32) {\n";
+  for (size_t j = 0; j < pending_red.size(); ++j) {
+    const Red& r = pending_red[j];
+    o << ind << "  const " << T(r.dtype) << " " << bc[j] << "_t = sum_partials((const " << T(r.dtype)
+      << "*)P.partials + " << r.slot << "LL * P.red_stride, " << r.points << "LL);\n";
+    o << ind << "  if (threadIdx.x == 0) " << bc[j] << " = " << bc[j] << "_t;\n";
+  }
+  o << ind << "}\n" << ind << "__syncthreads();\n";
+  for (size_t j = 0; j < pending_red.size(); ++j) {
+    const Red& r = pending_red[j];
     const std::string nm = sreg.at(r.root);
-    o << ind << "{ const " << T(r.dtype) << " tot = sum_partials((const " << T(r.dtype) << "*)P.partials + "
-      << r.slot << "LL * P.red_stride, " << r.points << "LL);\n";
     if (have[r.root])
-      o << ind << "  " << nm << " = op_add(" << nm << ", tot); }\n";
+      o << ind << nm << " = op_add(" << nm << ", " << bc[j] << ");\n";
     else
-      o << ind << "  " << nm << " = tot; }\n";
+      o << ind << nm << " = " << bc[j] << ";\n";
     have[r.root] = true;
   }
   pending_red.clear();
+}
+
+// After a grid barrier: the pending reductions and the scalar groups that
+// follow (g, g+1, ... while scalar) run on warp 0 alone, and every 0-d value
+// they set reaches the CTA's other warps through shared memory.  The values
+// are those every thread would compute (the same operations on the same
+// register copies); only the repetition goes.  FP64 arithmetic is scarce on
+// GB300 (about two lane operations per SM and clock), and eight warps
+// repeating a 128-partial sum and an IEEE division cost about 1 us per CG
+// phase at 256^2.  Returns the first group after the scalar run.
+int Gen::emit_warp0_scalars(int g) {
+  int h = g;
+  while (h < (int)S.groups.size() && S.groups[h].scalar) ++h;
+  std::vector<int64_t> set;
+  auto add = [&](int64_t r) {
+    if (std::find(set.begin(), set.end(), r) == set.end()) set.push_back(r);
+  };
+  for (const Red& r : pending_red) add(r.root);
+  for (int k = g; k < h; ++k)
+    for (int i = S.groups[k].begin; i < S.groups[k].end; ++i) add(S.tasks[i].args.back().root);
+  if (set.empty()) return g;
+  std::map<int64_t, std::string> bc;
+  for (int64_t r : set) {
+    bc[r] = "bc" + std::to_string(nbc++);
+    o << "    __shared__ " << T(R(r).dtype) << " " << bc[r] << ";\n";
+  }
+  o << "    if (threadIdx.x < 32) {\n";
+  for (const Red& r : pending_red) {
+    const std::string nm = sreg.at(r.root);
+    o << "      { const " << T(r.dtype) << " tot = sum_partials((const " << T(r.dtype) << "*)P.partials + "
+      << r.slot << "LL * P.red_stride, " << r.points << "LL);\n";
+    if (have[r.root])
+      o << "        " << nm << " = op_add(" << nm << ", tot); }\n";
+    else
+      o << "        " << nm << " = tot; }\n";
+    have[r.root] = true;
+  }
+  pending_red.clear();
+  for (int k = g; k < h; ++k) emit_scalar_group(k);
+  o << "      if (threadIdx.x == 0) {\n";
+  for (int64_t r : set) o << "        " << bc[r] << " = " << sreg.at(r) << ";\n";
+  o << "      }\n    }\n    __syncthreads();\n";
+  for (int64_t r : set) o << "    " << sreg.at(r) << " = " << bc[r] << ";\n";
+  return h;
 }
 
 KernelCode Gen::run() {
@@ -867,7 +932,11 @@ KernelCode Gen::run() {
       ++nbar;
       o << "    if (!grid_barrier(ctl, " << nbar << "u, P.timeout_ns"
         << (S.debug_skip == nbar ? ", blockIdx.x != 0" : "") << ")) break;\n";
-      emit_finalise("    ");
+      const int h = emit_warp0_scalars(g);
+      if (h > g) {
+        g = h - 1;
+        continue;
+      }
     }
     emit_group(g);
   }
