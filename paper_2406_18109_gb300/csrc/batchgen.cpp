@@ -516,7 +516,7 @@ bool BatchGen::run(BatchCode& out, std::string& why) {
     if (r.param >= 0) bc.ptr_roots[r.param] = r.root;
   for (const LaunchRoot& r : S.roots) produced[r.root] = false;
 
-  o << "  __shared__ double red_buf[" << S.block / 32 << "];\n";
+  o << "  __shared__ double red_buf[" << S.block << "];\n";
   o << "  __shared__ i64 s_ticket;\n";
   o << "  Ctl* ctl = P.ctl;\n  const i64 NI = P.ninst;\n";
   o << "  do {\n";

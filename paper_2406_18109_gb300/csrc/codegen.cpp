@@ -923,7 +923,7 @@ KernelCode Gen::run() {
   emit_params();
   std::ostringstream body;
   // the kernel body is generated into `o`; header assembled afterwards
-  o << "  __shared__ double red_buf[" << S.block / 32 << "];\n";
+  o << "  __shared__ double red_buf[" << S.block << "];\n";
   o << "  Ctl* ctl = P.ctl;\n";
   emit_prologue();
   o << "  do {\n";

@@ -21,7 +21,7 @@ __device__ T all_ops(T a, T b) {
 
 extern "C" __global__ void dfs_template_check(const float* x, const double* y, const int* rowptr, const int* col,
                                               float* out32, double* out64, Ctl* ctl, long long n) {
-  __shared__ double buf[32];
+  __shared__ double buf[1024];
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   float a = 0.f;
   double b = 0.0;

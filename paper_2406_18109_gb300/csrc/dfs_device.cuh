@@ -245,11 +245,14 @@ __device__ __forceinline__ u32 atom_acq_rel_add_u32(u32* p, u32 v) {
 // CTAs have arrived.  The CTA's writes are ordered before its arrival by the
 // block barrier and the arrival's release; the acquire load that sees the
 // last arrival orders every CTA's writes before the reads that follow (the
-// PTX memory model's release/acquire pattern at gpu scope; measured on GB300
-// at 1.27 us per barrier over 128 CTAs against 1.54 us with full fences
-// around a relaxed add).  The wait gives up after `timeout_ns` (or as soon as
-// any CTA has recorded an error), records the failure and returns false;
-// callers then skip the rest of the kernel, so no CTA ever waits forever.
+// PTX memory model's release/acquire pattern at gpu scope).  Measured on
+// GB300 over 128 CTAs: 1.28 us per barrier, against 1.43 us with a 64 ns
+// sleep between polls and 1.54 us with full fences around a relaxed add; one
+// flag per CTA polled by every CTA (1.3-7.8 us from 128 to 608 CTAs) or by a
+// master that then releases the rest (2.9-4.7 us) was slower.  The wait
+// gives up after `timeout_ns` (or as soon as any CTA has recorded an error),
+// records the failure and returns false; callers then skip the rest of the
+// kernel, so no CTA ever waits forever.
 // `arrive` is false only under the test hook that withholds one arrival.
 __device__ __forceinline__ bool grid_barrier(Ctl* ctl, u32 k, u64 timeout_ns, bool arrive = true) {
   __shared__ int s_ok;
@@ -266,7 +269,6 @@ __device__ __forceinline__ bool grid_barrier(Ctl* ctl, u32 k, u64 timeout_ns, bo
         ok = 0;
         break;
       }
-      __nanosleep(64);
     }
     s_ok = ok;
   }
@@ -315,16 +317,20 @@ template <typename T> __device__ __forceinline__ T warp_sum_xor(T v) {
 }
 
 // Sum of one value per thread in a fixed order; the result is returned to
-// thread 0 only.  `buf` holds blockDim.x/32 values.
+// thread 0 only.  `buf` holds blockDim.x values.  Every thread parks its value
+// in shared memory and warp 0 alone adds: lane l sums the values of lanes l of
+// warps 0, 1, ... in order, then a xor butterfly combines the 32 lane sums.
+// FP64 adds are scarce on GB300 (about two lane operations per SM and clock):
+// a butterfly in every warp cost 45 warp instructions per 256-thread block,
+// this 12.
 template <typename T> __device__ __forceinline__ T block_sum(T v, T* buf) {
-  v = warp_sum_xor(v);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) buf[w] = v;
+  buf[threadIdx.x] = v;
   __syncthreads();
   T r = T(0);
-  if (w == 0) {
+  if (threadIdx.x < 32) {
     const int nw = blockDim.x >> 5;
-    r = (l < nw) ? buf[l] : T(0);
+    r = buf[threadIdx.x];
+    for (int w = 1; w < nw; ++w) r += buf[threadIdx.x + 32 * w];
     r = warp_sum_xor(r);
   }
   __syncthreads();

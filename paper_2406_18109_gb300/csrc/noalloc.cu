@@ -38,7 +38,7 @@ static __device__ __align__(256) dfs::Ctl g_ctl;
 __global__ void __launch_bounds__(kBlock) dot_noalloc_kernel(const double* __restrict__ x,
                                                              const double* __restrict__ y, long long n,
                                                              double* out, double* partials, dfs::Ctl* ctl) {
-  __shared__ double buf[kBlock / 32];
+  __shared__ double buf[kBlock];
   const long long npts = (n + kTile - 1) / kTile;
   for (long long pt = blockIdx.x; pt < npts; pt += gridDim.x) {
     const long long lo = pt * kTile;
