@@ -902,6 +902,23 @@ def main():
                 "frac": achieved / peaks["hbm_gbs"], "traffic": None,
                 "peak_source": peaks["source"], "kernel": fused["dominant"], "kernel_ms": kern_ms,
                 "launches": fused["dominant_launches"], "algorithmic_bytes_per_launch": alg_bytes}
+    fp64_ops = None
+    if args.workload == "cg":
+        fp64_ops = nnz + 8 * nn
+    elif args.workload == "batched" and cfg["dtype"] == "f64":
+        fp64_ops = nnz + 8 * rows
+    if fp64_ops is not None:
+        # FP64 is a scarce pipe on GB300 (nominal 1.25 TFLOP/s counting an FMA
+        # as two: about two lane operations per SM and clock).  Lane operations
+        # per iteration: one FMA per stored entry (SpMV) and eight per row (the
+        # two dots, the x, r and p updates at two operations each but the dots'
+        # one)
+        sm_max = clk.get("sm_max_mhz") or 2070.0
+        peak_ops = sms * 2 * sm_max * 1e6 / 1e9
+        ach_ops = fp64_ops / (kern_ms / 1e3) / 1e9 if kern_ms > 0 else 0.0
+        roofline["fp64"] = {"achieved": ach_ops, "peak": peak_ops, "unit": "G lane-ops/s", "frac": ach_ops / peak_ops,
+                            "ops_per_launch": fp64_ops,
+                            "peak_source": f"derived: {sms} SMs x 2 FP64 lanes x {sm_max:.0f} MHz (1.25 TFLOP/s nominal)"}
     if args.workload == "bs":
         # issue-bound: instructions per option (ncu) x options / kernel time,
         # against SMs x 4 sub-partitions x 32 lanes x maximum SM clock
