@@ -61,6 +61,38 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
+def host_link_peak(torch, mib: int = 256, reps: int = 3) -> dict:
+    """Measured host<->device copy bandwidth (GB/s): pinned-host copies each
+    way alone, and both ways at once on two streams (the ceiling of an end to
+    end step that both uploads and downloads).  Best of `reps`."""
+    n = mib << 20
+    h_in = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+    h_out = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+    d_in = torch.empty(n, dtype=torch.uint8, device="cuda")
+    d_out = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    s0, s1 = torch.cuda.Stream(), torch.cuda.Stream()
+    best = {"h2d": 0.0, "d2h": 0.0, "both": 0.0}
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    def both():
+        with torch.cuda.stream(s0):
+            d_in.copy_(h_in, non_blocking=True)
+        with torch.cuda.stream(s1):
+            h_out.copy_(d_out, non_blocking=True)
+    for _ in range(reps + 1):
+        best["h2d"] = max(best["h2d"], n / timed(lambda: d_in.copy_(h_in, non_blocking=True)) / 1e9)
+        best["d2h"] = max(best["d2h"], n / timed(lambda: h_out.copy_(d_out, non_blocking=True)) / 1e9)
+        best["both"] = max(best["both"], 2 * n / timed(both) / 1e9)
+    del h_in, h_out, d_in, d_out
+    return best
+
+
 class Clocks:
     """Samples nvidia-smi during the timed region."""
 
@@ -870,6 +902,14 @@ def main():
             e = ea.run(k3, 2)
             extra["e2e"] = {"value": e["units"] / (e["ms"] / 1e3), "unit": unit,
                             "h2d_bytes_per_step": ea.h2d, "d2h_bytes_per_step": ea.d2h}
+            # the host link as a roofline of the end-to-end step: bytes that
+            # cross it per step over the step time, against copies both ways
+            # at once, measured now
+            link = host_link_peak(torch)
+            moved = (ea.h2d + ea.d2h) / (e["ms"] / 1e3 / k3) / 1e9
+            extra["e2e"]["roofline"] = {"bound": "host link", "achieved": moved, "peak": link["both"], "unit": "GB/s",
+                                        "frac": moved / link["both"], "peak_source": "measured: pinned copies both ways "
+                                        "at once (h2d %.0f, d2h %.0f GB/s alone)" % (link["h2d"], link["d2h"])}
         finally:
             ea.close()
 
