@@ -687,6 +687,7 @@ def run_serving(args, torch, stream, sms, cache, dev):
                      "peak_device_bytes": srv.stats.peak_bytes, "max_active": dict(srv.stats.max_active)})
         top = max(kd.items(), key=lambda kv: kv[1]["ms"]) if kd else (None, {"ms": 0.0, "launches": 0})
         summ["dominant_kernel"] = {"name": top[0], "ms": top[1]["ms"], "launches": top[1]["launches"]}
+        summ["result_buffers"] = dict(srv.stats_pool)
         return summ, clk
 
     if world > 1:

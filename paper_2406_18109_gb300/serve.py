@@ -18,6 +18,11 @@ Black-Scholes option batches) arrive over time.  The loop runs in ticks:
      solves that reached ||r|| <= tol ||b|| (or max_iters): copy x back to the
      host, free its stores, release its budget.
 
+Results are delivered into page-locked host buffers taken at set-up time
+(while the GPU iterates) from a pool keyed by shape and dtype; when the
+caller does not keep outputs, a buffer returns to the pool once its result
+has been handed over, so a steady stream pins no new host memory.
+
 Requests that arrive while others are on the GPU join the next tick's batches,
 so their work shares launches with the solves already running.  A solve's
 iterations, its convergence test (always after a multiple of iters_per_tick
@@ -116,6 +121,7 @@ class _Solve:
     bb: A.Array
     it: int = 0
     nbytes: int = 0
+    out: object = None      # page-locked host buffer the solution is delivered into
 
 
 @dataclass
@@ -162,6 +168,11 @@ class Server:
         self.used = 0
         self.stats = Stats()
         self._inflight = []   # host buffers read by work not yet synchronised
+        # page-locked result buffers, reused once their results are handed
+        # over when outputs are not kept (pinning host memory takes tens of
+        # milliseconds per 100 MB, which the GPU would otherwise wait out)
+        self._pool: dict[tuple, list] = {}
+        self.stats_pool = {"allocated": 0, "reused": 0}
 
     # ----------------------------------------------------------- operators
     def _need(self, req, admitted_now) -> int:
@@ -193,6 +204,22 @@ class Server:
         self.ops[m] = Am
         self.used += operator_bytes(m)
         return Am
+
+    # ----------------------------------------------------- result buffers
+    def _out_buffer(self, shape, dtype):
+        key = (tuple(shape), np.dtype(dtype).str)
+        free = self._pool.get(key)
+        if free:
+            self.stats_pool["reused"] += 1
+            return free.pop()
+        self.stats_pool["allocated"] += 1
+        return A.Runtime.host_empty(shape, dtype)
+
+    def _recycle(self, buf) -> None:
+        """Back to the pool once its result has been handed over (only when
+        results are not kept, so no caller holds it)."""
+        if not self.keep and buf is not None:
+            self._pool.setdefault((tuple(buf.shape), buf.dtype.str), []).append(buf)
 
     # ---------------------------------------------------------------- ticks
     def _now(self, t0: float) -> float:
@@ -229,7 +256,8 @@ class Server:
             del b                       # a temporary of the set-up window
             res = Result(req["rid"], kind, req["size"], req["arrival"], admitted=now)
             sols.append(_Solve(req, res, req["size"], Am, st, bb,
-                               nbytes=request_bytes(kind, req["size"])))
+                               nbytes=request_bytes(kind, req["size"]),
+                               out=self._out_buffer(st.x.shape, st.x.dtype)))
             rt.batch_next()
         rt.batch_end()
         # the set-up runs asynchronously: keep the host data it reads (and
@@ -268,20 +296,23 @@ class Server:
         results, hold = [], []
         rt.batch_begin()
         for req, S, K, T in data:
-            hc = A.Runtime.host_empty((req["size"],), np.float32)
-            hp = A.Runtime.host_empty((req["size"],), np.float32)
+            hc = self._out_buffer((req["size"],), np.float32)
+            hp = self._out_buffer((req["size"],), np.float32)
             wc, wp = rt.wrap_host(hc), rt.wrap_host(hp)
             call, put = W.black_scholes(S, K, T, self.bs_rate, self.bs_sigma)
             wc[...] = call
             wp[...] = put
             del call, put
-            hold.append((wc, wp))
+            hold.append((wc, wp, hc, hp))
             res = Result(req["rid"], "bs", req["size"], req["arrival"], admitted=now)
             res.output = (hc, hp) if self.keep else None
             results.append(res)
             rt.batch_next()
         rt.batch_end()
         rt.sync()
+        for _, _, hc, hp in hold:
+            self._recycle(hc)
+            self._recycle(hp)
         return results
 
     # ------------------------------------------------------------------ run
@@ -366,7 +397,7 @@ class Server:
                 if retire:
                     self.rt.batch_begin()
                 for s in retire:
-                    hx = A.Runtime.host_empty(s.st.x.shape, s.st.x.dtype)
+                    hx = s.out
                     w = self.rt.wrap_host(hx)
                     w[...] = s.st.x
                     hold.append(w)
@@ -385,6 +416,9 @@ class Server:
                         s.res.done = t
                         finished.append(s.res)
                 del hold
+                for s in retire:
+                    self._recycle(s.out)
+                    s.out = None
         self.rt.sync()
         self._inflight.clear()
         return finished

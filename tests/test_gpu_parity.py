@@ -428,6 +428,49 @@ def test_fig6_example_values_and_temporary():
     assert allocs == 3                           # w, v and the norm's 0-d result; z stays in registers
 
 
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_scalar_chains_between_reductions(dtype):
+    """Reductions finished after a grid barrier feed chains of scalar tasks
+    (divide, square root, multiply, maximum) whose results the next vector
+    phase broadcasts: in the fused kernel warp 0 computes them and hands them
+    to the CTA through shared memory.  All three execution modes agree bit
+    for bit, and every value matches the FP64 definition within 1e-12 (FP64)
+    or 1e-5 (FP32) relative to the magnitudes involved."""
+    n = 10_007                                   # 10 tiles of 1024 and a ragged tail
+    x, y, z = (inputs.uniform(s, 0.5, 2.0, n).astype(dtype) for s in (31, 32, 33))
+    res = {}
+    for mode in MODES:
+        with gpu_runtime(mode, tile=1024) as rt:
+            X, Y, Z = rt.array(x), rt.array(y), rt.array(z)
+            s1 = A.dot(X, Y)
+            s2 = s1 / A.dot(Z, Z)
+            s3 = A.sqrt(s2) * s1
+            Wv = X * s2 + Y
+            s4 = A.dot(Wv, Wv)
+            s5 = A.maximum(s4 / s3, s2)
+            V = Wv - Z * s5
+            res[mode] = [Wv.numpy(), V.numpy()] + [np.asarray(a.numpy()) for a in (s1, s2, s3, s4, s5)]
+            if mode == "persistent":
+                assert rt.stats()["launches"] == 1
+    for mode in MODES[1:]:
+        for k, (a, b) in enumerate(zip(res[mode], res["persistent"])):
+            assert np.array_equal(_bits(np.atleast_1d(a)), _bits(np.atleast_1d(b))), (mode, k)
+    tol = 1e-5 if dtype == np.float32 else 1e-12
+    xd, yd, zd = (v.astype(np.float64) for v in (x, y, z))
+    s1o = float(np.dot(xd, yd))
+    s2o = s1o / float(np.dot(zd, zd))
+    s3o = np.sqrt(s2o) * s1o
+    Wo = xd * s2o + yd
+    s4o = float(np.dot(Wo, Wo))
+    s5o = max(s4o / s3o, s2o)
+    Vo = Wo - zd * s5o
+    Wg, Vg, *sg = res["persistent"]
+    for got, want in zip(sg, (s1o, s2o, s3o, s4o, s5o)):
+        assert abs(float(got) - want) <= tol * abs(want), (got, want)
+    assert np.all(np.abs(Wg - Wo) <= tol * np.abs(Wo))
+    assert np.all(np.abs(Vg - Vo) <= tol * (np.abs(Wo) + np.abs(zd * s5o)))
+
+
 # ------------------------------------------------------- runtime behaviour
 def test_temporaries_are_never_allocated():
     n = 1 << 16

@@ -83,3 +83,29 @@ def test_tick_clock_and_summary():
     assert s["requests"] == 100 and s["sustained_rps"] == 50.0
     assert abs(s["p50_ms"] - 505.0) < 1e-9 and abs(s["p99_ms"] - 990.1) < 1e-9
     assert s["cg"]["count"] == 100 and s["unconverged"] == 0
+
+
+def test_result_buffers_are_reused_only_when_outputs_are_not_kept(monkeypatch):
+    """Page-locked result buffers come from a pool keyed by shape and dtype;
+    a buffer goes back to it after its result is handed over, and never when
+    the caller keeps the outputs."""
+    made = []
+
+    def fake_host_empty(shape, dtype):
+        a = np.empty(shape, dtype)
+        made.append(a)
+        return a
+    monkeypatch.setattr(serve.A.Runtime, "host_empty", staticmethod(fake_host_empty))
+    for keep in (False, True):
+        made.clear()
+        srv = serve.Server(None, None, keep_outputs=keep)
+        a = srv._out_buffer((8,), np.float64)
+        srv._recycle(a)
+        b = srv._out_buffer((8,), np.float64)
+        c = srv._out_buffer((8,), np.float32)            # another dtype: a new buffer
+        srv._recycle(b)
+        d = srv._out_buffer((4,), np.float64)            # another shape: a new buffer
+        assert (b is a) == (not keep)
+        assert c is not a and d is not a and d is not c
+        assert len(made) == (3 if not keep else 4)
+        assert srv.stats_pool == {"allocated": len(made), "reused": 1 if not keep else 0}
