@@ -663,6 +663,7 @@ def run_serving(args, torch, stream, sms, cache, dev):
             data = dict(zip([r["rid"] for r in reqs], ex.map(pinned, reqs)))
         rt.sync()
         s0 = rt.stats()
+        h0 = dict(srv.stats.host_s)
         clocks = Clocks(dev)
         clocks.start()
         torch.cuda.synchronize()
@@ -688,6 +689,7 @@ def run_serving(args, torch, stream, sms, cache, dev):
         top = max(kd.items(), key=lambda kv: kv[1]["ms"]) if kd else (None, {"ms": 0.0, "launches": 0})
         summ["dominant_kernel"] = {"name": top[0], "ms": top[1]["ms"], "launches": top[1]["launches"]}
         summ["result_buffers"] = dict(srv.stats_pool)
+        summ["host_s_by_part"] = {k: v - h0.get(k, 0.0) for k, v in srv.stats.host_s.items()}
         return summ, clk
 
     if world > 1:

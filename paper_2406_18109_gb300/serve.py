@@ -19,9 +19,10 @@ Black-Scholes option batches) arrive over time.  The loop runs in ticks:
      host, free its stores, release its budget.
 
 Results are delivered into page-locked host buffers taken at set-up time
-(while the GPU iterates) from a pool keyed by shape and dtype; when the
-caller does not keep outputs, a buffer returns to the pool once its result
-has been handed over, so a steady stream pins no new host memory.
+(while the GPU iterates) from a pool keyed by dtype and power-of-two
+capacity; when the caller does not keep outputs, a buffer returns to the pool
+once its result has been handed over, so a steady stream pins little new
+host memory.
 
 Requests that arrive while others are on the GPU join the next tick's batches,
 so their work shares launches with the solves already running.  A solve's
@@ -132,6 +133,15 @@ class Stats:
     max_active: dict = field(default_factory=dict)
     peak_bytes: int = 0
     evictions: int = 0
+    # host seconds per part of a tick: admission, option pricing (launch and
+    # wait), launching the iterations, set-up of new solves, the convergence
+    # read (mostly waiting for the tick's GPU work) and retirement
+    host_s: dict = field(default_factory=dict)
+
+    def add(self, part: str, t0: float) -> float:
+        t = time.perf_counter()
+        self.host_s[part] = self.host_s.get(part, 0.0) + (t - t0)
+        return t
 
 
 class Server:
@@ -206,20 +216,24 @@ class Server:
         return Am
 
     # ----------------------------------------------------- result buffers
-    def _out_buffer(self, shape, dtype):
-        key = (tuple(shape), np.dtype(dtype).str)
+    def _out_buffer(self, n: int, dtype):
+        """A 1-D page-locked buffer of at least n elements: its capacity is
+        the next power of two, so requests of similar sizes share buffers.
+        Callers use buf[:n]."""
+        cap = 1 << max(0, int(n) - 1).bit_length()
+        key = (cap, np.dtype(dtype).str)
         free = self._pool.get(key)
         if free:
             self.stats_pool["reused"] += 1
             return free.pop()
         self.stats_pool["allocated"] += 1
-        return A.Runtime.host_empty(shape, dtype)
+        return A.Runtime.host_empty((cap,), dtype)
 
     def _recycle(self, buf) -> None:
         """Back to the pool once its result has been handed over (only when
         results are not kept, so no caller holds it)."""
         if not self.keep and buf is not None:
-            self._pool.setdefault((tuple(buf.shape), buf.dtype.str), []).append(buf)
+            self._pool.setdefault((len(buf), buf.dtype.str), []).append(buf)
 
     # ---------------------------------------------------------------- ticks
     def _now(self, t0: float) -> float:
@@ -257,7 +271,7 @@ class Server:
             res = Result(req["rid"], kind, req["size"], req["arrival"], admitted=now)
             sols.append(_Solve(req, res, req["size"], Am, st, bb,
                                nbytes=request_bytes(kind, req["size"]),
-                               out=self._out_buffer(st.x.shape, st.x.dtype)))
+                               out=self._out_buffer(st.x.shape[0], st.x.dtype)))
             rt.batch_next()
         rt.batch_end()
         # the set-up runs asynchronously: keep the host data it reads (and
@@ -296,23 +310,24 @@ class Server:
         results, hold = [], []
         rt.batch_begin()
         for req, S, K, T in data:
-            hc = self._out_buffer((req["size"],), np.float32)
-            hp = self._out_buffer((req["size"],), np.float32)
+            bc = self._out_buffer(req["size"], np.float32)
+            bp = self._out_buffer(req["size"], np.float32)
+            hc, hp = bc[:req["size"]], bp[:req["size"]]
             wc, wp = rt.wrap_host(hc), rt.wrap_host(hp)
             call, put = W.black_scholes(S, K, T, self.bs_rate, self.bs_sigma)
             wc[...] = call
             wp[...] = put
             del call, put
-            hold.append((wc, wp, hc, hp))
+            hold.append((wc, wp, bc, bp))
             res = Result(req["rid"], "bs", req["size"], req["arrival"], admitted=now)
             res.output = (hc, hp) if self.keep else None
             results.append(res)
             rt.batch_next()
         rt.batch_end()
         rt.sync()
-        for _, _, hc, hp in hold:
-            self._recycle(hc)
-            self._recycle(hp)
+        for _, _, bc, bp in hold:
+            self._recycle(bc)
+            self._recycle(bp)
         return results
 
     # ------------------------------------------------------------------ run
@@ -325,8 +340,10 @@ class Server:
         active: dict[str, list[_Solve]] = {k: [] for k in SOLVERS}
         finished: list[Result] = []
         t0 = self.clock() if self.clock else time.perf_counter()
+        st = self.stats
         while qi < len(queue) or any(active.values()):
             now = self._now(t0)
+            tp = time.perf_counter()
             counts = {k: len(v) for k, v in active.items()}
             adm, add = admit(queue[qi:], now, self.used, self.budget, counts, self.max_active, self._need,
                              self._evictable())
@@ -341,6 +358,8 @@ class Server:
             qi += len(adm)
             if add:
                 self._evict_for(add)
+            tp = st.add("admit", tp)
+
             def setup_new():
                 for kind in SOLVERS:
                     reqs = [r for r in adm if r["kind"] == kind]
@@ -353,6 +372,7 @@ class Server:
             # tick's iterations are launched) and pricing of option batches
             if not self.overlap:
                 setup_new()
+                tp = st.add("setup", tp)
             bs = [r for r in adm if r["kind"] == "bs"]
             if bs:
                 self.used += sum(request_bytes("bs", r["size"]) for r in bs)
@@ -363,6 +383,7 @@ class Server:
                     res.done = t
                 finished.extend(done)
                 self.used -= sum(request_bytes("bs", r["size"]) for r in bs)
+                tp = st.add("price", tp)
             self.stats.peak_bytes = max(self.stats.peak_bytes, self.used)
             # one tick of every active solve
             for kind in SOLVERS:
@@ -371,8 +392,10 @@ class Server:
                     self._iterate(kind, active[kind])
                     for s in active[kind]:
                         s.it += self.C
+            tp = st.add("iterate", tp)
             if self.overlap:
                 setup_new()                      # host work while the GPU iterates; they join next tick
+                tp = st.add("setup", tp)
             self.stats.ticks += 1
             self._advance(0.0)
             # convergence test of every solve that iterated, one gather
@@ -382,6 +405,7 @@ class Server:
                 for s in sols:
                     arrs += [s.bb, s.st.rho if s.res.kind == "cg" else s.st.rr]
                 vals = self.rt.read_scalars(arrs)  # synchronises the stream
+                tp = st.add("read_scalars", tp)
                 self._inflight.clear()
                 retire = []
                 for i, s in enumerate(sols):
@@ -397,7 +421,7 @@ class Server:
                 if retire:
                     self.rt.batch_begin()
                 for s in retire:
-                    hx = s.out
+                    hx = s.out[:s.st.x.shape[0]]
                     w = self.rt.wrap_host(hx)
                     w[...] = s.st.x
                     hold.append(w)
@@ -419,6 +443,7 @@ class Server:
                 for s in retire:
                     self._recycle(s.out)
                     s.out = None
+                st.add("retire", tp)
         self.rt.sync()
         self._inflight.clear()
         return finished

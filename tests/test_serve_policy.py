@@ -86,9 +86,9 @@ def test_tick_clock_and_summary():
 
 
 def test_result_buffers_are_reused_only_when_outputs_are_not_kept(monkeypatch):
-    """Page-locked result buffers come from a pool keyed by shape and dtype;
-    a buffer goes back to it after its result is handed over, and never when
-    the caller keeps the outputs."""
+    """Page-locked result buffers come from a pool keyed by dtype and a
+    power-of-two capacity; a buffer goes back to it after its result is handed
+    over, and never when the caller keeps the outputs."""
     made = []
 
     def fake_host_empty(shape, dtype):
@@ -99,13 +99,15 @@ def test_result_buffers_are_reused_only_when_outputs_are_not_kept(monkeypatch):
     for keep in (False, True):
         made.clear()
         srv = serve.Server(None, None, keep_outputs=keep)
-        a = srv._out_buffer((8,), np.float64)
+        a = srv._out_buffer(100, np.float64)
+        assert len(a) == 128
         srv._recycle(a)
-        b = srv._out_buffer((8,), np.float64)
-        c = srv._out_buffer((8,), np.float32)            # another dtype: a new buffer
+        b = srv._out_buffer(70, np.float64)              # same capacity class (65..128)
+        c = srv._out_buffer(100, np.float32)             # another dtype: a new buffer
         srv._recycle(b)
-        d = srv._out_buffer((4,), np.float64)            # another shape: a new buffer
+        d = srv._out_buffer(129, np.float64)             # the next class: a new buffer
         assert (b is a) == (not keep)
-        assert c is not a and d is not a and d is not c
+        assert len(d) == 256 and c is not a and d is not a
         assert len(made) == (3 if not keep else 4)
         assert srv.stats_pool == {"allocated": len(made), "reused": 1 if not keep else 0}
+    assert len(serve.Server(None, None)._out_buffer(1, np.float64)) == 1
