@@ -744,7 +744,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bs", choices=["bs", "cg", "jacobi", "batched", "serve"])
     ap.add_argument("--requests", type=int, default=0, help="serving: requests per run (default: the config's)")
-    ap.add_argument("--no-overlap", action="store_true", help="serving: set new solves up before the tick's iterations")
+    ap.add_argument("--no-overlap", action="store_true",
+                    help="serving: one group of solves (the host waits for every convergence read)")
     ap.add_argument("--fp32", action="store_true", help="batched CG in FP32 instead of FP64")
     ap.add_argument("--quick", action="store_true", help="skip the comparison arms (for profiling)")
     ap.add_argument("--bs-n", type=int, default=0, help="Black-Scholes batch size (profiling a smaller case)")

@@ -373,6 +373,43 @@ int dfs_batch_repeat(dfs_ctx *ctx, int32_t n);
 int dfs_read_scalars(dfs_ctx *ctx, int32_t n, const dfs_store *stores, double *host_out);
 
 /*
+ * dfs_read_scalars_async -- the same gather as dfs_read_scalars, enqueued on
+ * the context's stream without waiting: it flushes, checks the stores, and
+ * returns once the descriptor upload, the gather kernel and the copy of the
+ * n values to host_vals[0..n) are issued.  A serving loop reads one group of
+ * solves' residuals this way while the GPU still has another group's
+ * iterations queued behind the copy, so the GPU does not wait for the host.
+ * host_work (2 n int64: the gather's descriptors) and host_vals (n doubles)
+ * must be page-locked host memory (dfs_host_alloc) that the caller neither
+ * reads nor writes until a ticket recorded after this call (dfs_record) has
+ * completed.  Errors as dfs_read_scalars, plus DFS_ERR_INVALID when a host
+ * buffer is not page-locked.  n == 0 issues nothing.
+ */
+int dfs_read_scalars_async(dfs_ctx *ctx, int32_t n, const dfs_store *stores, int64_t *host_work,
+                           double *host_vals);
+
+/*
+ * Completion tickets.  dfs_record flushes the pending window and records a
+ * CUDA event after all work issued on the context so far; *ticket names it.
+ * dfs_wait blocks until that work has finished and then returns any deferred
+ * device error (as dfs_sync does, but without waiting for work issued after
+ * the ticket).  dfs_poll sets *done to 1 when the work has finished (then
+ * returning deferred device errors) and to 0 otherwise, without blocking.
+ * dfs_ticket_elapsed_ms gives the device time between two completed tickets
+ * of the context (milliseconds, CUDA event resolution).  dfs_ticket_release
+ * forgets a ticket; its event is reused.  Tickets not released are freed at
+ * dfs_shutdown.
+ * Returns DFS_OK; DFS_ERR_INVALID for null pointers; DFS_ERR_STATE for an
+ * unknown ticket, a ticket not complete (elapsed time) or dfs_record while
+ * capturing; DFS_ERR_NO_DEVICE in an analysis-only context; DFS_ERR_CUDA.
+ */
+int dfs_record(dfs_ctx *ctx, uint64_t *ticket);
+int dfs_wait(dfs_ctx *ctx, uint64_t ticket);
+int dfs_poll(dfs_ctx *ctx, uint64_t ticket, int32_t *done);
+int dfs_ticket_elapsed_ms(dfs_ctx *ctx, uint64_t from, uint64_t to, float *ms);
+int dfs_ticket_release(dfs_ctx *ctx, uint64_t ticket);
+
+/*
  * dfs_set_launch_config -- changes the launch parameters of a live context
  * (block_threads: 128, 256, 512 or 1024; unroll: 1..8; ctas_per_sm: 0 =
  * as many as fit, else that many, with registers capped to fit them; see

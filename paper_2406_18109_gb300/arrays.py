@@ -284,6 +284,30 @@ class Runtime:
         """Values of many 0-d arrays with one gather and one copy (dfs_read_scalars)."""
         return B.dfs_read_scalars(self.ctx, [a.handle for a in arrays])
 
+    def read_scalars_async(self, arrays, work=None, vals=None) -> "ScalarRead":
+        """Enqueues one gather of many 0-d arrays into page-locked host memory
+        and returns at once (dfs_read_scalars_async, then a ticket); the
+        result's values() waits for it.  work / vals: reusable page-locked
+        buffers (host_empty) of at least 2 n int64 and n float64."""
+        return ScalarRead(self, arrays, work, vals)
+
+    # ------------------------------------------------------------- tickets
+    def record(self) -> int:
+        """A ticket for the work issued so far (dfs_record)."""
+        return B.dfs_record(self.ctx)
+
+    def wait(self, ticket: int) -> None:
+        B.dfs_wait(self.ctx, ticket)
+
+    def poll(self, ticket: int) -> bool:
+        return B.dfs_poll(self.ctx, ticket)
+
+    def elapsed_ms(self, t_from: int, t_to: int) -> float:
+        return B.dfs_ticket_elapsed_ms(self.ctx, t_from, t_to)
+
+    def release_ticket(self, ticket: int) -> None:
+        B.dfs_ticket_release(self.ctx, ticket)
+
     # ------------------------------------------------------- graph capture
     def capture_begin(self):
         B.dfs_capture_begin(self.ctx)
@@ -296,6 +320,35 @@ class Runtime:
 
     def graph_destroy(self, graph: int):
         B.dfs_graph_destroy(self.ctx, graph)
+
+
+
+class ScalarRead:
+    """An asynchronous gather of 0-d arrays (Runtime.read_scalars_async): the
+    values land in page-locked host memory when the stream reaches the copy.
+    The arrays' stores and the buffers stay referenced until values() returns."""
+
+    def __init__(self, rt: "Runtime", arrays, work=None, vals=None):
+        n = len(arrays)
+        if work is None or len(work) < 2 * n:
+            work = Runtime.host_empty((max(1, 2 * n),), np.int64)
+        if vals is None or len(vals) < n:
+            vals = Runtime.host_empty((max(1, n),), np.float64)
+        self.rt, self.n, self.arrays, self.work, self.vals = rt, n, list(arrays), work, vals
+        B.dfs_read_scalars_async(rt.ctx, [a.handle for a in self.arrays], work.ctypes.data, vals.ctypes.data)
+        self.ticket = B.dfs_record(rt.ctx)
+
+    def done(self) -> bool:
+        return self.ticket is None or B.dfs_poll(self.rt.ctx, self.ticket)
+
+    def values(self) -> list:
+        """Waits for the gather; the n values as floats."""
+        if self.ticket is not None:
+            B.dfs_wait(self.rt.ctx, self.ticket)
+            B.dfs_ticket_release(self.rt.ctx, self.ticket)
+            self.ticket = None
+            self.arrays = []
+        return [float(v) for v in self.vals[:self.n]]
 
 
 class Array:

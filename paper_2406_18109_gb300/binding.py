@@ -37,7 +37,9 @@ EXPORTS = ("dfs_config_default", "dfs_init", "dfs_shutdown", "dfs_store_create",
            "dfs_last_kernel_source", "dfs_version", "dfs_dot_noalloc", "dfs_capture_begin",
            "dfs_capture_end", "dfs_graph_launch", "dfs_graph_destroy", "dfs_batch_begin",
            "dfs_batch_next", "dfs_batch_end", "dfs_batch_repeat", "dfs_read_scalars",
-           "dfs_set_launch_config", "dfs_store_wrap_host", "dfs_host_alloc", "dfs_host_free")
+           "dfs_set_launch_config", "dfs_store_wrap_host", "dfs_host_alloc", "dfs_host_free",
+           "dfs_read_scalars_async", "dfs_record", "dfs_wait", "dfs_poll", "dfs_ticket_elapsed_ms",
+           "dfs_ticket_release")
 
 
 class dfs_config(C.Structure):
@@ -106,6 +108,12 @@ def lib():
             "dfs_store_wrap_host": (C.c_int, [P, I32, I32, pI64, P, pI64]),
             "dfs_host_alloc": (C.c_int, [C.c_size_t, C.POINTER(P)]),
             "dfs_host_free": (C.c_int, [P]),
+            "dfs_read_scalars_async": (C.c_int, [P, I32, pI64, P, P]),
+            "dfs_record": (C.c_int, [P, C.POINTER(C.c_uint64)]),
+            "dfs_wait": (C.c_int, [P, C.c_uint64]),
+            "dfs_poll": (C.c_int, [P, C.c_uint64, C.POINTER(C.c_int32)]),
+            "dfs_ticket_elapsed_ms": (C.c_int, [P, C.c_uint64, C.c_uint64, C.POINTER(C.c_float)]),
+            "dfs_ticket_release": (C.c_int, [P, C.c_uint64]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -291,6 +299,38 @@ def dfs_read_scalars(ctx, stores, out=None):
     buf = out if out is not None else (C.c_double * max(1, n))()
     _check(ctx, lib().dfs_read_scalars(ctx, n, hs, buf))
     return buf[:n]
+
+
+def dfs_read_scalars_async(ctx, stores, host_work: int, host_vals: int) -> None:
+    """Enqueues the gather of the 0-d `stores` into page-locked host memory
+    (addresses host_work: 2 int64 per store, host_vals: 1 double per store)."""
+    _check(ctx, lib().dfs_read_scalars_async(ctx, len(stores), _i64s(stores), host_work, host_vals))
+
+
+def dfs_record(ctx) -> int:
+    t = C.c_uint64()
+    _check(ctx, lib().dfs_record(ctx, C.byref(t)))
+    return t.value
+
+
+def dfs_wait(ctx, ticket: int) -> None:
+    _check(ctx, lib().dfs_wait(ctx, ticket))
+
+
+def dfs_poll(ctx, ticket: int) -> bool:
+    done = C.c_int32()
+    _check(ctx, lib().dfs_poll(ctx, ticket, C.byref(done)))
+    return bool(done.value)
+
+
+def dfs_ticket_elapsed_ms(ctx, t_from: int, t_to: int) -> float:
+    ms = C.c_float()
+    _check(ctx, lib().dfs_ticket_elapsed_ms(ctx, t_from, t_to, C.byref(ms)))
+    return float(ms.value)
+
+
+def dfs_ticket_release(ctx, ticket: int) -> None:
+    _check(ctx, lib().dfs_ticket_release(ctx, ticket))
 
 
 def dfs_set_launch_config(ctx, block_threads: int, unroll: int, ctas_per_sm: int) -> None:

@@ -137,6 +137,10 @@ struct dfs_ctx {
   int64_t* gather_host = nullptr;
   void* gather_dev = nullptr;
   size_t gather_cap = 0;  // scalars
+  // completion tickets (dfs_record): an event recorded on the stream each
+  std::map<uint64_t, cudaEvent_t> tickets;
+  std::vector<cudaEvent_t> ticket_pool;
+  uint64_t next_ticket = 1;
 };
 
 namespace dfs {
@@ -1099,6 +1103,86 @@ int write_json(const std::string& s, char* buf, size_t len, size_t* needed) {
 }  // namespace
 }  // namespace dfs
 
+namespace dfs {
+namespace {
+
+// Checks of dfs_read_scalars and dfs_read_scalars_async; flushes.
+int gather_check(dfs_ctx* c, int32_t n, const dfs_store* hs, const char* who) {
+  if (!c->device) return fail(c, DFS_ERR_NO_DEVICE, "analysis-only context");
+  if (c->capturing) return fail(c, DFS_ERR_STATE, std::string(who) + " while capturing");
+  for (int32_t i = 0; i < n; ++i) {
+    StoreRec* r = find_store(c, hs[i]);
+    if (!r) return fail(c, DFS_ERR_STATE, "unknown or released store");
+    if (r->ndim != 0) return fail(c, DFS_ERR_INVALID, std::string(who) + " takes 0-d stores");
+  }
+  int rc = flush(c);
+  if (rc) return rc;
+  for (int32_t i = 0; i < n; ++i) {
+    const StoreRec& r = *find_store(c, hs[i]);
+    const StoreRec& root = c->stores.at(r.root);
+    if (!root.ptr || !root.valid) return fail(c, DFS_ERR_STATE, "store has no value");
+  }
+  return DFS_OK;
+}
+
+// Grows the gather buffers to n scalars (synchronising the stream first, as
+// the old buffers may still be in use).
+int gather_reserve(dfs_ctx* c, int32_t n) {
+  if ((size_t)n > c->gather_cap) {
+    CUDA_OK(cudaStreamSynchronize(c->stream));
+    if (c->gather_host) cudaFreeHost(c->gather_host);
+    if (c->gather_dev) cudaFree(c->gather_dev);
+    c->gather_host = nullptr;
+    c->gather_dev = nullptr;
+    c->gather_cap = 0;
+    const size_t cap = std::max<size_t>(1024, (size_t)n);
+    // per scalar: descriptor (address, dtype) then the gathered double
+    CUDA_OK(cudaMallocHost((void**)&c->gather_host, cap * 3 * sizeof(int64_t)));
+    CUDA_OK(cudaMalloc(&c->gather_dev, cap * 3 * sizeof(int64_t)));
+    c->gather_cap = cap;
+  }
+  return DFS_OK;
+}
+
+// Enqueues the gather of n 0-d stores (n within the reserved capacity):
+// descriptors (address, dtype) from desc_host (2 n int64, written here) to
+// the device, the gather kernel, and the n doubles back to vals_host.  Both
+// host buffers are page-locked and must stay untouched until the stream
+// passes this point.
+int gather_enqueue(dfs_ctx* c, int32_t n, const dfs_store* hs, int64_t* desc_host, double* vals_host) {
+  for (int32_t i = 0; i < n; ++i) {
+    const StoreRec& r = *find_store(c, hs[i]);
+    const StoreRec& root = c->stores.at(r.root);
+    const char* p = (const char*)root.ptr;
+    for (int d = 0; d < root.ndim; ++d) p += (size_t)r.off[d] * root.stride[d] * dtype_size(r.dtype);
+    desc_host[2 * i] = (int64_t)(uintptr_t)p;
+    desc_host[2 * i + 1] = r.dtype;
+  }
+  int64_t* desc = static_cast<int64_t*>(c->gather_dev);
+  double* vals = reinterpret_cast<double*>(desc + 2 * c->gather_cap);
+  CUDA_OK(cudaMemcpyAsync(desc, desc_host, (size_t)n * 2 * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+  CUDA_OK(launch_gather_scalars(desc, n, vals, c->stream));
+  CUDA_OK(cudaMemcpyAsync(vals_host, vals, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  return DFS_OK;
+}
+
+bool page_locked(const void* p, size_t bytes) {
+  cudaPointerAttributes a0{}, a1{};
+  const char* last = (const char*)p + (bytes ? bytes - 1 : 0);
+  const bool ok = cudaPointerGetAttributes(&a0, p) == cudaSuccess && a0.type == cudaMemoryTypeHost &&
+                  cudaPointerGetAttributes(&a1, last) == cudaSuccess && a1.type == cudaMemoryTypeHost;
+  if (!ok) cudaGetLastError();
+  return ok;
+}
+
+cudaEvent_t* find_ticket(dfs_ctx* c, uint64_t t) {
+  auto it = c->tickets.find(t);
+  return it == c->tickets.end() ? nullptr : &it->second;
+}
+
+}  // namespace
+}  // namespace dfs
+
 using namespace dfs;
 
 // No C++ exception may cross the C ABI: an internal failure (a violated
@@ -1219,6 +1303,8 @@ int dfs_shutdown(dfs_ctx* c) {
         cudaEventDestroy(t.b);
       }
       for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
+      for (auto& kv : c->tickets) cudaEventDestroy(kv.second);
+      for (cudaEvent_t e : c->ticket_pool) cudaEventDestroy(e);
       if (c->ctl) cudaFree(c->ctl);
       c->jit.reset();
       if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -1857,50 +1943,141 @@ int dfs_read_scalars(dfs_ctx* c, int32_t n, const dfs_store* hs, double* out) {
   try {
     if (!c) return DFS_ERR_INVALID;
     if (n < 0 || (n > 0 && (!hs || !out))) return fail(c, DFS_ERR_INVALID, "bad arguments");
-    if (!c->device) return fail(c, DFS_ERR_NO_DEVICE, "analysis-only context");
-    if (c->capturing) return fail(c, DFS_ERR_STATE, "dfs_read_scalars while capturing");
-    for (int32_t i = 0; i < n; ++i) {
-      StoreRec* r = find_store(c, hs[i]);
-      if (!r) return fail(c, DFS_ERR_STATE, "unknown or released store");
-      if (r->ndim != 0) return fail(c, DFS_ERR_INVALID, "dfs_read_scalars takes 0-d stores");
-    }
-    int rc = flush(c);
+    int rc = gather_check(c, n, hs, "dfs_read_scalars");
     if (rc) return rc;
     if (n == 0) {
       CUDA_OK(cudaStreamSynchronize(c->stream));
       return check_device_error(c);
     }
-    if ((size_t)n > c->gather_cap) {
-      CUDA_OK(cudaStreamSynchronize(c->stream));
-      if (c->gather_host) cudaFreeHost(c->gather_host);
-      if (c->gather_dev) cudaFree(c->gather_dev);
-      c->gather_host = nullptr;
-      c->gather_dev = nullptr;
-      c->gather_cap = 0;
-      const size_t cap = std::max<size_t>(1024, (size_t)n);
-      // per scalar: descriptor (address, dtype) then the gathered double
-      CUDA_OK(cudaMallocHost((void**)&c->gather_host, cap * 3 * sizeof(int64_t)));
-      CUDA_OK(cudaMalloc(&c->gather_dev, cap * 3 * sizeof(int64_t)));
-      c->gather_cap = cap;
-    }
-    for (int32_t i = 0; i < n; ++i) {
-      const StoreRec& r = *find_store(c, hs[i]);
-      const StoreRec& root = c->stores.at(r.root);
-      if (!root.ptr || !root.valid) return fail(c, DFS_ERR_STATE, "store has no value");
-      const char* p = (const char*)root.ptr;
-      for (int d = 0; d < root.ndim; ++d) p += (size_t)r.off[d] * root.stride[d] * dtype_size(r.dtype);
-      c->gather_host[2 * i] = (int64_t)(uintptr_t)p;
-      c->gather_host[2 * i + 1] = r.dtype;
-    }
-    int64_t* desc = static_cast<int64_t*>(c->gather_dev);
-    double* vals = reinterpret_cast<double*>(desc + 2 * c->gather_cap);
-    CUDA_OK(cudaMemcpyAsync(desc, c->gather_host, (size_t)n * 2 * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
-    CUDA_OK(launch_gather_scalars(desc, n, vals, c->stream));
+    rc = gather_reserve(c, n);
+    if (rc) return rc;
     double* hv = reinterpret_cast<double*>(c->gather_host + 2 * c->gather_cap);
-    CUDA_OK(cudaMemcpyAsync(hv, vals, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    rc = gather_enqueue(c, n, hs, c->gather_host, hv);
+    if (rc) return rc;
     CUDA_OK(cudaStreamSynchronize(c->stream));
     std::memcpy(out, hv, (size_t)n * sizeof(double));
     return check_device_error(c);
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
+  }
+}
+
+int dfs_read_scalars_async(dfs_ctx* c, int32_t n, const dfs_store* hs, int64_t* host_work, double* host_vals) {
+  try {
+    if (!c) return DFS_ERR_INVALID;
+    if (n < 0 || (n > 0 && (!hs || !host_work || !host_vals))) return fail(c, DFS_ERR_INVALID, "bad arguments");
+    if (n > 0 && (!page_locked(host_work, (size_t)n * 2 * sizeof(int64_t)) ||
+                  !page_locked(host_vals, (size_t)n * sizeof(double))))
+      return fail(c, DFS_ERR_INVALID, "host buffers must be page-locked");
+    int rc = gather_check(c, n, hs, "dfs_read_scalars_async");
+    if (rc || n == 0) return rc;
+    rc = gather_reserve(c, n);
+    if (rc) return rc;
+    return gather_enqueue(c, n, hs, host_work, host_vals);
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
+  }
+}
+
+int dfs_record(dfs_ctx* c, uint64_t* ticket) {
+  try {
+    if (!c) return DFS_ERR_INVALID;
+    if (!ticket) return fail(c, DFS_ERR_INVALID, "null ticket");
+    if (!c->device) return fail(c, DFS_ERR_NO_DEVICE, "analysis-only context");
+    if (c->capturing) return fail(c, DFS_ERR_STATE, "dfs_record while capturing");
+    int rc = flush(c);
+    if (rc) return rc;
+    cudaEvent_t ev;
+    if (!c->ticket_pool.empty()) {
+      ev = c->ticket_pool.back();
+      c->ticket_pool.pop_back();
+    } else {
+      CUDA_OK(cudaEventCreate(&ev));
+    }
+    const cudaError_t e = cudaEventRecord(ev, c->stream);
+    if (e != cudaSuccess) {
+      c->ticket_pool.push_back(ev);
+      return fail(c, DFS_ERR_CUDA, std::string("cudaEventRecord: ") + cudaGetErrorString(e));
+    }
+    const uint64_t t = c->next_ticket++;
+    c->tickets[t] = ev;
+    *ticket = t;
+    return DFS_OK;
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
+  }
+}
+
+int dfs_wait(dfs_ctx* c, uint64_t ticket) {
+  try {
+    if (!c) return DFS_ERR_INVALID;
+    cudaEvent_t* ev = find_ticket(c, ticket);
+    if (!ev) return fail(c, DFS_ERR_STATE, "unknown ticket");
+    CUDA_OK(cudaEventSynchronize(*ev));
+    return check_device_error(c);
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
+  }
+}
+
+int dfs_poll(dfs_ctx* c, uint64_t ticket, int32_t* done) {
+  try {
+    if (!c) return DFS_ERR_INVALID;
+    if (!done) return fail(c, DFS_ERR_INVALID, "null result");
+    cudaEvent_t* ev = find_ticket(c, ticket);
+    if (!ev) return fail(c, DFS_ERR_STATE, "unknown ticket");
+    const cudaError_t e = cudaEventQuery(*ev);
+    if (e == cudaErrorNotReady) {
+      *done = 0;
+      return DFS_OK;
+    }
+    CUDA_OK(e);
+    *done = 1;
+    return check_device_error(c);
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
+  }
+}
+
+int dfs_ticket_elapsed_ms(dfs_ctx* c, uint64_t from, uint64_t to, float* ms) {
+  try {
+    if (!c) return DFS_ERR_INVALID;
+    if (!ms) return fail(c, DFS_ERR_INVALID, "null result");
+    cudaEvent_t* a = find_ticket(c, from);
+    cudaEvent_t* b = find_ticket(c, to);
+    if (!a || !b) return fail(c, DFS_ERR_STATE, "unknown ticket");
+    const cudaError_t e = cudaEventElapsedTime(ms, *a, *b);
+    if (e == cudaErrorNotReady) {
+      cudaGetLastError();
+      return fail(c, DFS_ERR_STATE, "ticket not complete");
+    }
+    CUDA_OK(e);
+    return DFS_OK;
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
+  }
+}
+
+int dfs_ticket_release(dfs_ctx* c, uint64_t ticket) {
+  try {
+    if (!c) return DFS_ERR_INVALID;
+    auto it = c->tickets.find(ticket);
+    if (it == c->tickets.end()) return fail(c, DFS_ERR_STATE, "unknown ticket");
+    c->ticket_pool.push_back(it->second);
+    c->tickets.erase(it);
+    return DFS_OK;
   } catch (const std::exception& e_) {
     return internal_error(c, e_.what());
   } catch (...) {

@@ -1,31 +1,39 @@
 """A serving loop with continuous batching over the fused runtime.
 
 Requests (CG and BiCGSTAB solves on resident Poisson operators, and
-Black-Scholes option batches) arrive over time.  The loop runs in ticks:
+Black-Scholes option batches) arrive over time.  Active solves form two
+groups that take turns on one CUDA stream; a turn of group g:
 
-  1. admit, in arrival order, the requests that have arrived while the
+  1. wait for g's last convergence read (an asynchronous gather of every
+     solve's r.r and b.b, dfs_read_scalars_async) -- the other group's
+     iterations were issued after it, so the GPU keeps working while the
+     host goes on -- and retire the solves that reached ||r|| <= tol ||b||
+     (or max_iters): one batched kernel copies their x to the host, their
+     stores are freed and their budget released;
+  2. admit, in arrival order, the requests that have arrived while the
      device-memory budget and the per-kind slot limit allow it (an idle
      operator is evicted, least recently used first, when the budget is
-     short); a Black-Scholes batch is priced at once and completes in the tick
-     that admits it; new solves have their data uploaded and are set up as one
-     batched window per kind (b = A x*, the solver's start state) after the
-     tick's iterations are launched, so that host work overlaps GPU work;
-  2. advance every active solve by `iters_per_tick` iterations: all solves of
+     short): new solves are set up in g (b = A x*, the start state, b.b) as
+     one batched window per kind; option batches are priced by one batched
+     launch whose kernel writes the prices to the host;
+  3. issue iters_per_tick iterations of every solve of g -- all solves of
      one kind form the instances of one batched launch (their uneven sizes
-     share one persistent kernel), repeated with dfs_batch_repeat while the
-     set of solves does not change;
-  3. read every active solve's r.r and b.b with one gather, and retire the
-     solves that reached ||r|| <= tol ||b|| (or max_iters): copy x back to the
-     host, free its stores, release its budget.
+     share one persistent kernel), repeated with dfs_batch_repeat -- and the
+     asynchronous read of their residuals.
+
+A result is complete when its copy to the host has finished (a completion
+ticket, dfs_record); with the real clock its completion time is the device
+time of that point.
 
 Results are delivered into page-locked host buffers taken at set-up time
-(while the GPU iterates) from a pool keyed by dtype and power-of-two
+(while the GPU works on the other group) from a pool keyed by dtype and
+power-of-two
 capacity; when the caller does not keep outputs, a buffer returns to the pool
 once its result has been handed over, so a steady stream pins little new
 host memory.
 
-Requests that arrive while others are on the GPU join the next tick's batches,
-so their work shares launches with the solves already running.  A solve's
+Requests that arrive while others are on the GPU join the next turn's
+batches, so their work shares launches with the solves already running.  A solve's
 iterations, its convergence test (always after a multiple of iters_per_tick
 of its own iterations) and its arithmetic (batched instances are bit-identical
 to solo runs with the same tiles) do not depend on what else is in the mix, so
@@ -274,8 +282,8 @@ class Server:
                                out=self._out_buffer(st.x.shape[0], st.x.dtype)))
             rt.batch_next()
         rt.batch_end()
-        # the set-up runs asynchronously: keep the host data it reads (and
-        # their stores) until the next synchronisation of the stream
+        # the set-up runs asynchronously: the caller keeps the host data it
+        # reads (and their stores) until work issued after it has completed
         self._inflight.append((items, xs_all))
         return sols
 
@@ -301,13 +309,17 @@ class Server:
                     pass               # not steady yet (a store got its first value): issue again
 
     def _price(self, reqs, payloads, now):
+        """One batched launch pricing every option batch of `reqs`; the
+        prices go straight from the kernel into page-locked host buffers.
+        Returns (results, buffers, holds): the results are complete once work
+        issued after this call has finished; holds keep the host data and
+        stores the launch reads or writes alive until then."""
         rt = self.rt
         hosts = [payloads(req) for req in reqs]
         arrs, _ = self._inputs([h for trio in hosts for h in trio])
         data = [(req, *arrs[3 * i:3 * i + 3]) for i, req in enumerate(reqs)]
-        # one batched launch; the prices go straight from the kernel into
-        # mapped page-locked host buffers (call and put become temporaries)
-        results, hold = [], []
+        # call and put become temporaries: the kernel stores into host memory
+        results, bufs, hold = [], [], [hosts, arrs]
         rt.batch_begin()
         for req, S, K, T in data:
             bc = self._out_buffer(req["size"], np.float32)
@@ -318,134 +330,192 @@ class Server:
             wc[...] = call
             wp[...] = put
             del call, put
-            hold.append((wc, wp, bc, bp))
+            hold.append((wc, wp))
+            bufs += [bc, bp]
             res = Result(req["rid"], "bs", req["size"], req["arrival"], admitted=now)
             res.output = (hc, hp) if self.keep else None
             results.append(res)
             rt.batch_next()
         rt.batch_end()
-        rt.sync()
-        for _, _, bc, bp in hold:
-            self._recycle(bc)
-            self._recycle(bp)
-        return results
+        return results, bufs, hold
 
     # ------------------------------------------------------------------ run
+    def _retire(self, group, sols, vals):
+        """Convergence test of the solves of one read; the converged ones (or
+        those at max_iters) copy x into their host buffers with one batched
+        kernel and leave.  Returns a delivery (results, buffers, holds), or
+        None."""
+        retire = []
+        for i, s in enumerate(sols):
+            bb, rr = vals[2 * i], vals[2 * i + 1]
+            rel = math.sqrt(max(rr, 0.0) / bb) if bb > 0 else 0.0
+            if rel <= self.tol or s.it >= self.max_iters or not math.isfinite(rel):
+                s.res.rel_residual = rel
+                s.res.converged = rel <= self.tol
+                retire.append(s)
+        if not retire:
+            return None
+        hold = []
+        self.rt.batch_begin()
+        for s in retire:
+            hx = s.out[:s.st.x.shape[0]]
+            w = self.rt.wrap_host(hx)
+            w[...] = s.st.x
+            hold.append(w)
+            self.rt.batch_next()
+            s.res.iterations = s.it
+            s.res.output = hx if self.keep else None
+            group[s.res.kind].remove(s)
+            self.used -= s.nbytes
+            self.op_users[s.m] -= 1
+            s.st = s.bb = None
+        self.rt.batch_end()
+        bufs = [s.out for s in retire]
+        for s in retire:
+            s.out = None
+        return [s.res for s in retire], bufs, hold
+
     def run(self, requests, payloads):
         """Serve `requests` (dicts with rid, arrival, kind, size, seed, in
         arrival order); payloads(req) gives the request's host data.  Returns
-        the Results in completion order."""
+        the Results in completion order.
+
+        Active solves form two groups that take turns (one group without
+        overlap).  A turn of group g: wait for g's last convergence read (the
+        other group's iterations, issued after it, keep the GPU busy
+        meanwhile), retire g's converged solves, admit arrived requests (new
+        solves join g, option batches are priced), issue g's next
+        iters_per_tick iterations and an asynchronous read of its residuals.
+        Every solve still iterates iters_per_tick at a time and is tested
+        after each block, so its iterations and result do not depend on the
+        groups or the mix.  A result is complete when its copy to the host
+        has finished: with the real clock its completion time is the device
+        time of that point (CUDA events), else the clock when it is seen."""
         queue = list(requests)
         qi = 0
-        active: dict[str, list[_Solve]] = {k: [] for k in SOLVERS}
+        G = 2 if self.overlap else 1
+        groups = [{k: [] for k in SOLVERS} for _ in range(G)]
+        pend = [None] * G          # (ScalarRead, solves, holds) in flight per group
+        gbuf = [(None, None)] * G  # reusable page-locked gather buffers per group
+        deliveries = []            # (ticket, results, buffers, holds, device bytes) in flight
         finished: list[Result] = []
-        t0 = self.clock() if self.clock else time.perf_counter()
         st = self.stats
-        while qi < len(queue) or any(active.values()):
-            now = self._now(t0)
-            tp = time.perf_counter()
-            counts = {k: len(v) for k, v in active.items()}
-            adm, add = admit(queue[qi:], now, self.used, self.budget, counts, self.max_active, self._need,
-                             self._evictable())
-            if not adm and not any(active.values()):
-                if queue[qi]["arrival"] > now:
-                    if self.clock is None:
-                        time.sleep(max(0.0, min(queue[qi]["arrival"] - now, 0.01)))
-                    else:
-                        self._advance(queue[qi]["arrival"] - now)
-                    continue
-                raise RuntimeError(f"request {queue[qi]['rid']} does not fit the device-memory budget")
-            qi += len(adm)
-            if add:
-                self._evict_for(add)
-            tp = st.add("admit", tp)
+        rt = self.rt
+        t0 = self.clock() if self.clock else time.perf_counter()
+        real = self.clock is None
+        t_ref, host_ref = None, 0.0
+        if real:
+            rt.sync()                               # the device-time origin is this moment
+            t_ref, host_ref = rt.record(), self._now(t0)
 
-            def setup_new():
+        def n_active():
+            return sum(len(v) for grp in groups for v in grp.values())
+
+        def complete(block: bool) -> None:
+            keep = []
+            for d in deliveries:
+                ticket, results, bufs, hold, nbytes = d
+                if block:
+                    rt.wait(ticket)
+                elif not rt.poll(ticket):
+                    keep.append(d)
+                    continue
+                t = host_ref + rt.elapsed_ms(t_ref, ticket) / 1e3 if real else self._now(t0)
+                rt.release_ticket(ticket)
+                for r in results:
+                    r.done = t
+                    finished.append(r)
+                for b in bufs:
+                    self._recycle(b)
+                self.used -= nbytes
+            deliveries[:] = keep
+
+        g = 0
+        try:
+            while qi < len(queue) or n_active() or any(p is not None for p in pend) or deliveries:
+                tp = time.perf_counter()
+                # 1. the group's convergence read, then retirement
+                if pend[g] is not None:
+                    rd, sols, _holds = pend[g]
+                    vals = rd.values()
+                    pend[g] = None
+                    tp = st.add("wait", tp)
+                    dl = self._retire(groups[g], sols, vals)
+                    if dl is not None:
+                        deliveries.append((rt.record(), *dl, 0))
+                    tp = st.add("retire", tp)
+                complete(block=False)
+                # 2. admission into this group
+                now = self._now(t0)
+                counts = {k: sum(len(grp[k]) for grp in groups) for k in SOLVERS}
+                adm, add = admit(queue[qi:], now, self.used, self.budget, counts, self.max_active, self._need,
+                                 self._evictable())
+                if not adm and not n_active() and all(p is None for p in pend):
+                    if deliveries:
+                        complete(block=True)
+                        continue
+                    if qi < len(queue) and queue[qi]["arrival"] > now:
+                        if self.clock is None:
+                            time.sleep(max(0.0, min(queue[qi]["arrival"] - now, 0.01)))
+                        else:
+                            self._advance(queue[qi]["arrival"] - now)
+                        continue
+                    if qi < len(queue):
+                        raise RuntimeError(f"request {queue[qi]['rid']} does not fit the device-memory budget")
+                    break
+                qi += len(adm)
+                if add:
+                    self._evict_for(add)
+                tp = st.add("admit", tp)
+                holds = []
                 for kind in SOLVERS:
                     reqs = [r for r in adm if r["kind"] == kind]
                     if reqs:
                         sols = self._setup_solves(kind, reqs, payloads, now)
+                        holds.append(self._inflight.pop())
                         for s in sols:
                             self.used += s.nbytes
-                        active[kind].extend(sols)
-            # admission: set-up windows of new solves (now, or after this
-            # tick's iterations are launched) and pricing of option batches
-            if not self.overlap:
-                setup_new()
+                        groups[g][kind].extend(sols)
                 tp = st.add("setup", tp)
-            bs = [r for r in adm if r["kind"] == "bs"]
-            if bs:
-                self.used += sum(request_bytes("bs", r["size"]) for r in bs)
+                bs = [r for r in adm if r["kind"] == "bs"]
+                if bs:
+                    nb = sum(request_bytes("bs", r["size"]) for r in bs)
+                    self.used += nb
+                    self.stats.peak_bytes = max(self.stats.peak_bytes, self.used)
+                    results, bufs, hold = self._price(bs, payloads, now)
+                    # the batch's stores stay allocated until its prices are home
+                    deliveries.append((rt.record(), results, bufs, hold, nb))
+                    tp = st.add("price", tp)
                 self.stats.peak_bytes = max(self.stats.peak_bytes, self.used)
-                done = self._price(bs, payloads, now)
-                t = self._now(t0)
-                for res in done:
-                    res.done = t
-                finished.extend(done)
-                self.used -= sum(request_bytes("bs", r["size"]) for r in bs)
-                tp = st.add("price", tp)
-            self.stats.peak_bytes = max(self.stats.peak_bytes, self.used)
-            # one tick of every active solve
-            for kind in SOLVERS:
-                if active[kind]:
-                    self.stats.max_active[kind] = max(self.stats.max_active.get(kind, 0), len(active[kind]))
-                    self._iterate(kind, active[kind])
-                    for s in active[kind]:
-                        s.it += self.C
-            tp = st.add("iterate", tp)
-            if self.overlap:
-                setup_new()                      # host work while the GPU iterates; they join next tick
-                tp = st.add("setup", tp)
-            self.stats.ticks += 1
-            self._advance(0.0)
-            # convergence test of every solve that iterated, one gather
-            sols = [s for s in active["cg"] + active["bicgstab"] if s.it > 0]
-            if sols:
-                arrs = []
-                for s in sols:
-                    arrs += [s.bb, s.st.rho if s.res.kind == "cg" else s.st.rr]
-                vals = self.rt.read_scalars(arrs)  # synchronises the stream
-                tp = st.add("read_scalars", tp)
-                self._inflight.clear()
-                retire = []
-                for i, s in enumerate(sols):
-                    bb, rr = vals[2 * i], vals[2 * i + 1]
-                    rel = math.sqrt(max(rr, 0.0) / bb) if bb > 0 else 0.0
-                    if rel <= self.tol or s.it >= self.max_iters or not math.isfinite(rel):
-                        s.res.rel_residual = rel
-                        s.res.converged = rel <= self.tol
-                        retire.append(s)
-                # solutions go from one batched copy kernel straight into
-                # mapped page-locked host buffers, one sync for all of them
-                hold = []
-                if retire:
-                    self.rt.batch_begin()
-                for s in retire:
-                    hx = s.out[:s.st.x.shape[0]]
-                    w = self.rt.wrap_host(hx)
-                    w[...] = s.st.x
-                    hold.append(w)
-                    self.rt.batch_next()
-                    s.res.iterations = s.it
-                    s.res.output = hx if self.keep else None
-                    active[s.res.kind].remove(s)
-                    self.used -= s.nbytes
-                    self.op_users[s.m] -= 1
-                    s.st = s.bb = None
-                if retire:
-                    self.rt.batch_end()
-                    self.rt.sync()
-                    t = self._now(t0)
-                    for s in retire:
-                        s.res.done = t
-                        finished.append(s.res)
-                del hold
-                for s in retire:
-                    self._recycle(s.out)
-                    s.out = None
-                st.add("retire", tp)
-        self.rt.sync()
-        self._inflight.clear()
+                # 3. this group's iterations and its convergence read
+                sols = []
+                for kind in SOLVERS:
+                    if groups[g][kind]:
+                        self.stats.max_active[kind] = max(self.stats.max_active.get(kind, 0), counts[kind] + len(
+                            [r for r in adm if r["kind"] == kind]))
+                        self._iterate(kind, groups[g][kind])
+                        for s in groups[g][kind]:
+                            s.it += self.C
+                        sols += groups[g][kind]
+                tp = st.add("iterate", tp)
+                if sols:
+                    arrs = []
+                    for s in sols:
+                        arrs += [s.bb, s.st.rho if s.res.kind == "cg" else s.st.rr]
+                    work, vals = gbuf[g]
+                    rd = rt.read_scalars_async(arrs, work, vals)
+                    gbuf[g] = (rd.work, rd.vals)
+                    pend[g] = (rd, sols, holds)
+                    st.add("read", tp)
+                self.stats.ticks += 1
+                self._advance(0.0)
+                g = (g + 1) % G
+            rt.sync()
+            complete(block=True)
+        finally:
+            self._inflight.clear()
+            if t_ref is not None:
+                rt.release_ticket(t_ref)
         return finished
 
     def _advance(self, dt: float) -> None:

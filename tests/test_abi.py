@@ -253,6 +253,32 @@ def test_capture_api_needs_a_device_and_checks_state():
     assert e.value.code == -2
 
 
+def test_tickets_and_async_scalar_read_check_their_arguments():
+    """Completion tickets and the asynchronous gather: unknown tickets and
+    null results are refused, and both need a device."""
+    rt = rt0()
+    lib, ctx = B.lib(), rt.ctx
+    assert lib.dfs_record(ctx, None) == -1
+    assert lib.dfs_wait(ctx, 99) == -7
+    assert lib.dfs_poll(ctx, 99, None) == -1
+    done = B.C.c_int32()
+    assert lib.dfs_poll(ctx, 99, B.C.byref(done)) == -7
+    ms = B.C.c_float()
+    assert lib.dfs_ticket_elapsed_ms(ctx, 1, 2, B.C.byref(ms)) == -7
+    assert lib.dfs_ticket_elapsed_ms(ctx, 1, 2, None) == -1
+    assert lib.dfs_ticket_release(ctx, 99) == -7
+    with pytest.raises(B.DfsError) as e:
+        rt.record()
+    assert e.value.code == -2
+    s = rt.empty(())
+    assert lib.dfs_read_scalars_async(ctx, 1, B._i64s([s.handle]), None, None) == -1
+    assert lib.dfs_read_scalars_async(ctx, -1, None, None, None) == -1
+    # host buffers that are not page-locked are refused before anything else
+    work = (B.C.c_int64 * 2)()
+    vals = (B.C.c_double * 1)()
+    assert lib.dfs_read_scalars_async(ctx, 1, B._i64s([s.handle]), work, vals) == -1
+
+
 def test_window_size_triggers_analysis():
     rt = rt0(tile=4, window_size=3)
     a = rt.empty((8,), np.float32)

@@ -235,3 +235,48 @@ def test_payloads_in_mapped_host_memory_give_the_same_results():
     ref, _, _ = _serve(reqs)
     for rid, r in ref.items():
         assert got[rid].iterations == r.iterations and _same(got[rid].output, r.output), rid
+
+
+def test_one_group_and_two_pipelined_groups_agree():
+    """The loop with two groups taking turns (the GPU iterates one group while
+    the host reads the other's residuals) and with one group (the host waits
+    for every read) retire every solve after the same iterations with the
+    same bits: groups change when work runs, not what it computes."""
+    reqs = _requests()
+    two, _, _ = _serve(reqs)
+    one, _, _ = _serve(reqs, overlap=False)
+    assert sorted(two) == sorted(one) == [r["rid"] for r in reqs]
+    for rid, r in two.items():
+        assert r.iterations == one[rid].iterations, rid
+        assert _same(r.output, one[rid].output), rid
+
+
+def test_async_scalar_read_and_tickets():
+    """dfs_read_scalars_async returns the values dfs_read_scalars returns,
+    once its ticket has completed; tickets poll, wait, time and release, and
+    a released ticket is unknown."""
+    with gpu_runtime("persistent", tile=256) as rt:
+        xs = [rt.array(inputs.uniform(i, -1, 1, 500 + 200 * i)) for i in range(5)]
+        dots = [A.dot(x, x) for x in xs]
+        want = rt.read_scalars(dots)
+        t_a = rt.record()
+        rd = rt.read_scalars_async(dots)
+        for x in xs:
+            x *= 2.0                             # work queued behind the read
+        t_b = rt.record()
+        assert rd.values() == want
+        rt.wait(t_b)
+        assert rt.poll(t_a) and rt.poll(t_b)
+        assert rt.elapsed_ms(t_a, t_b) >= 0.0
+        for t in (t_a, t_b):
+            rt.release_ticket(t)
+        with pytest.raises(A.B.DfsError) as e:
+            rt.wait(t_a)
+        assert e.value.code == -7
+        # buffers reused by a second read of other values: (2x).(2x) = 4 x.x exactly
+        dots2 = [A.dot(x, x) for x in xs]
+        rd2 = rt.read_scalars_async(dots2[:3], rd.work, rd.vals)
+        assert rd2.work is rd.work and rd2.values() == [4.0 * v for v in want[:3]]
+        with pytest.raises(A.B.DfsError) as e:
+            rt.read_scalars_async([xs[0]])       # not 0-d
+        assert e.value.code == -1
