@@ -11,7 +11,8 @@
 //   * a launch holding several fused groups (persistent mode) separates them
 //     by grid barriers wherever the previous group was not a replicated
 //     scalar group; scalar groups (all stores 0-d) run redundantly in every
-//     CTA on register copies of the 0-d values;
+//     CTA on register copies of the 0-d values (after a barrier, on warp 0
+//     with a shared-memory broadcast to the rest of the CTA);
 //   * reductions keep one partial per point, finished in a fixed order after
 //     the next barrier (or by the last CTA to exit), so every result is
 //     reproducible and identical between fused and unfused execution.
