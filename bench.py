@@ -946,6 +946,17 @@ def main():
                 "frac": achieved / peaks["hbm_gbs"], "traffic": None,
                 "peak_source": peaks["source"], "kernel": fused["dominant"], "kernel_ms": kern_ms,
                 "launches": fused["dominant_launches"], "algorithmic_bytes_per_launch": alg_bytes}
+    # measured DRAM traffic (ncu) of the dominant kernel where one was taken
+    # at the default size and the launch shape in use (profiles/)
+    shape = dict(base)
+    if tuned:
+        shape.update(tuned["config"])
+    ref_shape = cfg.get("dram_launch_shape")
+    same = ref_shape is not None and all(shape.get(k, 0) == v for k, v in ref_shape.items())
+    if args.workload == "cg" and same and cfg["m"] == 256:
+        roofline["traffic"] = cfg["dram_bytes_per_iteration"]
+    elif args.workload == "batched" and same and cfg["dtype"] == "f64" and cfg["count"] == 256:
+        roofline["traffic"] = cfg["dram_bytes_per_launch"]
     fp64_ops = None
     if args.workload == "cg":
         fp64_ops = nnz + 8 * nn

@@ -20,7 +20,12 @@ BLACK_SCHOLES = dict(n=1 << 26, seed=1, r=0.02, sigma=0.3, tile=16384, block=512
 # CG: 2-D 5-point Poisson on a 256x256 grid, 50 iterations, FP64 values,
 # int32 indices, x* ~ U[-1,1] (seed 0), b = A x*, x0 = 0; five iterations
 # share one flush window (one persistent launch) in the captured solve
-CG = dict(m=256, iters=50, seed=0, tile=512, block=256, unroll=2, iters_per_flush=5, window_size=1024)
+CG = dict(m=256, iters=50, seed=0, tile=512, block=256, unroll=2, iters_per_flush=5, window_size=1024,
+          # DRAM bytes (read + write) per iteration of the fused window, from an
+          # ncu capture of this kernel at this launch shape (profiles/): 5.87 MB
+          # per five-iteration launch; the rest of the traffic is served by L2
+          dram_bytes_per_iteration=5.865728e6 / 5,
+          dram_launch_shape=dict(tile=512, block=256, unroll=2))
 
 # Batched CG: 256 independent solves of uneven size (half 2-D Poisson with m
 # log-uniform in [32, 1024], half random diagonally dominant SPD with n
@@ -29,7 +34,11 @@ CG = dict(m=256, iters=50, seed=0, tile=512, block=256, unroll=2, iters_per_flus
 # for the FP32 variant).  Tiles follow the size-dependent policy (at least two
 # points per problem, at most tile_max elements); the bench autotunes
 # tile_max and the launch shape before capturing.
-BATCHED_CG = dict(count=256, seed=4, iters=100, dtype="f64", tile_max=2048, min_points=2, block=256, unroll=2)
+BATCHED_CG = dict(count=256, seed=4, iters=100, dtype="f64", tile_max=2048, min_points=2, block=256, unroll=2,
+                  # DRAM bytes (read + write) of one FP64 batched iteration, from an
+                  # ncu capture at this launch shape (profiles/)
+                  dram_bytes_per_launch=3.018065e9 + 0.672410e9,
+                  dram_launch_shape=dict(tile_max=2048, block=256, unroll=2, ctas_per_sm=0))
 
 # Jacobi: Fig. 1 stencil on an 8192x8192 FP32 grid (8190^2 interior),
 # 200 sweeps, interior U[0,1] (seed 2), boundary 1.0
