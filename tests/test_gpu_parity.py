@@ -493,6 +493,14 @@ def test_barrier_timeout_is_reported_and_context_survives():
             rt.sync()
         assert e.value.code == -6
         rt.sync()                                # error consumed; context usable
+        # the same time-out surfaces through a completion ticket
+        W.cg_iteration(Am, st)
+        t = rt.record()
+        with pytest.raises(B.DfsError) as e:
+            rt.wait(t)
+        assert e.value.code == -6
+        rt.release_ticket(t)
+        rt.sync()
     # a fresh context on the same device computes correctly
     x, *_ = _cg_gpu("persistent", 32, 5, tile=256)
     xo, *_ = _cg_oracle(32, 5)
