@@ -631,7 +631,7 @@ def run_serving(args, torch, stream, sms, cache, dev):
     def server():
         return SV.Server(rt, inputs.poisson3d_csr, budget_bytes=int(cfg["budget_gb"] * 1e9), tol=cfg["tol"],
                          iters_per_tick=cfg["iters_per_tick"], max_active=cfg["max_active"], keep_outputs=False,
-                         overlap=not args.no_overlap)
+                         overlap=not args.no_overlap, templates=not args.no_templates)
 
     # resident operators (every rung of the ladder), loaded before serving
     t_load = time.perf_counter()
@@ -744,6 +744,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bs", choices=["bs", "cg", "jacobi", "batched", "serve"])
     ap.add_argument("--requests", type=int, default=0, help="serving: requests per run (default: the config's)")
+    ap.add_argument("--no-templates", action="store_true",
+                    help="serving: issue every iteration task by task instead of replaying recorded windows")
     ap.add_argument("--no-overlap", action="store_true",
                     help="serving: one group of solves (the host waits for every convergence read)")
     ap.add_argument("--fp32", action="store_true", help="batched CG in FP32 instead of FP64")

@@ -410,6 +410,42 @@ int dfs_ticket_elapsed_ms(dfs_ctx *ctx, uint64_t from, uint64_t to, float *ms);
 int dfs_ticket_release(dfs_ctx *ctx, uint64_t ticket);
 
 /*
+ * Instance templates: the memoisation of Section 5.2 carried to task issue.
+ * A serving loop issues the same iteration window for every solve of a size,
+ * differing only in the stores; recording it once and replaying it with the
+ * stores substituted costs one call per instance instead of one per task.
+ *
+ * dfs_template_begin starts recording.  Until dfs_template_end, every store
+ * creation, view, task submission and store release is recorded as well as
+ * performed.  Calls that a replay cannot repeat (dfs_store_write, _wrap,
+ * _wrap_host, _read, the dfs_batch_* and capture/graph calls, the scalar
+ * reads, dfs_record) fail with DFS_ERR_STATE while recording, and so does
+ * releasing a store the recording did not create; either makes
+ * dfs_template_end fail.  dfs_template_end also fails unless every store the
+ * recording created (temporaries and views) was released by its end.  On
+ * success *id names the template.
+ *
+ * The template's inputs are the stores it used but did not create, in first
+ * use order; dfs_template_inputs copies up to cap of them to out and sets *n
+ * to their number.  dfs_template_replay issues the recorded sequence again
+ * with from[i] replaced by to[i] (n pairs): fresh stores for the recorded
+ * creations and views, the same partitions, privileges and immediates.  Every
+ * input must be mapped to a live store of the dtype and shape it had when it
+ * was recorded (DFS_ERR_INVALID otherwise, checked before anything is
+ * issued).  A replay may run inside a batch instance (between dfs_batch_begin
+ * / dfs_batch_next).  A partition handle keeps the tiling it was created
+ * with, so a template replays the tiling it recorded.
+ * dfs_template_free forgets a template.  Templates are freed at dfs_shutdown.
+ * Returns DFS_OK; DFS_ERR_INVALID for null pointers or bad counts;
+ * DFS_ERR_STATE for nesting, an unknown template, or a failed recording.
+ */
+int dfs_template_begin(dfs_ctx *ctx);
+int dfs_template_end(dfs_ctx *ctx, uint64_t *id);
+int dfs_template_inputs(dfs_ctx *ctx, uint64_t id, int32_t cap, dfs_store *out, int32_t *n);
+int dfs_template_replay(dfs_ctx *ctx, uint64_t id, int32_t n, const dfs_store *from, const dfs_store *to);
+int dfs_template_free(dfs_ctx *ctx, uint64_t id);
+
+/*
  * dfs_set_launch_config -- changes the launch parameters of a live context
  * (block_threads: 128, 256, 512 or 1024; unroll: 1..8; ctas_per_sm: 0 =
  * as many as fit, else that many, with registers capped to fit them; see

@@ -291,6 +291,23 @@ class Runtime:
         buffers (host_empty) of at least 2 n int64 and n float64."""
         return ScalarRead(self, arrays, work, vals)
 
+    # ----------------------------------------------------------- templates
+    def record_template(self, step, *args):
+        """Runs step(*args) while recording its store creations, views, tasks
+        and releases (dfs_template_begin/end) and returns the Template.  The
+        step must release everything it creates (its temporaries go out of
+        scope when it returns)."""
+        B.dfs_template_begin(self.ctx)
+        try:
+            step(*args)
+        except BaseException:
+            try:
+                B.dfs_template_end(self.ctx)
+            except B.DfsError:
+                pass
+            raise
+        return Template(self, B.dfs_template_end(self.ctx))
+
     # ------------------------------------------------------------- tickets
     def record(self) -> int:
         """A ticket for the work issued so far (dfs_record)."""
@@ -321,6 +338,28 @@ class Runtime:
     def graph_destroy(self, graph: int):
         B.dfs_graph_destroy(self.ctx, graph)
 
+
+
+
+class Template:
+    """A recorded instance window (Runtime.record_template): replay() issues
+    it again with its input stores replaced, in one call."""
+
+    def __init__(self, rt: "Runtime", tid: int):
+        self.rt, self.id = rt, tid
+        self.inputs = B.dfs_template_inputs(rt.ctx, tid)
+
+    def replay(self, src, dst) -> None:
+        """src, dst: arrays (or store handles) pairwise; every input of the
+        template must appear in src."""
+        h = [a.handle if isinstance(a, Array) else int(a) for a in src]
+        g = [a.handle if isinstance(a, Array) else int(a) for a in dst]
+        B.dfs_template_replay(self.rt.ctx, self.id, h, g)
+
+    def free(self) -> None:
+        if self.id is not None:
+            B.dfs_template_free(self.rt.ctx, self.id)
+            self.id = None
 
 
 class ScalarRead:

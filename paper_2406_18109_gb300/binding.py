@@ -39,7 +39,8 @@ EXPORTS = ("dfs_config_default", "dfs_init", "dfs_shutdown", "dfs_store_create",
            "dfs_batch_next", "dfs_batch_end", "dfs_batch_repeat", "dfs_read_scalars",
            "dfs_set_launch_config", "dfs_store_wrap_host", "dfs_host_alloc", "dfs_host_free",
            "dfs_read_scalars_async", "dfs_record", "dfs_wait", "dfs_poll", "dfs_ticket_elapsed_ms",
-           "dfs_ticket_release")
+           "dfs_ticket_release", "dfs_template_begin", "dfs_template_end", "dfs_template_inputs",
+           "dfs_template_replay", "dfs_template_free")
 
 
 class dfs_config(C.Structure):
@@ -114,6 +115,11 @@ def lib():
             "dfs_poll": (C.c_int, [P, C.c_uint64, C.POINTER(C.c_int32)]),
             "dfs_ticket_elapsed_ms": (C.c_int, [P, C.c_uint64, C.c_uint64, C.POINTER(C.c_float)]),
             "dfs_ticket_release": (C.c_int, [P, C.c_uint64]),
+            "dfs_template_begin": (C.c_int, [P]),
+            "dfs_template_end": (C.c_int, [P, C.POINTER(C.c_uint64)]),
+            "dfs_template_inputs": (C.c_int, [P, C.c_uint64, I32, pI64, C.POINTER(C.c_int32)]),
+            "dfs_template_replay": (C.c_int, [P, C.c_uint64, I32, pI64, pI64]),
+            "dfs_template_free": (C.c_int, [P, C.c_uint64]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -331,6 +337,32 @@ def dfs_ticket_elapsed_ms(ctx, t_from: int, t_to: int) -> float:
 
 def dfs_ticket_release(ctx, ticket: int) -> None:
     _check(ctx, lib().dfs_ticket_release(ctx, ticket))
+
+
+def dfs_template_begin(ctx) -> None:
+    _check(ctx, lib().dfs_template_begin(ctx))
+
+
+def dfs_template_end(ctx) -> int:
+    t = C.c_uint64()
+    _check(ctx, lib().dfs_template_end(ctx, C.byref(t)))
+    return t.value
+
+
+def dfs_template_inputs(ctx, tid: int) -> list:
+    n = C.c_int32()
+    _check(ctx, lib().dfs_template_inputs(ctx, tid, 0, None, C.byref(n)))
+    out = (C.c_int64 * max(1, n.value))()
+    _check(ctx, lib().dfs_template_inputs(ctx, tid, n.value, out, C.byref(n)))
+    return list(out[:n.value])
+
+
+def dfs_template_replay(ctx, tid: int, src, dst) -> None:
+    _check(ctx, lib().dfs_template_replay(ctx, tid, len(src), _i64s(src), _i64s(dst)))
+
+
+def dfs_template_free(ctx, tid: int) -> None:
+    _check(ctx, lib().dfs_template_free(ctx, tid))
 
 
 def dfs_set_launch_config(ctx, block_threads: int, unroll: int, ctas_per_sm: int) -> None:

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cstdio>
 #include <cstring>
@@ -141,6 +142,26 @@ struct dfs_ctx {
   std::map<uint64_t, cudaEvent_t> tickets;
   std::vector<cudaEvent_t> ticket_pool;
   uint64_t next_ticket = 1;
+  // instance templates (dfs_template_*): a recorded sequence of store
+  // creations, views, submissions and releases, replayed with other stores
+  struct RecEv {
+    int kind = 0;  // 0 create, 1 view, 2 submit, 3 release
+    int64_t h = 0, parent = 0;
+    int32_t dtype = 0, ndim = 0, op = 0;
+    int64_t shape[DFS_MAX_DIM] = {0, 0, 0}, off[DFS_MAX_DIM] = {0, 0, 0}, dom[DFS_MAX_DIM] = {1, 1, 1};
+    std::vector<dfs_arg> args;
+  };
+  struct Template {
+    std::vector<RecEv> evs;
+    std::vector<int64_t> ext;                    // stores used but not created, in first-use order
+    std::vector<std::array<int64_t, 2 + DFS_MAX_DIM>> ext_info;  // dtype, ndim, shape
+  };
+  bool recording = false;
+  std::string rec_fault;                         // why the recording cannot become a template
+  Template rec;
+  std::set<int64_t> rec_created, rec_live;
+  std::map<uint64_t, Template> templates;
+  uint64_t next_template = 1;
 };
 
 namespace dfs {
@@ -1183,6 +1204,35 @@ cudaEvent_t* find_ticket(dfs_ctx* c, uint64_t t) {
 }  // namespace
 }  // namespace dfs
 
+namespace dfs {
+namespace {
+
+// Template recording: notes a store the recorded sequence uses; a store it
+// did not create is an input of the template (first use fixes its dtype and
+// shape, which every replay's store must match).
+void rec_use(dfs_ctx* c, int64_t h) {
+  if (c->rec_created.count(h)) return;
+  for (int64_t e : c->rec.ext)
+    if (e == h) return;
+  const StoreRec* r = find_store(c, h);
+  if (!r) return;
+  std::array<int64_t, 2 + DFS_MAX_DIM> info{};
+  info[0] = r->dtype;
+  info[1] = r->ndim;
+  for (int d = 0; d < r->ndim; ++d) info[2 + d] = r->shape[d];
+  c->rec.ext.push_back(h);
+  c->rec.ext_info.push_back(info);
+}
+
+// Entry points that a template cannot replay refuse to run while recording.
+int refuse_recording(dfs_ctx* c, const char* who) {
+  c->rec_fault = std::string(who) + " while recording a template";
+  return fail(c, DFS_ERR_STATE, c->rec_fault);
+}
+
+}  // namespace
+}  // namespace dfs
+
 using namespace dfs;
 
 // No C++ exception may cross the C ABI: an internal failure (a violated
@@ -1354,7 +1404,19 @@ static int new_store(dfs_ctx* c, int32_t dtype, int32_t ndim, const int64_t* sha
 
 int dfs_store_create(dfs_ctx* c, int32_t dtype, int32_t ndim, const int64_t* shape, dfs_store* out) {
   try {
-    return new_store(c, dtype, ndim, shape, out, true);
+    const int rc = new_store(c, dtype, ndim, shape, out, true);
+    if (rc == DFS_OK && c->recording) {
+      dfs_ctx::RecEv ev;
+      ev.kind = 0;
+      ev.h = *out;
+      ev.dtype = dtype;
+      ev.ndim = ndim;
+      for (int d = 0; d < ndim; ++d) ev.shape[d] = shape[d];
+      c->rec.evs.push_back(ev);
+      c->rec_created.insert(*out);
+      c->rec_live.insert(*out);
+    }
+    return rc;
   } catch (const std::exception& e_) {
     return internal_error(c, e_.what());
   } catch (...) {
@@ -1365,6 +1427,7 @@ int dfs_store_create(dfs_ctx* c, int32_t dtype, int32_t ndim, const int64_t* sha
 int dfs_store_wrap(dfs_ctx* c, int32_t dtype, int32_t ndim, const int64_t* shape, void* dev_ptr, dfs_store* out) {
   try {
     if (!c) return DFS_ERR_INVALID;
+    if (c->recording) return refuse_recording(c, "dfs_store_wrap");
     if (!dev_ptr) return fail(c, DFS_ERR_INVALID, "null device pointer");
     int rc = new_store(c, dtype, ndim, shape, out, false);
     if (rc) return rc;
@@ -1384,6 +1447,7 @@ int dfs_store_wrap_host(dfs_ctx* c, int32_t dtype, int32_t ndim, const int64_t* 
                         dfs_store* out) {
   try {
     if (!c) return DFS_ERR_INVALID;
+    if (c->recording) return refuse_recording(c, "dfs_store_wrap_host");
     if (!host_ptr || !out) return fail(c, DFS_ERR_INVALID, "null pointer");
     if (!c->device) return fail(c, DFS_ERR_NO_DEVICE, "analysis-only context");
     if (dtype < DFS_F32 || dtype > DFS_I64 || ndim < 0 || ndim > MAXD || (ndim > 0 && !shape))
@@ -1466,6 +1530,21 @@ int dfs_store_view(dfs_ctx* c, dfs_store parent, const int64_t* offset, const in
     root.app_refs += 1;
     c->stores[v.handle] = v;
     *out = v.handle;
+    if (c->recording) {
+      rec_use(c, parent);
+      dfs_ctx::RecEv ev;
+      ev.kind = 1;
+      ev.h = v.handle;
+      ev.parent = parent;
+      ev.ndim = v.ndim;
+      for (int d = 0; d < v.ndim; ++d) {
+        ev.off[d] = offset[d];
+        ev.shape[d] = shape[d];
+      }
+      c->rec.evs.push_back(ev);
+      c->rec_created.insert(v.handle);
+      c->rec_live.insert(v.handle);
+    }
     return DFS_OK;
   } catch (const std::exception& e_) {
     return internal_error(c, e_.what());
@@ -1479,6 +1558,17 @@ int dfs_store_release(dfs_ctx* c, dfs_store s) {
     if (!c) return DFS_ERR_INVALID;
     StoreRec* r = find_store(c, s);
     if (!r) return fail(c, DFS_ERR_STATE, "unknown or already released store");
+    if (c->recording) {
+      if (!c->rec_created.count(s)) {
+        c->rec_fault = "a template may release only stores it created";
+      } else {
+        dfs_ctx::RecEv ev;
+        ev.kind = 3;
+        ev.h = s;
+        c->rec.evs.push_back(ev);
+        c->rec_live.erase(s);
+      }
+    }
     const int64_t root = r->root;
     r->released = true;
     StoreRec& rr = c->stores.at(root);
@@ -1496,6 +1586,7 @@ int dfs_store_release(dfs_ctx* c, dfs_store s) {
 int dfs_store_write(dfs_ctx* c, dfs_store s, const void* host_src, size_t bytes) {
   try {
     if (!c) return DFS_ERR_INVALID;
+    if (c->recording) return refuse_recording(c, "dfs_store_write");
     StoreRec* r = find_store(c, s);
     if (!r) return fail(c, DFS_ERR_STATE, "unknown or released store");
     if (r->root != r->handle) return fail(c, DFS_ERR_INVALID, "write a root store, not a view");
@@ -1539,6 +1630,7 @@ static int check_device_error(dfs_ctx* c) {
 int dfs_store_read(dfs_ctx* c, dfs_store s, void* host_dst, size_t bytes) {
   try {
     if (!c) return DFS_ERR_INVALID;
+    if (c->recording) return refuse_recording(c, "dfs_store_read");
     StoreRec* r = find_store(c, s);
     if (!r) return fail(c, DFS_ERR_STATE, "unknown or released store");
     if (!c->device) return fail(c, DFS_ERR_NO_DEVICE, "analysis-only context");
@@ -1693,6 +1785,17 @@ int dfs_submit(dfs_ctx* c, int32_t op, int32_t ndim, const int64_t* dom, int32_t
     }
     int rc = validate(c, t);
     if (rc) return rc;
+    if (c->recording) {
+      dfs_ctx::RecEv ev;
+      ev.kind = 2;
+      ev.op = op;
+      ev.ndim = ndim;
+      for (int d = 0; d < ndim; ++d) ev.dom[d] = dom[d];
+      ev.args.assign(args, args + nargs);
+      for (int i = 0; i < nargs; ++i)
+        if (args[i].privilege != DFS_PRIV_IMM) rec_use(c, args[i].store);
+      c->rec.evs.push_back(std::move(ev));
+    }
     for (const Arg& a : t.args)
       if (!a.imm) c->stores.at(a.root).pending += 1;
     c->window.push_back(std::move(t));
@@ -1748,6 +1851,7 @@ int dfs_sync(dfs_ctx* c) {
 int dfs_capture_begin(dfs_ctx* c) {
   try {
     if (!c) return DFS_ERR_INVALID;
+    if (c->recording) return refuse_recording(c, "dfs_capture_begin");
     if (!c->device) return fail(c, DFS_ERR_NO_DEVICE, "analysis-only context");
     if (c->capturing) return fail(c, DFS_ERR_STATE, "already capturing");
     int rc = flush(c);
@@ -1777,6 +1881,7 @@ int dfs_capture_begin(dfs_ctx* c) {
 int dfs_capture_end(dfs_ctx* c, dfs_graph* out) {
   try {
     if (!c || !out) return DFS_ERR_INVALID;
+    if (c->recording) return refuse_recording(c, "dfs_capture_end");
     if (!c->capturing) return fail(c, DFS_ERR_STATE, "not capturing");
     int rc = flush(c);
     cudaGraph_t graph = nullptr;
@@ -1835,6 +1940,7 @@ int dfs_capture_end(dfs_ctx* c, dfs_graph* out) {
 int dfs_graph_launch(dfs_ctx* c, dfs_graph h) {
   try {
     if (!c) return DFS_ERR_INVALID;
+    if (c->recording) return refuse_recording(c, "dfs_graph_launch");
     auto it = c->graphs.find(h);
     if (it == c->graphs.end()) return fail(c, DFS_ERR_STATE, "unknown graph");
     if (c->capturing) return fail(c, DFS_ERR_STATE, "cannot launch a graph while capturing");
@@ -1871,6 +1977,7 @@ int dfs_graph_destroy(dfs_ctx* c, dfs_graph h) {
 int dfs_batch_begin(dfs_ctx* c) {
   try {
     if (!c) return DFS_ERR_INVALID;
+    if (c->recording) return refuse_recording(c, "dfs_batch_begin");
     if (c->batching) return fail(c, DFS_ERR_STATE, "already batching");
     const int rc = flush(c);
     if (rc) return rc;
@@ -1887,6 +1994,7 @@ int dfs_batch_begin(dfs_ctx* c) {
 int dfs_batch_next(dfs_ctx* c) {
   try {
     if (!c) return DFS_ERR_INVALID;
+    if (c->recording) return refuse_recording(c, "dfs_batch_next");
     if (!c->batching) return fail(c, DFS_ERR_STATE, "dfs_batch_next outside a batch");
     c->batch_marks.push_back(c->window.size());
     return DFS_OK;
@@ -1900,6 +2008,7 @@ int dfs_batch_next(dfs_ctx* c) {
 int dfs_batch_end(dfs_ctx* c) {
   try {
     if (!c) return DFS_ERR_INVALID;
+    if (c->recording) return refuse_recording(c, "dfs_batch_end");
     if (!c->batching) return fail(c, DFS_ERR_STATE, "dfs_batch_end outside a batch");
     c->batching = false;
     const int rc = flush_batch(c);
@@ -1915,6 +2024,7 @@ int dfs_batch_end(dfs_ctx* c) {
 int dfs_batch_repeat(dfs_ctx* c, int32_t n) {
   try {
     if (!c) return DFS_ERR_INVALID;
+    if (c->recording) return refuse_recording(c, "dfs_batch_repeat");
     if (n < 0) return fail(c, DFS_ERR_INVALID, "negative repeat count");
     if (c->batching) return fail(c, DFS_ERR_STATE, "dfs_batch_repeat inside a batch");
     if (!c->device) return fail(c, DFS_ERR_NO_DEVICE, "analysis-only context");
@@ -1942,6 +2052,7 @@ int dfs_batch_repeat(dfs_ctx* c, int32_t n) {
 int dfs_read_scalars(dfs_ctx* c, int32_t n, const dfs_store* hs, double* out) {
   try {
     if (!c) return DFS_ERR_INVALID;
+    if (c->recording) return refuse_recording(c, "dfs_read_scalars");
     if (n < 0 || (n > 0 && (!hs || !out))) return fail(c, DFS_ERR_INVALID, "bad arguments");
     int rc = gather_check(c, n, hs, "dfs_read_scalars");
     if (rc) return rc;
@@ -1967,6 +2078,7 @@ int dfs_read_scalars(dfs_ctx* c, int32_t n, const dfs_store* hs, double* out) {
 int dfs_read_scalars_async(dfs_ctx* c, int32_t n, const dfs_store* hs, int64_t* host_work, double* host_vals) {
   try {
     if (!c) return DFS_ERR_INVALID;
+    if (c->recording) return refuse_recording(c, "dfs_read_scalars_async");
     if (n < 0 || (n > 0 && (!hs || !host_work || !host_vals))) return fail(c, DFS_ERR_INVALID, "bad arguments");
     if (n > 0 && (!page_locked(host_work, (size_t)n * 2 * sizeof(int64_t)) ||
                   !page_locked(host_vals, (size_t)n * sizeof(double))))
@@ -1986,6 +2098,7 @@ int dfs_read_scalars_async(dfs_ctx* c, int32_t n, const dfs_store* hs, int64_t* 
 int dfs_record(dfs_ctx* c, uint64_t* ticket) {
   try {
     if (!c) return DFS_ERR_INVALID;
+    if (c->recording) return refuse_recording(c, "dfs_record");
     if (!ticket) return fail(c, DFS_ERR_INVALID, "null ticket");
     if (!c->device) return fail(c, DFS_ERR_NO_DEVICE, "analysis-only context");
     if (c->capturing) return fail(c, DFS_ERR_STATE, "dfs_record while capturing");
@@ -2077,6 +2190,128 @@ int dfs_ticket_release(dfs_ctx* c, uint64_t ticket) {
     if (it == c->tickets.end()) return fail(c, DFS_ERR_STATE, "unknown ticket");
     c->ticket_pool.push_back(it->second);
     c->tickets.erase(it);
+    return DFS_OK;
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
+  }
+}
+
+int dfs_template_begin(dfs_ctx* c) {
+  try {
+    if (!c) return DFS_ERR_INVALID;
+    if (c->recording) return fail(c, DFS_ERR_STATE, "already recording a template");
+    if (c->capturing) return fail(c, DFS_ERR_STATE, "dfs_template_begin while capturing");
+    c->recording = true;
+    c->rec = dfs_ctx::Template{};
+    c->rec_created.clear();
+    c->rec_live.clear();
+    c->rec_fault.clear();
+    return DFS_OK;
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
+  }
+}
+
+int dfs_template_end(dfs_ctx* c, uint64_t* id) {
+  try {
+    if (!c) return DFS_ERR_INVALID;
+    if (!c->recording) return fail(c, DFS_ERR_STATE, "not recording a template");
+    c->recording = false;
+    std::string why = c->rec_fault;
+    if (why.empty() && !c->rec_live.empty()) why = "the recorded sequence did not release every store it created";
+    if (why.empty() && !id) why = "null template id";
+    if (!why.empty()) {
+      c->rec = dfs_ctx::Template{};
+      return fail(c, id ? DFS_ERR_STATE : DFS_ERR_INVALID, why);
+    }
+    const uint64_t t = c->next_template++;
+    c->templates[t] = std::move(c->rec);
+    c->rec = dfs_ctx::Template{};
+    *id = t;
+    return DFS_OK;
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
+  }
+}
+
+int dfs_template_inputs(dfs_ctx* c, uint64_t id, int32_t cap, dfs_store* out, int32_t* n) {
+  try {
+    if (!c) return DFS_ERR_INVALID;
+    if (!n || (cap > 0 && !out) || cap < 0) return fail(c, DFS_ERR_INVALID, "bad arguments");
+    auto it = c->templates.find(id);
+    if (it == c->templates.end()) return fail(c, DFS_ERR_STATE, "unknown template");
+    const auto& ext = it->second.ext;
+    *n = (int32_t)ext.size();
+    for (int32_t i = 0; i < cap && i < (int32_t)ext.size(); ++i) out[i] = ext[i];
+    return DFS_OK;
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
+  }
+}
+
+int dfs_template_replay(dfs_ctx* c, uint64_t id, int32_t n, const dfs_store* from, const dfs_store* to) {
+  try {
+    if (!c) return DFS_ERR_INVALID;
+    if (n < 0 || (n > 0 && (!from || !to))) return fail(c, DFS_ERR_INVALID, "bad arguments");
+    if (c->recording) return fail(c, DFS_ERR_STATE, "dfs_template_replay while recording a template");
+    auto it = c->templates.find(id);
+    if (it == c->templates.end()) return fail(c, DFS_ERR_STATE, "unknown template");
+    const dfs_ctx::Template& T = it->second;
+    std::unordered_map<int64_t, int64_t> m;
+    for (int32_t i = 0; i < n; ++i) m[from[i]] = to[i];
+    // every input mapped to a live store of the recorded dtype and shape,
+    // checked before anything is issued
+    for (size_t k = 0; k < T.ext.size(); ++k) {
+      auto mi = m.find(T.ext[k]);
+      if (mi == m.end()) return fail(c, DFS_ERR_INVALID, "a template input is not mapped");
+      const StoreRec* r = find_store(c, mi->second);
+      if (!r) return fail(c, DFS_ERR_STATE, "a template input maps to an unknown or released store");
+      const auto& info = T.ext_info[k];
+      bool same = r->dtype == info[0] && r->ndim == info[1];
+      for (int d = 0; same && d < r->ndim; ++d) same = r->shape[d] == info[2 + d];
+      if (!same) return fail(c, DFS_ERR_INVALID, "a template input maps to a store of another dtype or shape");
+    }
+    std::vector<dfs_arg> args;
+    for (const dfs_ctx::RecEv& ev : T.evs) {
+      int rc = DFS_OK;
+      if (ev.kind == 0) {
+        dfs_store h = 0;
+        rc = new_store(c, ev.dtype, ev.ndim, ev.shape, &h, true);
+        m[ev.h] = h;
+      } else if (ev.kind == 1) {
+        dfs_store h = 0;
+        rc = dfs_store_view(c, m.at(ev.parent), ev.off, ev.shape, &h);
+        m[ev.h] = h;
+      } else if (ev.kind == 2) {
+        args = ev.args;
+        for (dfs_arg& a : args)
+          if (a.privilege != DFS_PRIV_IMM) a.store = m.at(a.store);
+        rc = dfs_submit(c, ev.op, ev.ndim, ev.dom, (int32_t)args.size(), args.data());
+      } else {
+        rc = dfs_store_release(c, m.at(ev.h));
+      }
+      if (rc) return rc;  // the error message names the failing step; earlier steps stay issued
+    }
+    return DFS_OK;
+  } catch (const std::exception& e_) {
+    return internal_error(c, e_.what());
+  } catch (...) {
+    return internal_error(c, "unknown exception");
+  }
+}
+
+int dfs_template_free(dfs_ctx* c, uint64_t id) {
+  try {
+    if (!c) return DFS_ERR_INVALID;
+    if (!c->templates.erase(id)) return fail(c, DFS_ERR_STATE, "unknown template");
     return DFS_OK;
   } catch (const std::exception& e_) {
     return internal_error(c, e_.what());

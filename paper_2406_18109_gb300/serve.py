@@ -19,7 +19,9 @@ groups that take turns on one CUDA stream; a turn of group g:
   3. issue iters_per_tick iterations of every solve of g -- all solves of
      one kind form the instances of one batched launch (their uneven sizes
      share one persistent kernel), repeated with dfs_batch_repeat -- and the
-     asynchronous read of their residuals.
+     asynchronous read of their residuals.  An instance's iteration window is
+     recorded once per kind and operator size and replayed over each solve's
+     stores (dfs_template_replay): one call per instance, not one per task.
 
 A result is complete when its copy to the host has finished (a completion
 ticket, dfs_record); with the real clock its completion time is the device
@@ -169,7 +171,8 @@ class Server:
 
     def __init__(self, rt: A.Runtime, operator, *, budget_bytes: int = 120 * 10 ** 9, tol: float = 1e-8,
                  iters_per_tick: int = 8, max_iters: int = 20000, max_active: int = 64, clock=None,
-                 keep_outputs: bool = True, bs_rate: float = 0.02, bs_sigma: float = 0.3, overlap: bool = True):
+                 keep_outputs: bool = True, bs_rate: float = 0.02, bs_sigma: float = 0.3, overlap: bool = True,
+                 templates: bool = True):
         self.rt = rt
         self.operator_fn = operator
         self.budget = int(budget_bytes)
@@ -181,6 +184,11 @@ class Server:
         self.keep = keep_outputs
         self.bs_rate, self.bs_sigma = bs_rate, bs_sigma
         self.overlap = overlap
+        # recorded iteration windows per (kind, operator size), replayed for
+        # every other solve of that size (dfs_template_*): one call per
+        # instance instead of one per task
+        self.use_templates = templates
+        self._templates: dict[tuple, object] = {}
         self.ops: OrderedDict[int, A.CSR] = OrderedDict()   # resident operators, LRU order
         self.op_users: dict[int, int] = {}
         self.used = 0
@@ -287,15 +295,44 @@ class Server:
         self._inflight.append((items, xs_all))
         return sols
 
+    @staticmethod
+    def _stores_of(s) -> list:
+        """The stores one iteration of solve s reads and writes."""
+        st = s.st
+        vec = ([st.x, st.r, st.p, st.q, st.rho] if s.res.kind == "cg" else
+               [st.x, st.r, st.rhat, st.p, st.v, st.s, st.t, st.rho, st.alpha, st.omega, st.rr])
+        return [s.Am.rowptr, s.Am.col, s.Am.val] + vec
+
+    def _issue_iteration(self, kind, s) -> None:
+        """One iteration of solve s as a batch instance: the recorded window
+        of its kind and size replayed over its stores, else issued task by
+        task (and recorded, the first time)."""
+        step = W.cg_iteration_inplace if kind == "cg" else W.bicgstab_iteration_inplace
+        key = (kind, s.m)
+        ent = self._templates.get(key) if self.use_templates else False
+        if ent:
+            tpl, src = ent
+            tpl.replay(src, [a.handle for a in self._stores_of(s)])
+            return
+        if ent is None:
+            tpl = self.rt.record_template(step, s.Am, s.st)
+            src = [a.handle for a in self._stores_of(s)]
+            if set(tpl.inputs) <= set(src):
+                self._templates[key] = (tpl, src)
+            else:
+                tpl.free()
+                self._templates[key] = False
+            return
+        step(s.Am, s.st)
+
     def _iterate(self, kind, sols) -> None:
         """iters_per_tick iterations of every solve of one kind."""
         rt = self.rt
-        step = W.cg_iteration_inplace if kind == "cg" else W.bicgstab_iteration_inplace
         done = 0
         while done < self.C:
             rt.batch_begin()
             for s in sols:
-                step(s.Am, s.st)
+                self._issue_iteration(kind, s)
                 rt.batch_next()
             rt.batch_end()
             self.stats.batched_launches += 1

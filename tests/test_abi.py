@@ -383,3 +383,86 @@ def test_spmv_lanes_follow_the_mean_row_length(per_row, lanes):
         assert "spmv_row" in src and "spmv_warp" not in src
     else:
         assert f"act_, {lanes});" in src
+
+
+def _cg_inplace(rt, n=16, nnz=40):
+    Am = A.CSR.__new__(A.CSR)
+    Am.rt, Am.nrows, Am.ncols, Am.nnz = rt, n, n, nnz
+    Am.rowptr = rt.empty((n + 1,), np.int32)
+    Am.col = rt.empty((nnz,), np.int32)
+    Am.val = rt.empty((nnz,), np.float64)
+    Am.dtype = np.dtype(np.float64)
+    st = W.CGInPlace(*(rt.empty((n,)) for _ in range(4)), rt.empty(()))
+    return Am, st, [Am.rowptr, Am.col, Am.val, st.x, st.r, st.p, st.q, st.rho]
+
+
+def test_template_replay_issues_the_recorded_window():
+    """A recorded in-place CG iteration replayed over another solve's stores
+    issues the same tasks as submitting that solve's iteration directly: the
+    same canonical window key (Section 5.2), groups and temporaries."""
+    rt = rt0(tile=8, window_size=4096)
+    A1, s1, in1 = _cg_inplace(rt)
+    A2, s2, in2 = _cg_inplace(rt)
+    t0 = rt.stats()["tasks"]
+    tpl = rt.record_template(W.cg_iteration_inplace, A1, s1)
+    ntask = rt.stats()["tasks"] - t0
+    assert ntask >= 10 and sorted(tpl.inputs) == sorted(a.handle for a in in1)
+    with pytest.raises(B.DfsError):
+        rt.flush()                               # no device: the window is analysed and dropped
+    W.cg_iteration_inplace(A2, s2)
+    direct = rt.plan()
+    with pytest.raises(B.DfsError):
+        rt.flush()
+    t1 = rt.stats()["tasks"]
+    tpl.replay(in1, in2)
+    assert rt.stats()["tasks"] - t1 == ntask
+    rep = rt.plan()
+    for k in ("key", "groups", "scalar_groups", "barriers"):
+        assert rep[k] == direct[k], k
+    assert len(rep["temporaries"]) == len(direct["temporaries"]) >= 2   # alpha*p, alpha*q, ...
+    with pytest.raises(B.DfsError):
+        rt.flush()
+    # every input must be mapped, to a store of the recorded shape
+    with pytest.raises(B.DfsError) as e:
+        tpl.replay(in1[:-1], in2[:-1])
+    assert e.value.code == -1
+    other = rt.empty((17,))
+    with pytest.raises(B.DfsError) as e:
+        tpl.replay(in1, in2[:3] + [other] + in2[4:])
+    assert e.value.code == -1
+    tpl.free()
+
+
+def test_template_recording_refuses_what_a_replay_cannot_repeat():
+    rt = rt0(tile=8)
+    x = rt.empty((16,))
+    B.dfs_template_begin(rt.ctx)
+    with pytest.raises(B.DfsError) as e:
+        B.dfs_template_begin(rt.ctx)             # no nesting
+    assert e.value.code == -7
+    with pytest.raises(B.DfsError) as e:
+        rt.batch_begin()
+    assert e.value.code == -7
+    with pytest.raises(B.DfsError) as e:
+        B.dfs_store_write(rt.ctx, x.handle, np.zeros(16).ctypes.data, 128)
+    assert e.value.code == -7
+    with pytest.raises(B.DfsError) as e:
+        B.dfs_template_end(rt.ctx)               # the refused call spoils the recording
+    assert e.value.code == -7
+    # a created store still alive at the end spoils it too
+    B.dfs_template_begin(rt.ctx)
+    keep = x * 2.0
+    with pytest.raises(B.DfsError) as e:
+        B.dfs_template_end(rt.ctx)
+    assert e.value.code == -7
+    del keep
+    # releasing a store the recording did not create
+    y = rt.empty((16,))
+    B.dfs_template_begin(rt.ctx)
+    del y
+    with pytest.raises(B.DfsError) as e:
+        B.dfs_template_end(rt.ctx)
+    assert e.value.code == -7
+    with pytest.raises(B.DfsError) as e:
+        B.dfs_template_end(rt.ctx)               # not recording any more
+    assert e.value.code == -7

@@ -237,6 +237,19 @@ def test_payloads_in_mapped_host_memory_give_the_same_results():
         assert got[rid].iterations == r.iterations and _same(got[rid].output, r.output), rid
 
 
+def test_replayed_iteration_windows_equal_issued_ones():
+    """Iterations replayed from a recorded window per kind and size
+    (dfs_template_replay) retire every solve after the same iterations with
+    the same bits as iterations issued task by task."""
+    reqs = _requests()
+    rep, _, rst = _serve(reqs)
+    plain, _, _ = _serve(reqs, templates=False)
+    assert rst["batch_fallbacks"] == 0, rst["batch_fallback_reason"]
+    for rid, r in rep.items():
+        assert r.iterations == plain[rid].iterations, rid
+        assert _same(r.output, plain[rid].output), rid
+
+
 def test_one_group_and_two_pipelined_groups_agree():
     """The loop with two groups taking turns (the GPU iterates one group while
     the host reads the other's residuals) and with one group (the host waits
