@@ -85,7 +85,9 @@ typedef enum { DFS_REDOP_NONE = 0, DFS_REDOP_SUM = 1 } dfs_redop;
  *     Rounding: every operation rounds once to the store dtype (no
  *     contraction across operations), so a fused window equals the unfused
  *     stream bit for bit.
- *     NCDF(x) = 0.5 * (1 + erf(x * (1/sqrt 2))), evaluated in that order.
+ *     ERF(x) = copysign(erf(|x|), x): the odd extension of the CUDA math
+ *     library's erf on [0, inf], so ERF(-x) = -ERF(x) bit for bit.
+ *     NCDF(x) = 0.5 * (1 + ERF(x * (1/sqrt 2))), evaluated in that order.
  *   DFS_OP_DOT  [x R, y R, out RD(SUM)]   out (+)= sum_e x[e]*y[e]
  *   DFS_OP_SUM  [x R, out RD(SUM)]        out (+)= sum_e x[e]
  *     out is a 0-d store through None.  A reduction into a store that holds

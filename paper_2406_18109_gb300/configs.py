@@ -9,10 +9,10 @@ BLACK_SCHOLES = dict(n=1 << 26, seed=1, r=0.02, sigma=0.3, tile=16384, block=512
                      # thread instructions per option of the fused kernel (ncu
                      # smsp__inst_executed x 32 / options); the kernel is bound
                      # by instruction issue, see profiles/
-                     inst_per_option=187.0,
+                     inst_per_option=151.45,
                      # DRAM bytes (read + write) of one launch at n = 2^26, from
                      # an ncu capture of this kernel (profiles/)
-                     dram_bytes_per_launch=1307.45e6,
+                     dram_bytes_per_launch=1307.31e6,
                      # end to end (host arrays): kernels on mapped host memory
                      # ("zero_copy") or copies pipelined in chunks over contexts
                      e2e_mode="zero_copy", e2e_chunk=1 << 23, e2e_contexts=2)

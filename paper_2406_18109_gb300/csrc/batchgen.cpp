@@ -337,6 +337,7 @@ void BatchGen::vector_group(int g) {
             const std::string v = rd.var + "_" + slots[s];
             cur[rd.key] = w > 1 ? v + ".v[" + std::to_string(l) + "]" : v;
           }
+          LaneOps lane;
           for (int k = i; k < j; ++k) {
             const Task& t = S.tasks[k];
             const int dt = t.args.back().dtype;
@@ -348,9 +349,9 @@ void BatchGen::vector_group(int g) {
             };
             const std::string res = "v" + std::to_string(k) + "_" + slots[s] + "_" + std::to_string(l);
             if (is_ew(t.op)) {
-              o << pad << "const " << T(dt) << " " << res << " = " << op_device_fn(t.op) << "(" << val(0);
-              if (t.args.size() == 3) o << ", " << val(1);
-              o << ");\n";
+              std::vector<std::string> in{val(0)};
+              if (t.args.size() == 3) in.push_back(val(1));
+              lane.emit(o, pad, T(dt), t.op, res, in);
               cur[akey(t.args.back())] = res;
             } else if (t.op == DFS_OP_SPMV && spre.count(k)) {
               o << pad << "const " << T(dt) << " " << res << " = " << spre.at(k) << "_" << l << ";\n";

@@ -584,6 +584,7 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
           const std::string v = rd.var + "_" + slots[s];
           cur[rd.key] = (w > 1) ? v + ".v[" + std::to_string(l) + "]" : v;
         }
+        LaneOps lane;
         for (int i = n.first; i < n.last; ++i) {
           const Task& t = S.tasks[i];
           if (t.scalar()) continue;
@@ -596,9 +597,9 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
           };
           const std::string res = "v" + std::to_string(i) + "_" + slots[s] + "_" + std::to_string(l);
           if (is_elementwise(t.op)) {
-            o << pad << "const " << T(dt) << " " << res << " = " << op_fn(t.op) << "(" << val(0);
-            if (t.args.size() == 3) o << ", " << val(1);
-            o << ");\n";
+            std::vector<std::string> in{val(0)};
+            if (t.args.size() == 3) in.push_back(val(1));
+            lane.emit(o, pad, T(dt), t.op, res, in);
             cur[akey(t.args.back())] = res;
           } else if (t.op == DFS_OP_SPMV && spre.count(i)) {
             o << pad << "const " << T(dt) << " " << res << " = " << spre.at(i) << "_" << l << ";\n";
@@ -981,6 +982,53 @@ KernelCode Gen::run() {
 }  // namespace
 
 const char* op_device_fn(int op) { return op_fn(op); }
+
+std::string LaneOps::shared(const std::map<std::string, std::string>& m, const std::string& a) const {
+  auto it = m.find(a);
+  if (it != m.end()) return it->second;
+  auto ng = neg_.find(a);
+  if (ng != neg_.end()) {
+    it = m.find(ng->second);
+    if (it != m.end()) return it->second;
+  }
+  return std::string();
+}
+
+void LaneOps::emit(std::ostream& o, const std::string& pad, const std::string& T, int op, const std::string& res,
+                   const std::vector<std::string>& in) {
+  if (op == DFS_OP_ERF) {
+    // |-a| = |a| bit for bit, so erf(|a|) serves a and its negation
+    std::string m = shared(mag_, in[0]);
+    if (m.empty()) {
+      m = res + "_m";
+      o << pad << "const " << T << " " << m << " = erf_mag(" << in[0] << ");\n";
+    }
+    mag_[in[0]] = m;
+    o << pad << "const " << T << " " << res << " = erf_sign(" << m << ", " << in[0] << ");\n";
+    return;
+  }
+  if (op == DFS_OP_NCDF) {
+    // the scaled arguments of a and -a differ only in sign (round to
+    // nearest is symmetric), so they share erf of their magnitude
+    const std::string y = res + "_y";
+    o << pad << "const " << T << " " << y << " = ncdf_arg(" << in[0] << ");\n";
+    std::string m = shared(nmag_, in[0]);
+    if (m.empty()) {
+      m = res + "_m";
+      o << pad << "const " << T << " " << m << " = erf_mag(" << y << ");\n";
+    }
+    nmag_[in[0]] = m;
+    o << pad << "const " << T << " " << res << " = ncdf_of_erf(erf_sign(" << m << ", " << y << "));\n";
+    return;
+  }
+  o << pad << "const " << T << " " << res << " = " << op_fn(op) << "(" << in[0];
+  for (size_t k = 1; k < in.size(); ++k) o << ", " << in[k];
+  o << ");\n";
+  if (op == DFS_OP_NEG) {
+    neg_.emplace(res, in[0]);
+    neg_.emplace(in[0], res);
+  }
+}
 
 KernelCode generate(const LaunchSpec& spec) {
   Gen g(spec);

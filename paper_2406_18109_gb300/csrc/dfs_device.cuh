@@ -52,15 +52,24 @@ __device__ __forceinline__ float op_log(float a) { return logf(a); }
 __device__ __forceinline__ double op_log(double a) { return log(a); }
 __device__ __forceinline__ float op_sqrt(float a) { return __fsqrt_rn(a); }
 __device__ __forceinline__ double op_sqrt(double a) { return __dsqrt_rn(a); }
-__device__ __forceinline__ float op_erf(float a) { return erff(a); }
-__device__ __forceinline__ double op_erf(double a) { return erf(a); }
-// Standard normal CDF through erf: 0.5 * (1 + erf(x * (1/sqrt 2))).
-__device__ __forceinline__ float op_ncdf(float a) {
-  return op_mul(0.5f, op_add(1.0f, op_erf(op_mul(a, 0.70710678118654752440f))));
-}
-__device__ __forceinline__ double op_ncdf(double a) {
-  return op_mul(0.5, op_add(1.0, op_erf(op_mul(a, 0.70710678118654752440))));
-}
+// erf is odd, and ERF is defined as the odd extension of the library's erf on
+// [0, inf]: op_erf(a) = copysign(erf(|a|), a).  Any two arguments of equal
+// magnitude then share erf_mag exactly, which lets a fused body evaluate
+// N(d) and N(-d) with one erf (the code generator's sharing of negations).
+__device__ __forceinline__ float erf_mag(float a) { return erff(fabsf(a)); }
+__device__ __forceinline__ double erf_mag(double a) { return erf(fabs(a)); }
+__device__ __forceinline__ float erf_sign(float m, float a) { return copysignf(m, a); }
+__device__ __forceinline__ double erf_sign(double m, double a) { return copysign(m, a); }
+__device__ __forceinline__ float op_erf(float a) { return erf_sign(erf_mag(a), a); }
+__device__ __forceinline__ double op_erf(double a) { return erf_sign(erf_mag(a), a); }
+// Standard normal CDF through erf: 0.5 * (1 + erf(x * (1/sqrt 2))), in steps:
+// the scaled argument, erf of it, then the affine map.
+__device__ __forceinline__ float ncdf_arg(float a) { return op_mul(a, 0.70710678118654752440f); }
+__device__ __forceinline__ double ncdf_arg(double a) { return op_mul(a, 0.70710678118654752440); }
+__device__ __forceinline__ float ncdf_of_erf(float e) { return op_mul(0.5f, op_add(1.0f, e)); }
+__device__ __forceinline__ double ncdf_of_erf(double e) { return op_mul(0.5, op_add(1.0, e)); }
+__device__ __forceinline__ float op_ncdf(float a) { return ncdf_of_erf(op_erf(ncdf_arg(a))); }
+__device__ __forceinline__ double op_ncdf(double a) { return ncdf_of_erf(op_erf(ncdf_arg(a))); }
 
 // Reduction step and CSR row product: contraction into FMA is intended here
 // (one task's own arithmetic).

@@ -11,6 +11,7 @@
 #include <cstdint>
 #include <map>
 #include <memory>
+#include <ostream>
 #include <set>
 #include <string>
 #include <unordered_map>
@@ -195,6 +196,25 @@ KernelCode generate(const LaunchSpec& spec);
 
 // Device template of an element-wise op ("op_add", ...), nullptr otherwise.
 const char* op_device_fn(int op);
+
+// The element operations of one lane of a fused body, emitted as straight-line
+// code.  ERF is odd by definition (op_erf(a) = copysign(erf(|a|), a)), so
+// when a body takes erf of a value and of its negation (NEG then ERF or NCDF,
+// as in N(d) and N(-d) of the Black-Scholes chain) erf(|.|) is evaluated
+// once and both results keep the exact bits each task computes alone.  One
+// instance per lane: names are the lane's value expressions.
+class LaneOps {
+ public:
+  // Emits `const T res = op(in...)` (possibly in several statements).
+  void emit(std::ostream& o, const std::string& pad, const std::string& T, int op, const std::string& res,
+            const std::vector<std::string>& in);
+
+ private:
+  std::string shared(const std::map<std::string, std::string>& m, const std::string& a) const;
+  std::map<std::string, std::string> neg_;   // value -> a value equal to its negation
+  std::map<std::string, std::string> mag_;   // ERF argument -> erf(|argument|)
+  std::map<std::string, std::string> nmag_;  // NCDF argument x -> erf(|x / sqrt 2|)
+};
 
 // ------------------------------------------------------ batched execution
 // One size-generic kernel for K isomorphic instances of a window.  Sizes,

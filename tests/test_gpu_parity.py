@@ -290,6 +290,52 @@ def test_random_elementwise_windows(dtype):
             assert ok.all(), (trial, s)
 
 
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_erf_of_a_value_and_its_negation(dtype):
+    """ERF and NCDF of x and of NEG(x) in one window: the fused body evaluates
+    erf(|.|) once per pair, and each result keeps the bits of its task run
+    alone (unfused), ERF stays odd bit for bit, and the values match the
+    stored-dtype oracle -- on zeros, infinities, NaN, subnormals and the
+    largest finite values as well as ordinary ones."""
+    fi = np.finfo(dtype)
+    special = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, fi.tiny, fi.tiny / 8, -fi.tiny / 8, fi.max, -fi.max,
+                        1e-3, -0.5, 2.0, 3.9, -4.0, 6.0, 27.0], dtype)
+    x = np.concatenate([special, inputs.uniform(7, -8.0, 8.0, 3000, dtype)])
+    n, tile = x.size, 512
+    dom = ((n + tile - 1) // tile,)
+    stream = [("NEG", 1, [0]), ("ERF", 2, [0]), ("ERF", 3, [1]), ("NCDF", 4, [0]), ("NCDF", 5, [1])]
+    outs = {}
+    for mode in MODES:
+        with gpu_runtime(mode, tile=tile) as rt:
+            arrs = [rt.array(x)] + [rt.array(np.zeros(n, dtype)) for _ in range(5)]
+            for op, o, ins in stream:
+                rt.submit(op, dom, [arrs[i]._arg(B.DFS_PRIV_R) for i in ins] + [arrs[o]._arg(B.DFS_PRIV_W)])
+            outs[mode] = [a.numpy() for a in arrs]
+            if mode == "persistent":
+                src = rt.kernel_source()
+                assert src.count("erf_mag(") * 2 == src.count("erf_sign(")   # one erf per pair
+    for mode in MODES[1:]:
+        for s in range(6):
+            assert np.array_equal(_bits(outs[mode][s]), _bits(outs["persistent"][s])), (mode, s)
+    e, e_neg = outs["persistent"][2], outs["persistent"][3]
+    nan = np.isnan(x)
+    assert np.array_equal(_bits(e_neg[~nan]), _bits(-e[~nan]))
+    assert np.isnan(e[nan]).all() and np.isnan(e_neg[nan]).all()
+    m = Machine("stored")
+    P = Tiling((tile,), (0,), IDENTITY, ((0,), (n,)))
+    m.add(0, x)
+    for s in range(1, 6):
+        m.add(s, np.zeros(n, dtype))
+    for op, o, ins in stream:
+        m.run(XTask(op, dom, [Arg(i, P, "R") for i in ins] + [Arg(o, P, "W")]))
+    for s in range(1, 6):
+        # NCDF = 0.5 (1 + erf): for x << 0 the sum cancels, so its error is
+        # absolute, a few units in the last place of 1
+        rtol, atol = (2e-6 if dtype == np.float32 else 1e-14), (fi.tiny if s < 4 else 4 * fi.eps)
+        ok = np.isclose(outs["persistent"][s], m.arrays[s], rtol=rtol, atol=atol, equal_nan=True)
+        assert ok.all(), (s, x[~ok], outs["persistent"][s][~ok], m.arrays[s][~ok])
+
+
 # ---------------------------------------------------- reductions, SpMV
 @pytest.mark.parametrize("n", [1, 5, 255, 256, 257, 10007])
 def test_dot_and_sum(n):
