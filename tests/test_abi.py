@@ -123,6 +123,25 @@ def test_black_scholes_plan_fuses_everything():
     assert src.count("st4(") == src.count("st4(r3") + src.count("st4(r4")
 
 
+def test_batched_black_scholes_shares_erf_of_negations():
+    """The batched generator emits the same erf sharing as the single-window
+    one: per lane, N(-d1) and N(-d2) reuse erf(|.|) of N(d1) and N(d2)."""
+    rt = rt0(tile=1024)
+    arrs = [[rt.empty((n,), np.float32) for _ in range(3)] for n in (3000, 5000)]
+    keep = []
+    rt.batch_begin()
+    for S, K, T in arrs:
+        keep.append(W.black_scholes(S, K, T, 0.02, 0.3))
+        rt.batch_next()
+    with pytest.raises(B.DfsError) as e:
+        rt.batch_end()
+    assert e.value.code == -2
+    assert rt.stats()["batch_fallbacks"] == 0
+    src = rt.kernel_source()
+    assert "find_inst" in src
+    assert src.count("ncdf_of_erf(") > 0 and src.count("erf_mag(") * 2 == src.count("ncdf_of_erf(")
+
+
 def test_black_scholes_unfused_plan():
     rt = rt0(tile=8, fusion=False, launch="per_task")
     S, K, T = (rt.empty((30,), np.float32) for _ in range(3))
