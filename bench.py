@@ -148,29 +148,57 @@ class Clocks:
 
 
 # ------------------------------------------------------------------ oracle
-def _bs_oracle_worker(job):
-    """One host core pricing 2^20-option batches with the oracle for budget_s."""
-    seed, budget_s = job
+def _oracle_worker(job):
+    """One host core running the oracle on its own copy of the workload's
+    sample for budget_s; returns (units done, seconds)."""
+    workload, seed, budget_s = job
     from oracle import programs
-    cfg = configs.BLACK_SCHOLES
-    m = 1 << 20
-    S, K, T = inputs.bs_inputs(m, seed=seed)
     done, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < budget_s:
-        programs.black_scholes(S, K, T, cfg["r"], cfg["sigma"], np.float32)
-        done += m
+    if workload == "bs":
+        cfg = configs.BLACK_SCHOLES
+        m = 1 << 20
+        S, K, T = inputs.bs_inputs(m, seed=seed)
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < budget_s:
+            programs.black_scholes(S, K, T, cfg["r"], cfg["sigma"], np.float32)
+            done += m
+    elif workload == "cg":
+        cfg = configs.CG
+        rp, col, val, xs = inputs.cg_inputs(m=cfg["m"], seed=seed)
+        b = programs.spmv(rp, col, val, xs)
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < budget_s:
+            programs.cg(rp, col, val, b, 10)
+            done += 10
+    else:
+        cfg = configs.JACOBI
+        g = inputs.jacobi_grid(2046, seed=seed)
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < budget_s:
+            programs.jacobi(g, 2, np.float32)
+            done += 2
     return done, time.perf_counter() - t0
 
 
-def oracle_rate_all_cores(budget_s: float = 8.0):
-    """The Black-Scholes oracle on every host core at once (independent
-    batches in spawned processes; BLAS single-threaded in each)."""
+ALL_CORES_SAMPLE = {
+    "bs": "independent 2^20-option batches, one process per host core",
+    "cg": "independent 256^2 Poisson CG solves (10 iterations at a time), one process per host core",
+    "jacobi": "independent 2048^2 grids, one process per host core, sweeps scaled by area to 8192^2",
+}
+
+
+def oracle_rate_all_cores(workload: str = "bs", budget_s: float = 8.0):
+    """The oracle on every host core at once: independent problems in spawned
+    processes, BLAS single-threaded in each (the workload's weak-scaling rate
+    on the host)."""
     import multiprocessing as mp
     n = os.cpu_count() or 1
     with mp.get_context("spawn").Pool(n) as pool:
-        res = pool.map(_bs_oracle_worker, [(1000 + i, budget_s) for i in range(n)])
-    done = sum(d for d, _ in res)
-    return done / max(t for _, t in res), n
+        res = pool.map(_oracle_worker, [(workload, 1000 + i, budget_s) for i in range(n)])
+    rate = sum(d for d, _ in res) / max(t for _, t in res)
+    if workload == "jacobi":
+        rate *= (2046 * 2046) / (configs.JACOBI["N"] * configs.JACOBI["N"])
+    return rate, n
 
 
 def oracle_rate(workload: str, budget_s: float = 10.0):
@@ -997,10 +1025,10 @@ def main():
     if rank == 0 and world == 1 and not args.quick:
         v, u, sample = oracle_rate(args.workload, budget_s=10.0)
         cpu = {"value": v, "unit": u, "cores": 1, "kind": "oracle", "sample": sample}
-        if args.workload == "bs":
-            va, nc = oracle_rate_all_cores()
+        if args.workload in ALL_CORES_SAMPLE:
+            va, nc = oracle_rate_all_cores(args.workload)
             cpu["all_cores"] = {"value": va, "unit": u, "cores": nc,
-                                "sample": "independent 2^20-option batches, one process per host core, 8 s"}
+                                "sample": ALL_CORES_SAMPLE[args.workload] + ", 8 s"}
 
     line = {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
