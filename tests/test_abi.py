@@ -142,6 +142,32 @@ def test_batched_black_scholes_shares_erf_of_negations():
     assert src.count("ncdf_of_erf(") > 0 and src.count("erf_mag(") * 2 == src.count("ncdf_of_erf(")
 
 
+@pytest.mark.parametrize("stream, mags_per_sign", [
+    # ERF of x and NCDF of -x take erf of different arguments: nothing shared
+    ([("NEG", 1, 0), ("ERF", 2, 0), ("NCDF", 3, 1)], 1.0),
+    # N(-x) first, then N(x): the pair shares one erf either way round
+    ([("NEG", 1, 0), ("NCDF", 2, 1), ("NCDF", 3, 0)], 0.5),
+    # erf(-x) and erf(x) share too
+    ([("NEG", 1, 0), ("ERF", 2, 1), ("ERF", 3, 0)], 0.5),
+    # -(-x) is x again, but only a direct negation is tracked: no sharing
+    ([("NEG", 1, 0), ("NEG", 2, 1), ("NCDF", 3, 0), ("NCDF", 4, 2)], 1.0),
+])
+def test_erf_sharing_follows_negations_only(stream, mags_per_sign):
+    """Where a fused body evaluates erf(|.|) once for two results: exactly for
+    a value and its direct negation, and never across ERF and NCDF (whose erf
+    arguments differ by the 1/sqrt 2 scaling)."""
+    n, tile = 3001, 512
+    rt = rt0(tile=tile)
+    arrs = [rt.empty((n,), np.float32) for _ in range(5)]
+    for op, o, i in stream:
+        rt.submit(op, ((n + tile - 1) // tile,), [arrs[i]._arg(B.DFS_PRIV_R), arrs[o]._arg(B.DFS_PRIV_W)])
+    with pytest.raises(B.DfsError) as e:
+        rt.flush()
+    assert e.value.code == -2
+    src = rt.kernel_source()
+    assert src.count("erf_mag(") == mags_per_sign * src.count("erf_sign(")
+
+
 def test_black_scholes_unfused_plan():
     rt = rt0(tile=8, fusion=False, launch="per_task")
     S, K, T = (rt.empty((30,), np.float32) for _ in range(3))
