@@ -434,7 +434,10 @@ int dfs_ticket_release(dfs_ctx *ctx, uint64_t ticket);
  * creations and views, the same partitions, privileges and immediates.  Every
  * input must be mapped to a live store of the dtype and shape it had when it
  * was recorded (DFS_ERR_INVALID otherwise, checked before anything is
- * issued).  A replay may run inside a batch instance (between dfs_batch_begin
+ * issued).  If a later step fails (say, a flush the window size triggers
+ * cannot allocate), the call returns that step's error: tasks issued before
+ * it stay issued, and the stores this replay created are released, so none
+ * outlives what still uses it.  A replay may run inside a batch instance (between dfs_batch_begin
  * / dfs_batch_next).  A partition handle keeps the tiling it was created
  * with, so a template replays the tiling it recorded.
  * dfs_template_free forgets a template.  Templates are freed at dfs_shutdown.

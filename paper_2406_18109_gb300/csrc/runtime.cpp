@@ -2258,6 +2258,17 @@ int dfs_template_inputs(dfs_ctx* c, uint64_t id, int32_t cap, dfs_store* out, in
 }
 
 int dfs_template_replay(dfs_ctx* c, uint64_t id, int32_t n, const dfs_store* from, const dfs_store* to) {
+  // stores this replay created and has not released yet: if a step fails,
+  // their application references are dropped, so nothing the caller cannot
+  // name stays allocated (tasks already issued keep what they use alive)
+  std::vector<dfs_store> live;
+  auto undo = [&]() {
+    if (!c || live.empty()) return;
+    const std::string why = c->err;
+    for (auto h = live.rbegin(); h != live.rend(); ++h)
+      if (find_store(c, *h)) dfs_store_release(c, *h);
+    c->err = why;
+  };
   try {
     if (!c) return DFS_ERR_INVALID;
     if (n < 0 || (n > 0 && (!from || !to))) return fail(c, DFS_ERR_INVALID, "bad arguments");
@@ -2286,25 +2297,40 @@ int dfs_template_replay(dfs_ctx* c, uint64_t id, int32_t n, const dfs_store* fro
         dfs_store h = 0;
         rc = new_store(c, ev.dtype, ev.ndim, ev.shape, &h, true);
         m[ev.h] = h;
+        if (!rc) live.push_back(h);
       } else if (ev.kind == 1) {
         dfs_store h = 0;
         rc = dfs_store_view(c, m.at(ev.parent), ev.off, ev.shape, &h);
         m[ev.h] = h;
+        if (!rc) live.push_back(h);
       } else if (ev.kind == 2) {
         args = ev.args;
         for (dfs_arg& a : args)
           if (a.privilege != DFS_PRIV_IMM) a.store = m.at(a.store);
         rc = dfs_submit(c, ev.op, ev.ndim, ev.dom, (int32_t)args.size(), args.data());
       } else {
-        rc = dfs_store_release(c, m.at(ev.h));
+        const dfs_store h = m.at(ev.h);
+        rc = dfs_store_release(c, h);
+        if (!rc) {
+          auto li = std::find(live.begin(), live.end(), h);
+          if (li != live.end()) live.erase(li);
+        }
       }
-      if (rc) return rc;  // the error message names the failing step; earlier steps stay issued
+      if (rc) {
+        // the error message names the failing step; earlier tasks stay issued
+        undo();
+        return rc;
+      }
     }
     return DFS_OK;
   } catch (const std::exception& e_) {
-    return internal_error(c, e_.what());
+    const int rc = internal_error(c, e_.what());
+    undo();
+    return rc;
   } catch (...) {
-    return internal_error(c, "unknown exception");
+    const int rc = internal_error(c, "unknown exception");
+    undo();
+    return rc;
   }
 }
 
@@ -2382,6 +2408,7 @@ int dfs_stats_json(dfs_ctx* c, char* buf, size_t len, size_t* needed) {
     o << "}";
     o << ", \"batches\": " << c->batches << ", \"batched_instances\": " << c->batched_instances
       << ", \"window_size\": " << c->cfg.window_size << ", \"window_growths\": " << s.window_growths
+      << ", \"stores\": " << c->stores.size()
     << ", \"batch_repeats\": " << c->batch_repeats << ", \"batch_fallbacks\": " << c->batch_fallbacks << ", \"batch_fallback_reason\": \"" << c->batch_fallback_reason
       << "\"";
     o << ", \"sms\": " << c->sms << "}";

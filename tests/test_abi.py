@@ -480,6 +480,34 @@ def test_template_replay_issues_the_recorded_window():
     tpl.free()
 
 
+def test_failed_replay_releases_the_stores_it_created():
+    """A replay that fails part-way (here the window fills on its first task,
+    and an analysis-only context cannot launch the flush) leaves no store of
+    its own behind: the temporary it had created is released with it."""
+    rt = rt0(tile=8, window_size=3)
+    a, b = rt.empty((16,)), rt.empty((16,))
+
+    def step(a, b):
+        t = a * 2.0
+        b += t
+    tpl = rt.record_template(step, a, b)
+    assert rt.stats()["tasks"] == 2
+    with pytest.raises(B.DfsError):
+        rt.flush()                                # analysed and dropped: the recorded t is freed
+    base = rt.stats()["stores"]
+    b += 1.0
+    b += 1.0                                      # two tasks in the window, no new store
+    with pytest.raises(B.DfsError) as e:
+        tpl.replay([a, b], [a, b])                # its MUL is the window's third task
+    assert e.value.code == -2
+    assert rt.stats()["stores"] == base
+    tpl.replay([a, b], [a, b])                    # a fresh window takes the whole replay
+    assert rt.stats()["stores"] == base + 1       # t stays alive for the pending tasks
+    with pytest.raises(B.DfsError):
+        rt.flush()
+    assert rt.stats()["stores"] == base
+
+
 def test_template_recording_refuses_what_a_replay_cannot_repeat():
     rt = rt0(tile=8)
     x = rt.empty((16,))
