@@ -1300,9 +1300,21 @@ int dfs_init(dfs_ctx** out, const dfs_config* cfg_in) {
         if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return DFS_ERR_CUDA;
         c->own_stream = true;
       }
-      if (cudaMalloc(&c->ctl, sizeof(Ctl)) != cudaSuccess) return DFS_ERR_OOM;
-      if (cudaMemset(c->ctl, 0, sizeof(Ctl)) != cudaSuccess) return DFS_ERR_CUDA;
-      if (cudaDeviceSynchronize() != cudaSuccess) return DFS_ERR_CUDA;
+      // a failure from here on gives back the stream and control block
+      auto undo = [&](int rc) {
+        if (c->ctl) cudaFree(c->ctl);
+        c->ctl = nullptr;
+        if (c->own_stream) cudaStreamDestroy(c->stream);
+        c->stream = nullptr;
+        c->own_stream = false;
+        return rc;
+      };
+      if (cudaMalloc(&c->ctl, sizeof(Ctl)) != cudaSuccess) {
+        c->ctl = nullptr;
+        return undo(DFS_ERR_OOM);
+      }
+      if (cudaMemset(c->ctl, 0, sizeof(Ctl)) != cudaSuccess) return undo(DFS_ERR_CUDA);
+      if (cudaDeviceSynchronize() != cudaSuccess) return undo(DFS_ERR_CUDA);
       c->device = true;
       (void)cp;
     } else {
