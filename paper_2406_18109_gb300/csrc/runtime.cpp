@@ -231,15 +231,18 @@ bool arity_ok(int op, int nargs) {
 bool elementwise(int op) { return (op >= DFS_OP_COPY && op <= DFS_OP_NCDF) || (op >= DFS_OP_ADD && op <= DFS_OP_MIN); }
 
 // Shape of a non-0-d argument's sub-store as a function of the point.
-std::string shape_key(const Arg& a) {
-  std::ostringstream o;
-  o << a.part.kind;
+// Two accesses touch sub-stores of one shape at every point: the same
+// partition kind and rank, extents, and (tilings) tile, offset from the view
+// origin and projection.
+bool same_substores(const Arg& a, const Arg& b) {
+  if (a.part.kind != b.part.kind || a.nd != b.nd) return false;
   for (int d = 0; d < a.nd; ++d) {
-    o << "[" << (a.part.vhi[d] - a.part.vlo[d]);
-    if (a.part.kind) o << "," << a.part.tile[d] << "," << (a.part.off[d] - a.part.vlo[d]) << "," << a.part.proj[d];
-    o << "]";
+    if (a.part.vhi[d] - a.part.vlo[d] != b.part.vhi[d] - b.part.vlo[d]) return false;
+    if (a.part.kind && (a.part.tile[d] != b.part.tile[d] || a.part.proj[d] != b.part.proj[d] ||
+                        a.part.off[d] - a.part.vlo[d] != b.part.off[d] - b.part.vlo[d]))
+      return false;
   }
-  return o.str();
+  return true;
 }
 
 int validate(dfs_ctx* c, const Task& t) {
@@ -280,16 +283,15 @@ int validate(dfs_ctx* c, const Task& t) {
     const Arg& out = A.back();
     if (out.imm || !out.is_w() || out.is_rd()) return bad("element-wise output must be a store with W or RW");
     if (!dtype_is_float(out.dtype)) return bad("element-wise ops need a floating dtype");
-    std::string key;
+    const Arg* first = nullptr;  // the first operand with a shape
     for (size_t k = 0; k + 1 < A.size(); ++k)
       if (!A[k].imm && A[k].priv != DFS_PRIV_R) return bad("element-wise inputs are read (R) or immediates");
     for (const Arg& a : A) {
       if (a.imm) continue;
       if (a.dtype != out.dtype) return bad("element-wise operands must share one dtype");
       if (a.nd == 0) continue;
-      const std::string k = shape_key(a);
-      if (key.empty()) key = k;
-      else if (k != key) return bad("element-wise operands must have equal sub-store shapes at every point");
+      if (!first) first = &a;
+      else if (!same_substores(a, *first)) return bad("element-wise operands must have equal sub-store shapes at every point");
     }
     if (out.nd == 0 && !scalar_task) return bad("a 0-d output needs every operand 0-d");
     if (out.nd != 0 && out.part.kind == 0 && t.npoints() != 1) return bad("array operands need a tiling when the domain has several points");
@@ -300,7 +302,7 @@ int validate(dfs_ctx* c, const Task& t) {
       if (A[k].imm || A[k].priv != DFS_PRIV_R || A[k].nd == 0) return bad("reduction inputs are non-0-d stores read (R)");
       if (A[k].dtype != out.dtype || !dtype_is_float(out.dtype)) return bad("reduction operands must share one floating dtype");
     }
-    if (op == DFS_OP_DOT && shape_key(A[0]) != shape_key(A[1])) return bad("DOT operands must have equal sub-store shapes");
+    if (op == DFS_OP_DOT && !same_substores(A[0], A[1])) return bad("DOT operands must have equal sub-store shapes");
     if (A[0].part.kind == 0 && t.npoints() != 1) return bad("reduction inputs need a tiling when the domain has several points");
   } else if (op == DFS_OP_SPMV) {
     for (int k = 0; k < 5; ++k)

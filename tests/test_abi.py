@@ -82,6 +82,29 @@ def test_submission_validation():
     assert rt.plan()["groups"] == []
 
 
+def test_operands_must_touch_equal_sub_stores():
+    """Element-wise and DOT operands need sub-stores of one shape at every
+    point: equal extents, tiles, offsets from the view origin and projections.
+    Views of different roots at different origins qualify; a different tile,
+    extent or offset does not."""
+    rt = rt0(tile=4)
+    a = rt.empty((12,), np.float32)
+    b = rt.empty((16,), np.float32)
+    s = rt.empty((), np.float32)
+    T4 = rt.tiling((4,))
+    T2 = rt.tiling((2,))
+    T4o = rt.tiling((4,), offset=(1,))
+    av, bv = a[0:8], b[8:16]                     # 8 elements each, other origins
+    rt.submit("ADD", (2,), [(av.handle, T4, 1), (bv.handle, T4, 1), (av.handle, T4, 2)])
+    rt.submit("DOT", (2,), [(av.handle, T4, 1), (bv.handle, T4, 1), (s.handle, rt.none, 4)])
+    n_ok = rt.stats()["tasks"]
+    expect_invalid(lambda: rt.submit("ADD", (2,), [(av.handle, T4, 1), (bv.handle, T2, 1), (av.handle, T4, 2)]))
+    expect_invalid(lambda: rt.submit("ADD", (3,), [(a.handle, T4, 1), (b[0:12].handle, T4o, 1), (a.handle, T4, 2)]))
+    expect_invalid(lambda: rt.submit("ADD", (2,), [(av.handle, T4, 1), (b[0:12].handle, T4, 1), (av.handle, T4, 2)]))
+    expect_invalid(lambda: rt.submit("DOT", (2,), [(av.handle, T4, 1), (bv.handle, T2, 1), (s.handle, rt.none, 4)]))
+    assert rt.stats()["tasks"] == n_ok
+
+
 def test_view_bounds_checked():
     rt = rt0()
     g = rt.empty((4, 4), np.float32)
