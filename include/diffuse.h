@@ -477,10 +477,11 @@ int dfs_version(void);
  * device WITHOUT allocating any device memory.
  *
  * The paper has no counterpart: this entry point serves callers that cannot
- * allocate when they need a reduction -- code running under CUDA stream
- * capture (cudaMalloc is not allowed there and breaks the capture), serving
- * loops that reserve all device memory at start-up, and plug-ins whose host
- * framework owns every device allocation.
+ * allocate when they need a reduction -- serving or real-time loops that
+ * reserve all their device memory at start-up (an allocation later could
+ * block, synchronise the device or fail under the memory budget), and
+ * plug-ins whose host framework owns every device allocation and hands them
+ * none.
  *
  * x, y: device pointers to n doubles (8-byte aligned); out: device pointer to
  * one double.  All three are owned by the caller.  The result is written
@@ -489,12 +490,14 @@ int dfs_version(void);
  * in order), so repeated calls give identical bits.
  *
  * Scratch: a file-scope __device__ array of DFS_NOALLOC_MAX_N /
- * DFS_NOALLOC_TILE doubles plus a 32-byte counter, held by every GPU that
- * loads the library until the process exits.  Every call on a device shares
+ * DFS_NOALLOC_TILE doubles (128 KB) plus the runtime's 160-byte control block
+ * (exit counter; cleared by every call), held by every GPU that loads the
+ * library until the process exits.  Every call on a device shares
  * it, so calls whose kernels overlap on the GPU (different streams, no
  * ordering between them) race and give wrong results; order them.
  * The first call on each device resolves the scratch's device address with
- * that device current; make that first call before any stream capture.
+ * that device current (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  Host threads may call concurrently.
  *
  * Returns DFS_OK; DFS_ERR_INVALID for null pointers or n < 0;
  * DFS_ERR_TOO_LARGE when n > DFS_NOALLOC_MAX_N (nothing is launched);

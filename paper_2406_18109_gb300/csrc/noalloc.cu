@@ -2,8 +2,6 @@
 //
 // Some callers cannot allocate device memory at the time they need a
 // reduction:
-//   * code running while a CUDA stream capture is active: cudaMalloc is not
-//     allowed during capture and would invalidate the graph being recorded;
 //   * serving or real-time loops that reserve all their device memory at
 //     start-up and must not allocate afterwards, because an allocation can
 //     block, synchronise the device, or fail under a memory budget;
@@ -17,6 +15,7 @@
 // inputs and the output.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <mutex>
 
 #include "../../include/diffuse.h"
@@ -55,11 +54,15 @@ __global__ void __launch_bounds__(kBlock) dot_noalloc_kernel(const double* __res
   }
 }
 
+// Device addresses of the scratch on one device.  The plain fields are
+// written once, under g_mu, before `ready` is set with release ordering; a
+// caller that loads `ready` as true with acquire ordering therefore sees them
+// complete, without taking the lock (host threads may call concurrently).
 struct DeviceScratch {
   double* partials = nullptr;
   dfs::Ctl* ctl = nullptr;
   int sms = 0;
-  bool ready = false;
+  std::atomic<bool> ready{false};
 };
 
 std::mutex g_mu;
@@ -70,7 +73,7 @@ DeviceScratch g_dev[kMaxDevices];
 // once per device, with that device current.
 int setup(int dev, DeviceScratch& s) {
   std::lock_guard<std::mutex> lk(g_mu);
-  if (s.ready) return DFS_OK;
+  if (s.ready.load(std::memory_order_relaxed)) return DFS_OK;   // set by another thread under g_mu
   void* p = nullptr;
   if (cudaGetSymbolAddress(&p, g_partials) != cudaSuccess || !p) return DFS_ERR_CUDA;
   s.partials = static_cast<double*>(p);
@@ -78,7 +81,7 @@ int setup(int dev, DeviceScratch& s) {
   if (cudaGetSymbolAddress(&p, g_ctl) != cudaSuccess || !p) return DFS_ERR_CUDA;
   s.ctl = static_cast<dfs::Ctl*>(p);
   if (cudaDeviceGetAttribute(&s.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return DFS_ERR_CUDA;
-  s.ready = true;
+  s.ready.store(true, std::memory_order_release);
   return DFS_OK;
 }
 
@@ -90,7 +93,7 @@ extern "C" int dfs_dot_noalloc(const double* x, const double* y, int64_t n, doub
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DFS_ERR_CUDA;
   DeviceScratch& s = g_dev[dev];
-  if (!s.ready) {
+  if (!s.ready.load(std::memory_order_acquire)) {
     const int rc = setup(dev, s);
     if (rc) return rc;
   }
