@@ -996,6 +996,8 @@ std::string LaneOps::shared(const std::map<std::string, std::string>& m, const s
 
 void LaneOps::emit(std::ostream& o, const std::string& pad, const std::string& T, int op, const std::string& res,
                    const std::vector<std::string>& in) {
+  if (!defined_.insert(res).second)
+    throw std::runtime_error("code generator: value " + res + " defined twice in one loop body");
   if (op == DFS_OP_ERF) {
     // |-a| = |a| bit for bit, so erf(|a|) serves a and its negation
     std::string m = shared(mag_, in[0]);

@@ -203,6 +203,13 @@ const char* op_device_fn(int op);
 // as in N(d) and N(-d) of the Black-Scholes chain) erf(|.|) is evaluated
 // once and both results keep the exact bits each task computes alone.  One
 // instance per lane: names are the lane's value expressions.
+//
+// Invariant: every expression handed to emit (an operand or a result) names
+// an immutable per-lane value -- a `const` load, an immediate, a 0-d register
+// that no task of the loop nest writes, or an earlier result `v<task>_...`.
+// A store rewritten inside the window gets a new result name, so sharing
+// keyed by these strings can never reuse a stale value.  emit refuses (throws)
+// a result name it has already defined.
 class LaneOps {
  public:
   // Emits `const T res = op(in...)` (possibly in several statements).
@@ -214,6 +221,7 @@ class LaneOps {
   std::map<std::string, std::string> neg_;   // value -> a value equal to its negation
   std::map<std::string, std::string> mag_;   // ERF argument -> erf(|argument|)
   std::map<std::string, std::string> nmag_;  // NCDF argument x -> erf(|x / sqrt 2|)
+  std::set<std::string> defined_;            // result names emitted so far
 };
 
 // ------------------------------------------------------ batched execution

@@ -79,7 +79,8 @@ def test_batched_fp32():
         rp, col, val, xs = inputs.batched_cg_matrix(SPECS[i])
         b = programs.spmv(rp, col, val.astype(np.float32), xs.astype(np.float32), np.float32)
         xo, _, _ = programs.cg(rp, col, val, b, iters, dt=np.float32)
-        assert np.linalg.norm(xb[i] - xo) / np.linalg.norm(xo) < 1e-4
+        # FP32 reductions against the stored-dtype oracle: 1e-5 (measured on GB300: 1.4e-7)
+        assert np.linalg.norm(xb[i] - xo) / np.linalg.norm(xo) < 1e-5
 
 
 def test_batched_graph_replay():
@@ -145,7 +146,7 @@ def test_cached_batch_kernel_serves_new_stores():
             assert st["batches"] == rnd + 1 and st["batch_fallbacks"] == 0
             for (S, K, T), (c, p) in zip(data, outs):
                 co, po = programs.black_scholes(S, K, T, prm["r"], prm["sigma"], np.float32)
-                tol = 1e-5 * (S.astype(np.float64) + K)
+                tol = 4 * np.finfo(np.float32).eps * (S.astype(np.float64) + K)   # stored-dtype oracle
                 assert np.all(np.abs(c.numpy() - co) <= tol) and np.all(np.abs(p.numpy() - po) <= tol)
             del arrs, outs
 

@@ -2,9 +2,11 @@
 
 The iteration is the naturally written program of workloads.bicgstab_iteration
 (two SpMVs, five dot products, scalar updates, vector updates per iteration).
-FP64 results must agree with the FP64 oracle to 1e-10 norm-wise after a fixed
-number of iterations (BiCGSTAB's non-monotone residual amplifies rounding
-differences more than CG's), and fused must equal unfused bit for bit."""
+FP64 results must agree with the FP64 oracle to 1e-12 norm-wise after a fixed
+number of iterations (measured on GB300: 1.1e-14), and fused must equal
+unfused bit for bit.  The residual norm is the norm of a difference that
+cancels, so it is compared to 1e-12 of ||b|| and to 1e-10 of itself
+(measured: 4.7e-12 of itself)."""
 import numpy as np
 import pytest
 
@@ -40,8 +42,8 @@ def test_bicgstab_matches_oracle(mode):
     b = programs.spmv(rp, col, val, xs)
     xo, it, rel = programs.bicgstab(rp, col, val, b, 0.0, iters)
     assert it == iters
-    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-10
-    assert abs(np.sqrt(rr) / np.linalg.norm(b) - rel) <= 1e-8 * rel + 1e-14
+    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-12
+    assert abs(np.sqrt(rr) / np.linalg.norm(b) - rel) <= min(1e-12, 1e-10 * rel)
     if mode == "persistent":
         # set-up takes at most two launches, then one launch per iteration
         assert st["launches"] <= iters + 2
@@ -72,7 +74,7 @@ def test_bicgstab_converges_to_manufactured_solution():
 
 def test_inplace_iteration_matches_oracle():
     """The in-place form (state stores updated in place, used by batching and
-    serving) before convergence: 1e-10 norm-wise, as the naturally written one."""
+    serving) before convergence: 1e-12 norm-wise, as the naturally written one."""
     m, iters = 13, 15
     rp, col, val = inputs.poisson3d_csr(m)
     xs = inputs.uniform(9, -1, 1, m ** 3)
@@ -85,5 +87,5 @@ def test_inplace_iteration_matches_oracle():
         x, rr = s.x.numpy(), float(s.rr.numpy())
     b = programs.spmv(rp, col, val, xs)
     xo, it, rel = programs.bicgstab(rp, col, val, b, 0.0, iters)
-    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-10
-    assert abs(np.sqrt(rr) / np.linalg.norm(b) - rel) <= 1e-8 * rel + 1e-14
+    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-12
+    assert abs(np.sqrt(rr) / np.linalg.norm(b) - rel) <= min(1e-12, 1e-10 * rel)

@@ -51,7 +51,7 @@ def test_replayed_cg_iteration_matches_oracle(mode):
     bo = programs.spmv(rp, col, val, xs)
     xo, _, rhoo = programs.cg(rp, col, val, bo, iters)
     assert _rel(x, xo) < 1e-12
-    assert abs(rho - rhoo) <= 1e-10 * abs(rhoo)
+    assert abs(rho - rhoo) <= 1e-12 * abs(rhoo)
     xi, rhoi = _cg_inplace(mode, m, iters, graph=False)
     assert np.array_equal(x.view(np.uint64), xi.view(np.uint64)) and rho == rhoi
 

@@ -2,7 +2,8 @@
 
 Every comparison runs the same seeded inputs through the CUDA path (via the
 C-ABI) and through ``oracle/``.  Tolerances: FP64 reductions/solvers 1e-12
-norm-wise relative; FP32 Black-Scholes |diff| <= 1e-5 (S + K) per option;
+norm-wise relative; FP32 Black-Scholes |diff| <= 1e-5 (S + K) per option
+against the FP64 oracle and <= 4 eps32 (S + K) against the stored-dtype one;
 element-wise FP32 work whose operations round the same way on both sides
 (the Jacobi stencil: adds and a multiply) bit for bit.  Fused execution must
 equal unfused execution bit for bit (every element operation rounds once).
@@ -42,14 +43,29 @@ def test_black_scholes_matches_oracle(mode):
     S, K, T = inputs.bs_inputs(n, seed=BS["seed"])
     c, p, st = _bs_gpu(mode, S, K, T, tile=4096)
     scale = S.astype(np.float64) + K.astype(np.float64)
-    for dt in (np.float32, np.float64):
-        c_o, p_o = programs.black_scholes(S, K, T, BS["r"], BS["sigma"], dt)
-        assert np.all(np.abs(c - c_o) <= 1e-5 * scale)
-        assert np.all(np.abs(p - p_o) <= 1e-5 * scale)
+    c64, p64 = programs.black_scholes(S, K, T, BS["r"], BS["sigma"], np.float64)
+    assert np.all(np.abs(c - c64) <= 1e-5 * scale)
+    assert np.all(np.abs(p - p64) <= 1e-5 * scale)
+    _assert_stored_dtype_close(S, K, T, c, p)
     if mode == "persistent":
         assert st["launches"] == 1
     if mode == "unfused":
         assert st["launches"] == W.BLACK_SCHOLES_TASKS
+
+
+def _assert_stored_dtype_close(S, K, T, c, p):
+    """Against the stored-dtype oracle (the same 23 steps, each rounded to
+    float32): the two sides differ only in the library's log, exp and erf
+    (each within a couple of float32 ulp on both sides), so every price agrees
+    to a few ulp of the terms it is made of: |diff| <= 4 eps32 (S + K).
+    Measured on GB300 over 100,003 options: 2.1 eps32 (S + K) at most, 57 % of
+    calls and 67 % of puts bit-identical.  A wrong constant in the chain (say
+    1/sqrt 2 to four digits) moves prices by tens of eps32 S."""
+    c32, p32 = programs.black_scholes(S, K, T, BS["r"], BS["sigma"], np.float32)
+    tol = 4 * np.finfo(np.float32).eps * (S.astype(np.float64) + K.astype(np.float64))
+    assert np.all(np.abs(c.astype(np.float64) - c32) <= tol)
+    assert np.all(np.abs(p.astype(np.float64) - p32) <= tol)
+
 
 
 def test_black_scholes_fused_equals_unfused_bitwise():
@@ -73,6 +89,7 @@ def test_black_scholes_full_size_sampled():
     scale = S[idx].astype(np.float64) + K[idx].astype(np.float64)
     assert np.all(np.abs(c[idx] - c_o) <= 1e-5 * scale)
     assert np.all(np.abs(p[idx] - p_o) <= 1e-5 * scale)
+    _assert_stored_dtype_close(S[idx], K[idx], T[idx], c[idx], p[idx])
     # put-call parity holds at every one of the 2^26 options
     lhs = c.astype(np.float64) - p.astype(np.float64)
     rhs = S.astype(np.float64) - K.astype(np.float64) * np.exp(-BS["r"] * T.astype(np.float64))
@@ -110,9 +127,10 @@ def test_cg_matches_oracle(mode):
     x, r, rho, b, st = _cg_gpu(mode, m, iters, tile=256)
     xo, ro, rhoo, bo = _cg_oracle(m, iters)
     assert _rel(b, bo) < 1e-14
+    # measured on GB300: x 1.2e-15, r 2.6e-14, rho 4.8e-14 (relative)
     assert _rel(x, xo) < 1e-12
-    assert _rel(r, ro) < 1e-10 * max(1.0, np.linalg.norm(bo) / np.linalg.norm(ro))
-    assert abs(rho - rhoo) <= 1e-10 * abs(rhoo) + 1e-30
+    assert _rel(r, ro) < 1e-12
+    assert abs(rho - rhoo) <= 1e-12 * abs(rhoo)
     if mode == "persistent":
         # b = A x* and the CG start share one flush, then one launch per iteration
         assert st["launches"] == iters + 1 and st["barriers"] == 2 * iters
@@ -123,7 +141,7 @@ def test_cg_single_point_domain():
     # scalar divides share it and the paper's pass fuses them with vector tasks
     x, r, rho, b, st = _cg_gpu("persistent", 20, 25, tile=512)
     xo, ro, rhoo, bo = _cg_oracle(20, 25)
-    assert _rel(x, xo) < 1e-12 and abs(rho - rhoo) <= 1e-10 * abs(rhoo)
+    assert _rel(x, xo) < 1e-12 and abs(rho - rhoo) <= 1e-12 * abs(rhoo)
     xu, *_ = _cg_gpu("unfused", 20, 25, tile=512)
     assert np.array_equal(_bits(x), _bits(xu))
 
@@ -140,8 +158,8 @@ def test_cg_full_size():
     x, r, rho, b, st = _cg_gpu("persistent", cfg["m"], cfg["iters"], tile=cfg["tile"],
                                block=cfg["block"], unroll=cfg["unroll"])
     xo, ro, rhoo, bo = _cg_oracle(cfg["m"], cfg["iters"])
-    assert _rel(x, xo) < 1e-12
-    assert abs(rho - rhoo) <= 1e-10 * abs(rhoo)
+    assert _rel(x, xo) < 1e-12 and _rel(r, ro) < 1e-12
+    assert abs(rho - rhoo) <= 1e-12 * abs(rhoo)
     assert st["kernels_compiled"] + st["kernel_disk_hits"] <= 4    # isomorphic iterations share one kernel
     assert st["plan_hits"] >= cfg["iters"] - 1
 
@@ -334,6 +352,52 @@ def test_erf_of_a_value_and_its_negation(dtype):
         rtol, atol = (2e-6 if dtype == np.float32 else 1e-14), (fi.tiny if s < 4 else 4 * fi.eps)
         ok = np.isclose(outs["persistent"][s], m.arrays[s], rtol=rtol, atol=atol, equal_nan=True)
         assert ok.all(), (s, x[~ok], outs["persistent"][s][~ok], m.arrays[s][~ok])
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_erf_sharing_after_a_rewrite_in_the_window(dtype):
+    """A value and its negation stop being negations once either store is
+    rewritten inside the window: the fused body must then evaluate erf of the
+    new value, not reuse the magnitude it computed for the old one.  Stores 0
+    and 1 are rewritten between the NEG and the ERF/NCDF tasks that read them;
+    fused results equal the unfused tasks bit for bit."""
+    n, tile = 4099, 512
+    dom = ((n + tile - 1) // tile,)
+    x = inputs.uniform(31, -3.0, 3.0, n, dtype)
+    z = inputs.uniform(32, -3.0, 3.0, n, dtype)
+    stream = [("NEG", 1, [0]), ("ERF", 2, [0]), ("NCDF", 3, [1]),
+              ("ADD", 0, [4, 0.25]),                        # store 0 rewritten after its negation
+              ("ERF", 5, [0]), ("ERF", 6, [1]), ("NCDF", 7, [0]), ("NCDF", 8, [1]),
+              ("NEG", 9, [0]), ("MUL", 1, [4, 1.5]),         # now store 1 (the old negation) rewritten
+              ("ERF", 10, [9]), ("ERF", 11, [1]), ("NCDF", 12, [9]), ("NCDF", 13, [1])]
+    nst = 14
+    outs = {}
+    for mode in MODES:
+        with gpu_runtime(mode, tile=tile) as rt:
+            arrs = [rt.array(x), rt.array(np.zeros(n, dtype)), rt.array(np.zeros(n, dtype)),
+                    rt.array(np.zeros(n, dtype)), rt.array(z)] + [rt.array(np.zeros(n, dtype)) for _ in range(5, nst)]
+            for op, o, ins in stream:
+                opnds = [arrs[i]._arg(B.DFS_PRIV_R) if isinstance(i, int) else i for i in ins]
+                rt.submit(op, dom, opnds + [arrs[o]._arg(B.DFS_PRIV_W)])
+            outs[mode] = [a.numpy() for a in arrs]
+    for mode in MODES[1:]:
+        for s in range(nst):
+            assert np.array_equal(_bits(outs[mode][s]), _bits(outs["persistent"][s])), (mode, s)
+    got = outs["persistent"]
+    # ERF is odd bit for bit; the rewritten values are no longer negations
+    assert np.array_equal(_bits(got[10]), _bits(-got[5]))
+    assert not np.array_equal(np.abs(got[5]), np.abs(got[6]))
+    m = Machine("stored")
+    P = Tiling((tile,), (0,), IDENTITY, ((0,), (n,)))
+    init = {0: x, 4: z}
+    for s in range(nst):
+        m.add(s, init.get(s, np.zeros(n, dtype)))
+    for op, o, ins in stream:
+        m.run(XTask(op, dom, [Arg(i, P, "R") if isinstance(i, int) else Imm(i) for i in ins] + [Arg(o, P, "W")]))
+    fi = np.finfo(dtype)
+    for s in range(nst):
+        ok = np.isclose(got[s], m.arrays[s], rtol=(2e-6 if dtype == np.float32 else 1e-14), atol=4 * fi.eps)
+        assert ok.all(), s
 
 
 # ---------------------------------------------------- reductions, SpMV

@@ -3,7 +3,8 @@ Black-Scholes requests.
 
 Each request's result must be bit-identical alone and in the mix (the mix
 admits requests while others are mid-solve, so they share batched launches),
-and agree with the oracle.  Option prices: per option within 1e-5 (S + K).
+and agree with the oracle.  Option prices: per option within 4 eps32 (S + K) of
+the stored-dtype oracle.
 Solves: the oracle, run with the same convergence test (every 4
 iterations), stops within one test of the GPU (near convergence the updates
 are dominated by rounding, which the two paths do in different orders, and
@@ -67,7 +68,7 @@ def test_mix_equals_alone_and_oracle():
         if req["kind"] == "bs":
             S, K, T = inputs.serving_payload(req)
             c, p = programs.black_scholes(S, K, T, prm["r"], prm["sigma"], np.float32)
-            tol = 1e-5 * (S.astype(np.float64) + K)
+            tol = 4 * np.finfo(np.float32).eps * (S.astype(np.float64) + K)   # stored-dtype oracle
             assert np.all(np.abs(got.output[0] - c) <= tol) and np.all(np.abs(got.output[1] - p) <= tol)
             continue
         k, tol, m = got.iterations, 1e-8, req["size"]
@@ -154,7 +155,7 @@ def test_serving_full_size_requests():
     Poisson 64^3..256^3, options 2^16..2^24) in its launch configuration:
     every solve converged, its true residual ||b - A x|| (oracle SpMV) within
     1.5 tol ||b||; option prices on a sample of 4096 options per batch
-    within 1e-5 (S + K)."""
+    within 4 eps32 (S + K) of the stored-dtype oracle."""
     from paper_2406_18109_gb300 import configs
     cfg = configs.SERVING
     reqs = inputs.serving_requests(8, seed=cfg["seed"], mean_gap_s=cfg["mean_gap_ms"] * 1e-3)
@@ -171,7 +172,7 @@ def test_serving_full_size_requests():
             S, K, T = inputs.serving_payload(req)
             idx = np.sort(rng.choice(len(S), 4096, replace=False))
             c, p = programs.black_scholes(S[idx], K[idx], T[idx], prm["r"], prm["sigma"], np.float32)
-            tol = 1e-5 * (S[idx].astype(np.float64) + K[idx])
+            tol = 4 * np.finfo(np.float32).eps * (S[idx].astype(np.float64) + K[idx])   # stored-dtype oracle
             assert np.all(np.abs(r.output[0][idx] - c) <= tol) and np.all(np.abs(r.output[1][idx] - p) <= tol)
             continue
         assert r.converged and r.iterations % cfg["iters_per_tick"] == 0, req
