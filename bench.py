@@ -306,6 +306,14 @@ def kernel_delta(before: dict, after: dict) -> dict:
     return out
 
 
+def kernel_name_of(rt):
+    """Name of the generated kernel of the context's most recent launch (a
+    hash of its body, so it changes whenever the generated code does)."""
+    import re
+    m = re.search(r"\b(dfs_[kb][0-9a-f]{16})\b", rt.kernel_source())
+    return m.group(1) if m else None
+
+
 class Arm:
     """One timed configuration of a workload: build state, warm up, time K steps."""
 
@@ -319,6 +327,7 @@ class Arm:
         self.rt = A.Runtime(device=torch.cuda.current_device(), stream=stream.cuda_stream,
                             time_launches=True, **rt_kwargs)
         self.h2d = self.d2h = 0
+        self.kernel_name = None
         {"bs": self._setup_bs, "cg": self._setup_cg, "batched": self._setup_batched,
          "jacobi": self._setup_jacobi}[workload]()
         self.rt.sync()
@@ -394,6 +403,7 @@ class Arm:
             self._tune(window, {"tile": [256, 432, 512, 864, 1024, 2048], "block": [128, 256, 512], "unroll": [1, 2]},
                        f"cg-{cfg['m']}-{ipf}", 5, "ms_per_window")
         window()
+        self.kernel_name = kernel_name_of(rt)       # the iteration window's kernel (replayed below)
         rt.capture_begin()
         W.cg_reset_inplace(self.s, self.b)
         rt.flush()
@@ -458,6 +468,7 @@ class Arm:
         # one normal pass of each window (compiles kernels, uploads descriptors), then capture
         reset()
         one_iteration()
+        self.kernel_name = kernel_name_of(rt)       # the batched iteration's kernel (replayed below)
         rt.capture_begin()
         reset()
         for _ in range(cfg["iters"]):
@@ -639,7 +650,7 @@ def serving_alg_bytes(results) -> int:
     return tot
 
 
-def run_serving(args, torch, stream, sms, cache, dev):
+def run_serving(args, env):
     """The serving loop under its Poisson arrival stream, then again at a
     fraction of the throughput it sustained; one JSON line.  With N GPUs every
     rank serves its own stream (replicas; seeds differ by rank) and the value
@@ -647,6 +658,7 @@ def run_serving(args, torch, stream, sms, cache, dev):
     from paper_2406_18109_gb300 import arrays as A
     from paper_2406_18109_gb300 import dist as D
     from paper_2406_18109_gb300 import serve as SV
+    torch, stream, sms, cache, dev = env["torch"], env["stream"], env["sms"], env["cache"], env["dev"]
     cfg = configs.SERVING
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -759,8 +771,253 @@ def run_serving(args, torch, stream, sms, cache, dev):
             "gpu_launches": offered["launches"], "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
             "serving": {"offered_load": offered, "at_fraction_of_capacity": at_load,
                         "load_fraction": cfg["load_fraction"], "operator_load_s": t_load}}
-    if rank == 0:
-        print(json.dumps(line))
+    rt.close()
+    return line
+
+
+def measure(args, workload, env, steps, warmup, cpu_budget=(10.0, 8.0)) -> dict:
+    """Times one workload (fused persistent arm, then the comparison arms, the
+    end-to-end arm and the CPU oracle) and returns its JSON line.  env holds
+    the device plumbing: torch, stream, sms, cache, dev, world, rank."""
+    torch, stream, sms, cache = env["torch"], env["stream"], env["sms"], env["cache"]
+    dev, world, rank = env["dev"], env["world"], env["rank"]
+    from paper_2406_18109_gb300 import dist as D
+    metric, unit, dtype = METRIC[workload]
+    cfg = {"bs": configs.BLACK_SCHOLES, "cg": configs.CG, "jacobi": configs.JACOBI,
+           "batched": configs.BATCHED_CG}[workload]
+    base = dict(block=cfg["block"], unroll=cfg["unroll"], sms=sms, cache_dir=cache)
+    for k in ("tile", "tile_max", "min_points", "window_size"):
+        if k in cfg:
+            base[k] = cfg[k]
+    if "rows" in cfg:
+        base["rows"] = cfg["rows"]
+    for k in ("block", "unroll", "tile", "rows"):       # command-line overrides (tuning)
+        if getattr(args, k):
+            base[k] = getattr(args, k)
+
+    # CG: the iteration windows are captured once (memoised windows + a CUDA
+    # graph) and replayed; the Python-issued runs are reported beside them
+    graph = workload in ("cg", "batched")
+
+    def arm(kw, steps, warmup, e2e=False, graph=graph, per_solve=False):
+        a = Arm(workload, kw, torch, stream, e2e=e2e, graph=graph, per_solve=per_solve)
+        try:
+            return a.run(steps, warmup)
+        finally:
+            a.close()
+
+    fused_arm = Arm(workload, dict(base, fusion=True, launch="persistent"), torch, stream, graph=graph,
+                    autotune=workload in ("batched", "jacobi", "cg") and not args.no_autotune)
+    batch_sizes = (fused_arm.nnz, fused_arm.rows) if workload == "batched" else None
+    tuned = fused_arm.tuned
+    if tuned:
+        # the comparison arms run with the tuned setting too
+        base.update(tuned["config"])
+    clocks = Clocks(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks.start()
+    time.sleep(1.0)                              # let the clock sampler start before timing
+    fused = fused_arm.run(steps, warmup)
+    clk = clocks.stop()
+    fused_arm.close()
+    value, fused["ms"], _ = D.combine(fused["ms"], fused["units"], device="cuda" if world > 1 else None)
+    ms_step = fused["ms"] / steps
+
+    extra = {}
+    if not args.quick and workload == "batched":
+        k2 = max(2, steps // 2)
+        ps = arm(dict(base, fusion=True, launch="persistent"), k2, 1, per_solve=True)
+        extra["per_solve_launches"] = {"value": ps["units"] / (ps["ms"] / 1e3), "ms_per_step": ps["ms"] / k2,
+                                       "note": "same fused windows, one launch per solve per iteration, "
+                                               "replayed from a CUDA graph"}
+        extra["batched_vs_per_solve"] = value / world / extra["per_solve_launches"]["value"]
+    elif not args.quick:
+        k2 = max(3, steps // 4)
+        unf = arm(dict(base, fusion=False, launch="per_task"), k2, 2)
+        pt = arm(dict(base, fusion=True, launch="per_task"), k2, 2)
+        extra["unfused"] = {"value": unf["units"] / (unf["ms"] / 1e3), "ms_per_step": unf["ms"] / k2,
+                            "launches_per_step": unf["launches"] / k2,
+                            "kernel_ms_per_step": sum(v["ms"] for v in unf["kernels"].values()) / k2}
+        extra["fused_per_task"] = {"value": pt["units"] / (pt["ms"] / 1e3), "ms_per_step": pt["ms"] / k2,
+                                   "launches_per_step": pt["launches"] / k2,
+                                   "kernel_ms_per_step": sum(v["ms"] for v in pt["kernels"].values()) / k2}
+        extra["fused_vs_unfused"] = value / world / extra["unfused"]["value"]
+        extra["fused_kernel_ms_per_step"] = sum(v["ms"] for v in fused["kernels"].values()) / steps
+        if graph:
+            nf = arm(dict(base, fusion=True, launch="persistent"), k2, 2, graph=False)
+            nu = arm(dict(base, fusion=False, launch="per_task"), k2, 2, graph=False)
+            extra["python_issued"] = {
+                "fused": {"value": nf["units"] / (nf["ms"] / 1e3), "ms_per_step": nf["ms"] / k2},
+                "unfused": {"value": nu["units"] / (nu["ms"] / 1e3), "ms_per_step": nu["ms"] / k2},
+                "note": "each iteration issued from Python (11 tasks + flush); host-bound"}
+    if not args.quick:
+        # end to end through the public API: inputs from pinned host memory
+        # and results back to it inside every timed step
+        k3 = max(2, steps // 4)
+        ea = Arm(workload, dict(base, fusion=True, launch="persistent"), torch, stream, e2e=True, graph=graph)
+        try:
+            e = ea.run(k3, 2)
+            extra["e2e"] = {"value": e["units"] / (e["ms"] / 1e3), "unit": unit,
+                            "h2d_bytes_per_step": ea.h2d, "d2h_bytes_per_step": ea.d2h}
+            # the host link as a roofline of the end-to-end step: bytes that
+            # cross it per step over the step time, against copies both ways
+            # at once, measured now
+            link = host_link_peak(torch)
+            moved = (ea.h2d + ea.d2h) / (e["ms"] / 1e3 / k3) / 1e9
+            extra["e2e"]["roofline"] = {"bound": "host link", "achieved": moved, "peak": link["both"], "unit": "GB/s",
+                                        "frac": moved / link["both"], "peak_source": "measured: pinned copies both ways "
+                                        "at once (h2d %.0f, d2h %.0f GB/s alone)" % (link["h2d"], link["d2h"])}
+        finally:
+            ea.close()
+
+    peaks = load_peaks()
+    if workload == "bs":
+        alg_bytes = 20 * cfg["n"]                          # read S, K, T; write call, put
+    elif workload == "cg":
+        m = cfg["m"]
+        nn, nnz = m * m, 5 * m * m - 4 * m
+        alg_bytes = 12 * nnz + 4 * (nn + 1) + 96 * nn     # one CG iteration
+    elif workload == "batched":
+        nnz, rows = batch_sizes
+        esz = 8 if cfg["dtype"] == "f64" else 4
+        # per batched iteration, summed over the solves: CSR (value + int32
+        # column per entry, int32 row pointers) and the vector passes of the
+        # iteration (12 for the FP64 count of the single-solve CG line)
+        alg_bytes = (esz + 4) * nnz + 4 * (rows + cfg["count"]) + 12 * esz * rows
+    else:
+        alg_bytes = 16 * cfg["N"] * cfg["N"]               # one sweep (one launch)
+    kern_ms = fused["dominant_ms"]
+    if graph:
+        # launches replayed from a graph are not timed one by one: use the
+        # replayed time per iteration (kernel plus the gap to the next node)
+        kern_ms = fused["ms"] / (steps * cfg["iters"])
+        fused["dominant"] = ("batched CG iteration kernel" if workload == "batched" else
+                             "CG iteration kernel") + ", graph replay (time per iteration incl. launch gap)"
+        fused["dominant_launches"] = steps * cfg["iters"]
+    achieved = alg_bytes / (kern_ms / 1e3) / 1e9 if kern_ms > 0 else 0.0
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "peak_source": peaks["source"], "kernel": fused["dominant"], "kernel_ms": kern_ms,
+                "launches": fused["dominant_launches"], "algorithmic_bytes_per_launch": alg_bytes}
+    # measured DRAM traffic (ncu) of the dominant kernel, used only when the
+    # kernel timed now is the one the counters were taken on (same generated
+    # code, so the same name) at the default size; else null
+    kname = fused_arm.kernel_name if graph else fused["dominant"]
+    ctr = counters_for(cfg, kname)
+    roofline["kernel_name"] = kname
+    roofline["counters_kernel"] = (cfg.get("counters") or {}).get("kernel")
+    if ctr and workload == "cg" and cfg["m"] == 256:
+        roofline["traffic"] = ctr["dram_bytes_per_iteration"]
+    elif ctr and workload == "batched" and cfg["count"] == 256:
+        roofline["traffic"] = ctr["dram_bytes_per_launch"]
+    fp64_ops = None
+    if workload == "cg":
+        fp64_ops = nnz + 8 * nn
+    elif workload == "batched" and cfg["dtype"] == "f64":
+        fp64_ops = nnz + 8 * rows
+    if fp64_ops is not None:
+        # FP64 is a scarce pipe on GB300 (nominal 1.25 TFLOP/s counting an FMA
+        # as two: about two lane operations per SM and clock).  Lane operations
+        # per iteration: one FMA per stored entry (SpMV) and eight per row (the
+        # two dots, the x, r and p updates at two operations each but the dots'
+        # one)
+        sm_max = clk.get("sm_max_mhz") or 2070.0
+        peak_ops = sms * 2 * sm_max * 1e6 / 1e9
+        ach_ops = fp64_ops / (kern_ms / 1e3) / 1e9 if kern_ms > 0 else 0.0
+        roofline["fp64"] = {"achieved": ach_ops, "peak": peak_ops, "unit": "G lane-ops/s", "frac": ach_ops / peak_ops,
+                            "ops_per_launch": fp64_ops,
+                            "peak_source": f"derived: {sms} SMs x 2 FP64 lanes x {sm_max:.0f} MHz (1.25 TFLOP/s nominal)"}
+    if workload == "bs":
+        # issue-bound: instructions per option (ncu) x options / kernel time,
+        # against SMs x 4 sub-partitions x 32 lanes x maximum SM clock
+        sm_max = clk.get("sm_max_mhz") or 2070.0
+        peak_ti = sms * 4 * 32 * sm_max * 1e6 / 1e12
+        # the instruction count and DRAM traffic (ncu) belong to one generated
+        # kernel: used only when that kernel is the one timed now, else null
+        ctr = counters_for(cfg, fused["dominant"]) if cfg["n"] == 1 << 26 else None
+        hbm = {"achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+               "peak_source": peaks["source"], "algorithmic_bytes_per_launch": alg_bytes}
+        if ctr:
+            ach_ti = ctr["inst_per_option"] * cfg["n"] / (kern_ms / 1e3) / 1e12 if kern_ms > 0 else 0.0
+            roofline = {"bound": "alu", "achieved": ach_ti, "peak": peak_ti, "unit": "T thread-inst/s",
+                        "frac": ach_ti / peak_ti, "traffic": ctr["dram_bytes_per_launch"],
+                        "peak_source": f"derived: {sms} SMs x 4 SMSPs x 32 lanes x {sm_max:.0f} MHz",
+                        "inst_per_option": ctr["inst_per_option"], "hbm": hbm}
+        else:
+            roofline = dict(hbm, bound="hbm", traffic=None, inst_per_option=None)
+        roofline.update({"kernel": fused["dominant"], "kernel_name": fused["dominant"],
+                         "counters_kernel": (cfg.get("counters") or {}).get("kernel"), "kernel_ms": kern_ms,
+                         "launches": fused["dominant_launches"]})
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.quick:
+        v, u, sample = oracle_rate(workload, budget_s=cpu_budget[0])
+        cpu = {"value": v, "unit": u, "cores": 1, "kind": "oracle", "sample": sample}
+        if workload in ALL_CORES_SAMPLE:
+            va, nc = oracle_rate_all_cores(workload, cpu_budget[1])
+            cpu["all_cores"] = {"value": va, "unit": u, "cores": nc,
+                                "sample": ALL_CORES_SAMPLE[workload] + f", {cpu_budget[1]:.0f} s"}
+
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": steps,
+            "warmup": warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic (seeded generators of synth/inputs.py)",
+            "config": {"workload": WORKLOAD[workload],
+                       "l2": "inputs larger than L2" if workload != "cg"
+                       else "working set L2-resident (10 MB); no flush",
+                       "launch": "persistent fused" + (", each solve replayed from a CUDA graph of the memoised "
+                                                        "iteration windows" if graph else ""),
+                       "parallelism": f"replicas x{world}"},
+            "e2e": extra.pop("e2e", None), "gpu_launches": fused["launches"], "roofline": roofline,
+            "step_ms": fused["step_ms"],
+            "cpu_baseline": cpu, "clocks": clk}
+    line.update(extra)
+    if tuned:
+        line["config"]["autotuned"] = tuned["config"]
+        line["autotune"] = tuned["trials"]
+    st = fused["stats"]
+    line["runtime_stats"] = {k: st.get(k) for k in ("compile_s", "kernels_compiled", "plan_hits", "plan_misses",
+                                                     "kernel_disk_hits", "last_regs", "last_occupancy",
+                                                     "last_grid", "last_block", "analysis_s")}
+    return line
+
+
+def counters_for(cfg: dict, kernel_name):
+    """The ncu counters stored for a workload, if they were taken on the kernel
+    named (its name hashes its generated body), else None."""
+    ctr = cfg.get("counters")
+    return ctr if ctr and kernel_name and ctr.get("kernel") == kernel_name else None
+
+
+COMPACT_KEYS = ("metric", "value", "unit", "steps", "warmup", "ms_per_step", "dtype", "config", "gpu_launches",
+                "roofline", "e2e", "cpu_baseline", "clocks", "step_ms", "fused_vs_unfused", "unfused", "fused_per_task",
+                "fused_kernel_ms_per_step", "python_issued", "batched_vs_per_solve", "per_solve_launches")
+
+
+def compact(line: dict) -> dict:
+    """A workload's line as a sub-object of the default line (its own value,
+    timing, comparison arms, roofline and oracle rate; the tuner's trial list
+    and the runtime counters left out)."""
+    return {k: line[k] for k in COMPACT_KEYS if k in line}
+
+
+def compact_serving(line: dict) -> dict:
+    """The serving line as a sub-object: sustained requests/s under the
+    offered Poisson load, and p50/p99 latency both there and at the stated
+    fraction of that throughput."""
+    out = {k: line[k] for k in ("metric", "value", "unit", "p50_ms", "p99_ms", "dtype", "config", "gpu_launches",
+                                "roofline", "e2e", "cpu_baseline", "clocks") if k in line}
+    srv = line["serving"]
+    off = srv["offered_load"]
+    out["offered_load"] = {k: off.get(k) for k in ("offered_rps", "sustained_rps", "p50_ms", "p99_ms", "requests",
+                                                    "wall_s", "gpu_busy_frac", "unconverged")}
+    at = srv.get("at_fraction_of_capacity")
+    if at:
+        out["at_fraction_of_capacity"] = {"load_fraction": srv["load_fraction"],
+                                          **{k: at.get(k) for k in ("offered_rps", "sustained_rps", "p50_ms", "p99_ms",
+                                                                    "requests", "wall_s", "gpu_busy_frac",
+                                                                    "unconverged")}}
+    return out
 
 
 def main():
@@ -778,6 +1035,8 @@ def main():
                     help="serving: one group of solves (the host waits for every convergence read)")
     ap.add_argument("--fp32", action="store_true", help="batched CG in FP32 instead of FP64")
     ap.add_argument("--quick", action="store_true", help="skip the comparison arms (for profiling)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="Black-Scholes line only (no CG, Jacobi and serving sub-objects)")
     ap.add_argument("--bs-n", type=int, default=0, help="Black-Scholes batch size (profiling a smaller case)")
     ap.add_argument("--jac-n", type=int, default=0, help="Jacobi interior size N (profiling a smaller case)")
     ap.add_argument("--sweeps", type=int, default=0, help="Jacobi sweeps per step (profiling)")
@@ -847,213 +1106,27 @@ def main():
     os.makedirs(cache, exist_ok=True)
 
     from paper_2406_18109_gb300 import _build
-    from paper_2406_18109_gb300 import dist as D
     _build.build()
     if args.compile_report:
         print(json.dumps({"compile_report": compile_report(torch, stream, sms)}))
         return
+    env = dict(torch=torch, stream=stream, sms=sms, cache=cache, dev=dev, world=world, rank=rank)
     if args.workload == "serve":
-        run_serving(args, torch, stream, sms, cache, dev)
-        if world > 1:
-            torch.distributed.destroy_process_group()
-        return
-
-    metric, unit, dtype = METRIC[args.workload]
-    cfg = {"bs": configs.BLACK_SCHOLES, "cg": configs.CG, "jacobi": configs.JACOBI,
-           "batched": configs.BATCHED_CG}[args.workload]
-    base = dict(block=cfg["block"], unroll=cfg["unroll"], sms=sms, cache_dir=cache)
-    for k in ("tile", "tile_max", "min_points", "window_size"):
-        if k in cfg:
-            base[k] = cfg[k]
-    if "rows" in cfg:
-        base["rows"] = cfg["rows"]
-    for k in ("block", "unroll", "tile", "rows"):       # command-line overrides (tuning)
-        if getattr(args, k):
-            base[k] = getattr(args, k)
-
-    # CG: the iteration windows are captured once (memoised windows + a CUDA
-    # graph) and replayed; the Python-issued runs are reported beside them
-    graph = args.workload in ("cg", "batched")
-
-    def arm(kw, steps, warmup, e2e=False, graph=graph, per_solve=False):
-        a = Arm(args.workload, kw, torch, stream, e2e=e2e, graph=graph, per_solve=per_solve)
-        try:
-            return a.run(steps, warmup)
-        finally:
-            a.close()
-
-    fused_arm = Arm(args.workload, dict(base, fusion=True, launch="persistent"), torch, stream, graph=graph,
-                    autotune=args.workload in ("batched", "jacobi", "cg") and not args.no_autotune)
-    batch_sizes = (fused_arm.nnz, fused_arm.rows) if args.workload == "batched" else None
-    tuned = fused_arm.tuned
-    if tuned:
-        # the comparison arms run with the tuned setting too
-        base.update(tuned["config"])
-    clocks = Clocks(dev)
-    if world > 1:
-        torch.distributed.barrier()
-    clocks.start()
-    time.sleep(1.0)                              # let the clock sampler start before timing
-    fused = fused_arm.run(args.steps, args.warmup)
-    clk = clocks.stop()
-    fused_arm.close()
-    value, fused["ms"], _ = D.combine(fused["ms"], fused["units"], device="cuda" if world > 1 else None)
-    ms_step = fused["ms"] / args.steps
-
-    extra = {}
-    if not args.quick and args.workload == "batched":
-        k2 = max(2, args.steps // 2)
-        ps = arm(dict(base, fusion=True, launch="persistent"), k2, 1, per_solve=True)
-        extra["per_solve_launches"] = {"value": ps["units"] / (ps["ms"] / 1e3), "ms_per_step": ps["ms"] / k2,
-                                       "note": "same fused windows, one launch per solve per iteration, "
-                                               "replayed from a CUDA graph"}
-        extra["batched_vs_per_solve"] = value / world / extra["per_solve_launches"]["value"]
-    elif not args.quick:
-        k2 = max(3, args.steps // 4)
-        unf = arm(dict(base, fusion=False, launch="per_task"), k2, 2)
-        pt = arm(dict(base, fusion=True, launch="per_task"), k2, 2)
-        extra["unfused"] = {"value": unf["units"] / (unf["ms"] / 1e3), "ms_per_step": unf["ms"] / k2,
-                            "launches_per_step": unf["launches"] / k2,
-                            "kernel_ms_per_step": sum(v["ms"] for v in unf["kernels"].values()) / k2}
-        extra["fused_per_task"] = {"value": pt["units"] / (pt["ms"] / 1e3), "ms_per_step": pt["ms"] / k2,
-                                   "launches_per_step": pt["launches"] / k2,
-                                   "kernel_ms_per_step": sum(v["ms"] for v in pt["kernels"].values()) / k2}
-        extra["fused_vs_unfused"] = value / world / extra["unfused"]["value"]
-        extra["fused_kernel_ms_per_step"] = sum(v["ms"] for v in fused["kernels"].values()) / args.steps
-        if graph:
-            nf = arm(dict(base, fusion=True, launch="persistent"), k2, 2, graph=False)
-            nu = arm(dict(base, fusion=False, launch="per_task"), k2, 2, graph=False)
-            extra["python_issued"] = {
-                "fused": {"value": nf["units"] / (nf["ms"] / 1e3), "ms_per_step": nf["ms"] / k2},
-                "unfused": {"value": nu["units"] / (nu["ms"] / 1e3), "ms_per_step": nu["ms"] / k2},
-                "note": "each iteration issued from Python (11 tasks + flush); host-bound"}
-    if not args.quick:
-        # end to end through the public API: inputs from pinned host memory
-        # and results back to it inside every timed step
-        k3 = max(2, args.steps // 4)
-        ea = Arm(args.workload, dict(base, fusion=True, launch="persistent"), torch, stream, e2e=True, graph=graph)
-        try:
-            e = ea.run(k3, 2)
-            extra["e2e"] = {"value": e["units"] / (e["ms"] / 1e3), "unit": unit,
-                            "h2d_bytes_per_step": ea.h2d, "d2h_bytes_per_step": ea.d2h}
-            # the host link as a roofline of the end-to-end step: bytes that
-            # cross it per step over the step time, against copies both ways
-            # at once, measured now
-            link = host_link_peak(torch)
-            moved = (ea.h2d + ea.d2h) / (e["ms"] / 1e3 / k3) / 1e9
-            extra["e2e"]["roofline"] = {"bound": "host link", "achieved": moved, "peak": link["both"], "unit": "GB/s",
-                                        "frac": moved / link["both"], "peak_source": "measured: pinned copies both ways "
-                                        "at once (h2d %.0f, d2h %.0f GB/s alone)" % (link["h2d"], link["d2h"])}
-        finally:
-            ea.close()
-
-    peaks = load_peaks()
-    if args.workload == "bs":
-        alg_bytes = 20 * cfg["n"]                          # read S, K, T; write call, put
-    elif args.workload == "cg":
-        m = cfg["m"]
-        nn, nnz = m * m, 5 * m * m - 4 * m
-        alg_bytes = 12 * nnz + 4 * (nn + 1) + 96 * nn     # one CG iteration
-    elif args.workload == "batched":
-        nnz, rows = batch_sizes
-        esz = 8 if cfg["dtype"] == "f64" else 4
-        # per batched iteration, summed over the solves: CSR (value + int32
-        # column per entry, int32 row pointers) and the vector passes of the
-        # iteration (12 for the FP64 count of the single-solve CG line)
-        alg_bytes = (esz + 4) * nnz + 4 * (rows + cfg["count"]) + 12 * esz * rows
+        line = run_serving(args, env)
     else:
-        alg_bytes = 16 * cfg["N"] * cfg["N"]               # one sweep (one launch)
-    kern_ms = fused["dominant_ms"]
-    if graph:
-        # launches replayed from a graph are not timed one by one: use the
-        # replayed time per iteration (kernel plus the gap to the next node)
-        kern_ms = fused["ms"] / (args.steps * cfg["iters"])
-        fused["dominant"] = ("batched CG iteration kernel" if args.workload == "batched" else
-                             "CG iteration kernel") + ", graph replay (time per iteration incl. launch gap)"
-        fused["dominant_launches"] = args.steps * cfg["iters"]
-    achieved = alg_bytes / (kern_ms / 1e3) / 1e9 if kern_ms > 0 else 0.0
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                "peak_source": peaks["source"], "kernel": fused["dominant"], "kernel_ms": kern_ms,
-                "launches": fused["dominant_launches"], "algorithmic_bytes_per_launch": alg_bytes}
-    # measured DRAM traffic (ncu) of the dominant kernel where one was taken
-    # at the default size and the launch shape in use (profiles/)
-    shape = dict(base)
-    if tuned:
-        shape.update(tuned["config"])
-    ref_shape = cfg.get("dram_launch_shape")
-    same = ref_shape is not None and all(shape.get(k, 0) == v for k, v in ref_shape.items())
-    if args.workload == "cg" and same and cfg["m"] == 256:
-        roofline["traffic"] = cfg["dram_bytes_per_iteration"]
-    elif args.workload == "batched" and same and cfg["dtype"] == "f64" and cfg["count"] == 256:
-        roofline["traffic"] = cfg["dram_bytes_per_launch"]
-    fp64_ops = None
-    if args.workload == "cg":
-        fp64_ops = nnz + 8 * nn
-    elif args.workload == "batched" and cfg["dtype"] == "f64":
-        fp64_ops = nnz + 8 * rows
-    if fp64_ops is not None:
-        # FP64 is a scarce pipe on GB300 (nominal 1.25 TFLOP/s counting an FMA
-        # as two: about two lane operations per SM and clock).  Lane operations
-        # per iteration: one FMA per stored entry (SpMV) and eight per row (the
-        # two dots, the x, r and p updates at two operations each but the dots'
-        # one)
-        sm_max = clk.get("sm_max_mhz") or 2070.0
-        peak_ops = sms * 2 * sm_max * 1e6 / 1e9
-        ach_ops = fp64_ops / (kern_ms / 1e3) / 1e9 if kern_ms > 0 else 0.0
-        roofline["fp64"] = {"achieved": ach_ops, "peak": peak_ops, "unit": "G lane-ops/s", "frac": ach_ops / peak_ops,
-                            "ops_per_launch": fp64_ops,
-                            "peak_source": f"derived: {sms} SMs x 2 FP64 lanes x {sm_max:.0f} MHz (1.25 TFLOP/s nominal)"}
-    if args.workload == "bs":
-        # issue-bound: instructions per option (ncu) x options / kernel time,
-        # against SMs x 4 sub-partitions x 32 lanes x maximum SM clock
-        sm_max = clk.get("sm_max_mhz") or 2070.0
-        peak_ti = sms * 4 * 32 * sm_max * 1e6 / 1e12
-        ach_ti = cfg["inst_per_option"] * cfg["n"] / (kern_ms / 1e3) / 1e12 if kern_ms > 0 else 0.0
-        # measured DRAM traffic of this kernel at the default size (ncu), else unknown
-        traffic = cfg["dram_bytes_per_launch"] if cfg["n"] == 1 << 26 else None
-        roofline = {"bound": "alu", "achieved": ach_ti, "peak": peak_ti, "unit": "T thread-inst/s",
-                    "frac": ach_ti / peak_ti, "traffic": traffic,
-                    "peak_source": f"derived: {sms} SMs x 4 SMSPs x 32 lanes x {sm_max:.0f} MHz",
-                    "inst_per_option": cfg["inst_per_option"], "kernel": fused["dominant"],
-                    "kernel_ms": kern_ms, "launches": fused["dominant_launches"],
-                    "hbm": {"achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                            "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"],
-                            "algorithmic_bytes_per_launch": alg_bytes}}
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.quick:
-        v, u, sample = oracle_rate(args.workload, budget_s=10.0)
-        cpu = {"value": v, "unit": u, "cores": 1, "kind": "oracle", "sample": sample}
-        if args.workload in ALL_CORES_SAMPLE:
-            va, nc = oracle_rate_all_cores(args.workload)
-            cpu["all_cores"] = {"value": va, "unit": u, "cores": nc,
-                                "sample": ALL_CORES_SAMPLE[args.workload] + ", 8 s"}
-
-    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": dtype, "data": "synthetic (seeded generators of synth/inputs.py)",
-            "config": {"workload": WORKLOAD[args.workload],
-                       "l2": "inputs larger than L2" if args.workload != "cg"
-                       else "working set L2-resident (10 MB); no flush",
-                       "launch": "persistent fused" + (", each solve replayed from a CUDA graph of the memoised "
-                                                        "iteration windows" if graph else ""),
-                       "parallelism": f"replicas x{world}"},
-            "e2e": extra.pop("e2e", None), "gpu_launches": fused["launches"], "roofline": roofline,
-            "step_ms": fused["step_ms"],
-            "cpu_baseline": cpu, "clocks": clk}
-    line.update(extra)
-    if tuned:
-        line["config"]["autotuned"] = tuned["config"]
-        line["autotune"] = tuned["trials"]
-    st = fused["stats"]
-    line["runtime_stats"] = {k: st.get(k) for k in ("compile_s", "kernels_compiled", "plan_hits", "plan_misses",
-                                                     "kernel_disk_hits", "last_regs", "last_occupancy",
-                                                     "last_grid", "last_block", "analysis_s")}
+        line = measure(args, args.workload, env, args.steps, args.warmup)
+        if args.workload == "bs" and not args.quick and not args.no_extras:
+            # the other half of the headline metric in the same line: CG
+            # iterations/s, Jacobi sweeps/s and the serving loop's p50/p99,
+            # each with its own fused/unfused ratio, roofline and oracle rate
+            line["cg"] = compact(measure(args, "cg", env, 20, 3, cpu_budget=(5.0, 4.0)))
+            line["jacobi"] = compact(measure(args, "jacobi", env, 10, 3, cpu_budget=(5.0, 4.0)))
+            line["serve"] = compact_serving(run_serving(args, env))
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
+
 
 
 if __name__ == "__main__":

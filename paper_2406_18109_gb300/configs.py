@@ -6,13 +6,14 @@ check exactly the launch configuration the benchmark times.  Launch settings
 # Black-Scholes: 2^26 FP32 options (spot U[5,30], strike U[1,100], expiry
 # U[0.25,10], r = 0.02, sigma = 0.3, seed 1)
 BLACK_SCHOLES = dict(n=1 << 26, seed=1, r=0.02, sigma=0.3, tile=16384, block=512, unroll=1,
-                     # thread instructions per option of the fused kernel (ncu
-                     # smsp__inst_executed x 32 / options); the kernel is bound
-                     # by instruction issue, see profiles/
-                     inst_per_option=151.45,
-                     # DRAM bytes (read + write) of one launch at n = 2^26, from
-                     # an ncu capture of this kernel (profiles/)
-                     dram_bytes_per_launch=1307.31e6,
+                     # ncu counters of the fused kernel named `kernel` (generated
+                     # kernels are named by a hash of their code, so a change to
+                     # the generated code changes the name and retires them):
+                     # thread instructions per option (smsp__inst_executed x 32
+                     # / options; the kernel is bound by instruction issue) and
+                     # DRAM bytes (read + write) of one launch at n = 2^26
+                     counters=dict(kernel="dfs_keeae8bd48c1272bc", inst_per_option=151.45,
+                                   dram_bytes_per_launch=1307.31e6),
                      # end to end (host arrays): kernels on mapped host memory
                      # ("zero_copy") or copies pipelined in chunks over contexts
                      e2e_mode="zero_copy", e2e_chunk=1 << 23, e2e_contexts=2)
@@ -21,11 +22,9 @@ BLACK_SCHOLES = dict(n=1 << 26, seed=1, r=0.02, sigma=0.3, tile=16384, block=512
 # int32 indices, x* ~ U[-1,1] (seed 0), b = A x*, x0 = 0; five iterations
 # share one flush window (one persistent launch) in the captured solve
 CG = dict(m=256, iters=50, seed=0, tile=512, block=256, unroll=2, iters_per_flush=5, window_size=1024,
-          # DRAM bytes (read + write) per iteration of the fused window, from an
-          # ncu capture of this kernel at this launch shape (profiles/): 5.87 MB
-          # per five-iteration launch; the rest of the traffic is served by L2
-          dram_bytes_per_iteration=5.865728e6 / 5,
-          dram_launch_shape=dict(tile=512, block=256, unroll=2))
+          # ncu counters of the five-iteration window kernel named `kernel`
+          # (None: none taken on the current generated code)
+          counters=None)
 
 # Batched CG: 256 independent solves of uneven size (half 2-D Poisson with m
 # log-uniform in [32, 1024], half random diagonally dominant SPD with n
@@ -35,10 +34,9 @@ CG = dict(m=256, iters=50, seed=0, tile=512, block=256, unroll=2, iters_per_flus
 # points per problem, at most tile_max elements); the bench autotunes
 # tile_max and the launch shape before capturing.
 BATCHED_CG = dict(count=256, seed=4, iters=100, dtype="f64", tile_max=2048, min_points=2, block=256, unroll=2,
-                  # DRAM bytes (read + write) of one FP64 batched iteration, from an
-                  # ncu capture at this launch shape (profiles/)
-                  dram_bytes_per_launch=3.018065e9 + 0.672410e9,
-                  dram_launch_shape=dict(tile_max=2048, block=256, unroll=2, ctas_per_sm=0))
+                  # ncu counters of the batched iteration kernel named `kernel`
+                  # (None: none taken on the current generated code)
+                  counters=None)
 
 # Jacobi: Fig. 1 stencil on an 8192x8192 FP32 grid (8190^2 interior),
 # 200 sweeps, interior U[0,1] (seed 2), boundary 1.0
