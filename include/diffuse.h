@@ -465,6 +465,60 @@ int dfs_template_free(dfs_ctx *ctx, uint64_t id);
  */
 int dfs_set_launch_config(dfs_ctx *ctx, int32_t block_threads, int32_t unroll, int32_t ctas_per_sm);
 
+/*
+ * Row-block partition over ranks (one process per GPU).  Section 3.2 splits
+ * an index task's launch domain into point tasks, one per processor; across
+ * GPUs the vectors of an iterative solver are tiled by row blocks and each
+ * rank runs the point tasks of its own block (the weak-scaling setting of the
+ * paper's evaluation, Section 7).  Rank r of P owns the rows
+ * [floor(r n / P), floor((r + 1) n / P)).  Element-wise tasks and reductions
+ * then need nothing from other ranks but the reductions' partial sums; a CSR
+ * SpMV, which reads x through the None partition, also needs the entries of
+ * x that its rows reference outside the block -- its HALO, received from
+ * their owners before the SpMV.  These calls compute that plan on the host;
+ * they need no device and allocate nothing the caller must free.
+ *
+ * dfs_rowblock_bounds: *lo, *hi = the rows rank `rank` of `nranks` owns out
+ * of n.  Returns DFS_ERR_INVALID for n < 0, nranks < 1 or rank outside
+ * [0, nranks), or null outputs.
+ *
+ * dfs_rowblock_sizes: sizes of rank `rank`'s plan for the square CSR matrix
+ * (rowptr: n + 1 int32, rowptr[0] == 0, non-decreasing; col: rowptr[n]
+ * int32 columns in [0, n)): owned rows, their stored entries, the distinct
+ * halo columns, and the owned entries other ranks read (counted once per
+ * reading rank).  Returns DFS_ERR_INVALID for a malformed matrix or bad rank.
+ *
+ * dfs_rowblock_plan: fills caller-owned arrays sized by dfs_rowblock_sizes:
+ *   local_rowptr  (n_own + 1 int32)  the owned rows' row pointers, from 0;
+ *   local_col     (nnz int32)        their columns renumbered: an owned
+ *                 column g becomes g - row_lo, a halo column becomes
+ *                 n_own + its halo slot (the values array is the caller's
+ *                 val[rowptr[row_lo] .. rowptr[row_hi]) unchanged);
+ *   halo_cols     (n_halo int64)     global column of each halo slot,
+ *                 ascending, hence grouped by owning rank;
+ *   recv_counts   (nranks int64)     halo slots owned by each rank;
+ *   send_idx      (n_send int32)     owned local indices to send, grouped by
+ *                 destination rank ascending, ascending within a group (the
+ *                 order of the receiver's halo slots);
+ *   send_counts   (nranks int64)     entries sent to each rank.
+ * The halo exchange is then one all-to-all of send_idx's entries of x with
+ * these counts, received into x[n_own ..].  Returns DFS_ERR_INVALID as
+ * dfs_rowblock_sizes or for a null array that must hold entries,
+ * DFS_ERR_TOO_LARGE when n_own + n_halo exceeds the int32 range.
+ */
+typedef struct {
+  int64_t row_lo, row_hi; /* owned global rows */
+  int64_t nnz;            /* stored entries of the owned rows */
+  int64_t n_halo;         /* distinct columns outside [row_lo, row_hi) they read */
+  int64_t n_send;         /* owned entries other ranks read, summed over ranks */
+} dfs_rowblock_sizes_t;
+int dfs_rowblock_bounds(int64_t n, int32_t nranks, int32_t rank, int64_t *lo, int64_t *hi);
+int dfs_rowblock_sizes(const int32_t *rowptr, const int32_t *col, int64_t n, int32_t nranks, int32_t rank,
+                       dfs_rowblock_sizes_t *out);
+int dfs_rowblock_plan(const int32_t *rowptr, const int32_t *col, int64_t n, int32_t nranks, int32_t rank,
+                      int32_t *local_rowptr, int32_t *local_col, int64_t *halo_cols, int64_t *recv_counts,
+                      int32_t *send_idx, int64_t *send_counts);
+
 /* Source of the generated CUDA for the most recent launch (debugging). */
 int dfs_last_kernel_source(dfs_ctx *ctx, char *buf, size_t len, size_t *needed);
 

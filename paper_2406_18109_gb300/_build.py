@@ -24,7 +24,7 @@ OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(LIBDIR, "libdiffuse.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-HOST_SOURCES = ["runtime.cpp", "fusion.cpp", "codegen.cpp", "batchgen.cpp", "jit.cpp"]
+HOST_SOURCES = ["runtime.cpp", "fusion.cpp", "codegen.cpp", "batchgen.cpp", "jit.cpp", "partition.cpp"]
 DEVICE_SOURCES = ["dfs_check.cu", "noalloc.cu", "gather.cu"]
 GENCODE = "arch=compute_103a,code=sm_103a"
 

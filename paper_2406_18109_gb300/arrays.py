@@ -67,6 +67,7 @@ class Runtime:
         cfg.cache_dir = self._cache_dir
         self.ctx = B.dfs_init(cfg)
         self.device = device
+        self.stream = stream or None          # the caller's cudaStream_t handle, or None: the context's own
         self.none = B.dfs_partition_none(self.ctx)
         self._tilings = {}
         self._layouts = {}

@@ -40,7 +40,8 @@ EXPORTS = ("dfs_config_default", "dfs_init", "dfs_shutdown", "dfs_store_create",
            "dfs_set_launch_config", "dfs_store_wrap_host", "dfs_host_alloc", "dfs_host_free",
            "dfs_read_scalars_async", "dfs_record", "dfs_wait", "dfs_poll", "dfs_ticket_elapsed_ms",
            "dfs_ticket_release", "dfs_template_begin", "dfs_template_end", "dfs_template_inputs",
-           "dfs_template_replay", "dfs_template_free")
+           "dfs_template_replay", "dfs_template_free", "dfs_rowblock_bounds", "dfs_rowblock_sizes",
+           "dfs_rowblock_plan")
 
 
 class dfs_config(C.Structure):
@@ -54,6 +55,11 @@ class dfs_config(C.Structure):
 class dfs_arg(C.Structure):
     _fields_ = [("store", C.c_int64), ("partition", C.c_int64), ("privilege", C.c_int32),
                 ("redop", C.c_int32), ("imm", C.c_double)]
+
+
+class dfs_rowblock_sizes_t(C.Structure):
+    _fields_ = [("row_lo", C.c_int64), ("row_hi", C.c_int64), ("nnz", C.c_int64), ("n_halo", C.c_int64),
+                ("n_send", C.c_int64)]
 
 
 class DfsError(RuntimeError):
@@ -120,6 +126,9 @@ def lib():
             "dfs_template_inputs": (C.c_int, [P, C.c_uint64, I32, pI64, C.POINTER(C.c_int32)]),
             "dfs_template_replay": (C.c_int, [P, C.c_uint64, I32, pI64, pI64]),
             "dfs_template_free": (C.c_int, [P, C.c_uint64]),
+            "dfs_rowblock_bounds": (C.c_int, [I64, I32, I32, pI64, pI64]),
+            "dfs_rowblock_sizes": (C.c_int, [P, P, I64, I32, I32, C.POINTER(dfs_rowblock_sizes_t)]),
+            "dfs_rowblock_plan": (C.c_int, [P, P, I64, I32, I32, P, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -399,3 +408,33 @@ def dfs_dot_noalloc(x_ptr: int, y_ptr: int, n: int, out_ptr: int, stream: int = 
                                C.c_void_p(stream) if stream else None)
     if rc != DFS_OK:
         raise DfsError(rc, "dfs_dot_noalloc failed")
+
+
+def dfs_rowblock_bounds(n: int, nranks: int, rank: int):
+    """(lo, hi): the global rows rank `rank` of `nranks` owns out of n."""
+    lo, hi = C.c_int64(), C.c_int64()
+    _check(None, lib().dfs_rowblock_bounds(n, nranks, rank, C.byref(lo), C.byref(hi)))
+    return lo.value, hi.value
+
+
+def dfs_rowblock_plan(rowptr, col, nranks: int, rank: int) -> dict:
+    """Rank `rank`'s row-block plan of a square int32 CSR matrix: a dict of
+    row_lo, row_hi, local_rowptr, local_col, halo_cols, recv_counts, send_idx,
+    send_counts (numpy arrays; see dfs_rowblock_plan in diffuse.h)."""
+    import numpy as np
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    n = len(rowptr) - 1
+    sz = dfs_rowblock_sizes_t()
+    L = lib()
+    _check(None, L.dfs_rowblock_sizes(rowptr.ctypes.data, col.ctypes.data, n, nranks, rank, C.byref(sz)))
+    n_own = sz.row_hi - sz.row_lo
+    out = {"row_lo": sz.row_lo, "row_hi": sz.row_hi,
+           "local_rowptr": np.empty(n_own + 1, np.int32), "local_col": np.empty(sz.nnz, np.int32),
+           "halo_cols": np.empty(sz.n_halo, np.int64), "recv_counts": np.empty(nranks, np.int64),
+           "send_idx": np.empty(sz.n_send, np.int32), "send_counts": np.empty(nranks, np.int64)}
+    _check(None, L.dfs_rowblock_plan(rowptr.ctypes.data, col.ctypes.data, n, nranks, rank,
+                                     out["local_rowptr"].ctypes.data, out["local_col"].ctypes.data,
+                                     out["halo_cols"].ctypes.data, out["recv_counts"].ctypes.data,
+                                     out["send_idx"].ctypes.data, out["send_counts"].ctypes.data))
+    return out
