@@ -403,6 +403,7 @@ class Arm:
             self._tune(window, {"tile": [256, 432, 512, 864, 1024, 2048], "block": [128, 256, 512], "unroll": [1, 2]},
                        f"cg-{cfg['m']}-{ipf}", 5, "ms_per_window")
         window()
+        window()                                    # a steady window (the first also holds the start tasks)
         self.kernel_name = kernel_name_of(rt)       # the iteration window's kernel (replayed below)
         rt.capture_begin()
         W.cg_reset_inplace(self.s, self.b)
@@ -794,6 +795,10 @@ def measure(args, workload, env, steps, warmup, cpu_budget=(10.0, 8.0)) -> dict:
     for k in ("block", "unroll", "tile", "rows"):       # command-line overrides (tuning)
         if getattr(args, k):
             base[k] = getattr(args, k)
+    if "stage_x" in cfg:
+        base["stage_x"] = cfg["stage_x"]
+    if args.stage_x:
+        base["stage_x"] = args.stage_x == "on"
 
     # CG: the iteration windows are captured once (memoised windows + a CUDA
     # graph) and replayed; the Python-issued runs are reported beside them
@@ -906,7 +911,7 @@ def measure(args, workload, env, steps, warmup, cpu_budget=(10.0, 8.0)) -> dict:
     kname = fused_arm.kernel_name if graph else fused["dominant"]
     ctr = counters_for(cfg, kname)
     roofline["kernel_name"] = kname
-    roofline["counters_kernel"] = (cfg.get("counters") or {}).get("kernel")
+    roofline["counters_kernel"] = counters_kernels(cfg)
     if ctr and workload == "cg" and cfg["m"] == 256:
         roofline["traffic"] = ctr["dram_bytes_per_iteration"]
     elif ctr and workload == "batched" and cfg["count"] == 256:
@@ -947,7 +952,7 @@ def measure(args, workload, env, steps, warmup, cpu_budget=(10.0, 8.0)) -> dict:
         else:
             roofline = dict(hbm, bound="hbm", traffic=None, inst_per_option=None)
         roofline.update({"kernel": fused["dominant"], "kernel_name": fused["dominant"],
-                         "counters_kernel": (cfg.get("counters") or {}).get("kernel"), "kernel_ms": kern_ms,
+                         "counters_kernel": counters_kernels(cfg), "kernel_ms": kern_ms,
                          "launches": fused["dominant_launches"]})
 
     cpu = None
@@ -985,8 +990,17 @@ def measure(args, workload, env, steps, warmup, cpu_budget=(10.0, 8.0)) -> dict:
 def counters_for(cfg: dict, kernel_name):
     """The ncu counters stored for a workload, if they were taken on the kernel
     named (its name hashes its generated body), else None."""
-    ctr = cfg.get("counters")
-    return ctr if ctr and kernel_name and ctr.get("kernel") == kernel_name else None
+    ctrs = cfg.get("counters") or []
+    for ctr in ([ctrs] if isinstance(ctrs, dict) else ctrs):
+        if kernel_name and ctr.get("kernel") == kernel_name:
+            return ctr
+    return None
+
+
+def counters_kernels(cfg: dict):
+    """Names of the kernels a workload's stored counters belong to."""
+    ctrs = cfg.get("counters") or []
+    return [c["kernel"] for c in ([ctrs] if isinstance(ctrs, dict) else ctrs)]
 
 
 COMPACT_KEYS = ("metric", "value", "unit", "steps", "warmup", "ms_per_step", "dtype", "config", "gpu_launches",
@@ -1047,6 +1061,8 @@ def main():
     ap.add_argument("--e2e-contexts", type=int, default=0, help="Black-Scholes end to end: streams (tuning)")
     ap.add_argument("--e2e-mode", default="", choices=["", "zero_copy", "pipeline"],
                     help="Black-Scholes end to end: kernels on mapped host memory, or pipelined copies")
+    ap.add_argument("--stage-x", default="", choices=["", "on", "off"],
+                    help="SpMV x windows staged in shared memory (default: the workload's configuration)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="CG / batched CG / Jacobi: keep the configured tiling and launch shape")
     ap.add_argument("--compile-report", action="store_true",

@@ -94,11 +94,22 @@ typedef enum { DFS_REDOP_NONE = 0, DFS_REDOP_SUM = 1 } dfs_redop;
  *     no value yet starts from zero; otherwise it folds into the value.
  *     The order of summation is fixed (per point, then over points in
  *     order), so results are reproducible run to run.
- *   DFS_OP_SPMV [rowptr R, col R, val R, x R, y W]   y = A x, CSR
+ *   DFS_OP_SPMV [rowptr R, col R, val R, x R, y W (, win R)]   y = A x, CSR
  *     rowptr/col are int32, val/x/y one float dtype; rowptr, col, val and x
  *     are read through None (any row may touch any column); y through a
  *     1-D Tiling whose sub-store at each point is the block of rows it owns.
+ *     win (optional) is an access hint that does not change y: an int32 1-D
+ *     store read through a Tiling of 6 elements per point (tile 6, offset 0
+ *     relative to the store, one record per point of y's tiling), holding up
+ *     to three windows (lo0, len0, lo1, len1, lo2, len2) of x, in elements of
+ *     x, that the point's rows read (dfs_spmv_windows computes them).  A
+ *     kernel that gives each point its own block of rows copies the windows
+ *     into shared memory (bulk copies) before the rows run and reads x there;
+ *     a record whose windows are out of x's bounds, not 16-byte aligned
+ *     (start and size) or larger than DFS_SPMV_STAGE_BYTES in all is ignored
+ *     for that point.  Results are bit-identical with and without win.
  */
+#define DFS_SPMV_STAGE_BYTES 53248 /* shared memory for staged x windows per CTA */
 typedef enum {
   DFS_OP_COPY = 1,
   DFS_OP_NEG = 2,
@@ -506,6 +517,25 @@ int dfs_set_launch_config(dfs_ctx *ctx, int32_t block_threads, int32_t unroll, i
  * dfs_rowblock_sizes or for a null array that must hold entries,
  * DFS_ERR_TOO_LARGE when n_own + n_halo exceeds the int32 range.
  */
+/*
+ * dfs_spmv_windows -- the windows of x that each point of an SpMV reads, for
+ * the optional `win` argument of DFS_OP_SPMV.  The matrix is CSR (rowptr:
+ * nrows + 1 int32, rowptr[0] == 0, non-decreasing; col: rowptr[nrows] int32
+ * in [0, ncols)); point p owns rows [p tile, min((p + 1) tile, nrows)).  For
+ * each point, the distinct columns of its rows are merged into intervals
+ * (gaps of up to 64 columns are absorbed), the closest intervals are merged
+ * until at most three remain, and each interval is widened to 16-byte
+ * boundaries of an x of `elem_bytes`-byte elements whose first element is
+ * 16-byte aligned, then clipped to the 16-byte-aligned part of [0, ncols)
+ * (columns left outside are read from global memory).  A point whose
+ * windows exceed budget_bytes in all gets an empty record (all zeros).
+ * out: 6 int32 per point, ceil(nrows / tile) points, owned by the caller.
+ * Host only; needs no device.  Returns DFS_ERR_INVALID for a malformed
+ * matrix, tile < 1, elem_bytes not 4 or 8, or a null pointer.
+ */
+int dfs_spmv_windows(const int32_t *rowptr, const int32_t *col, int64_t nrows, int64_t ncols, int64_t tile,
+                     int32_t elem_bytes, int64_t budget_bytes, int32_t *out);
+
 typedef struct {
   int64_t row_lo, row_hi; /* owned global rows */
   int64_t nnz;            /* stored entries of the owned rows */

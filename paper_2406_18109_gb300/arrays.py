@@ -21,6 +21,7 @@ from __future__ import annotations
 import ctypes as C
 import math
 import struct
+import weakref
 
 import numpy as np
 
@@ -47,7 +48,8 @@ class Runtime:
                  stream: int | None = None, cache_dir: str | None = None, timeout_s: float = 2.0,
                  tile: int | None = None, rows: int | None = None, sms: int = 152,
                  debug_skip_arrival: int = 0, time_launches: bool = False, tile_max: int = 16384,
-                 min_points: int | None = None, window_growth: bool = False, window_max: int = 0):
+                 min_points: int | None = None, window_growth: bool = False, window_max: int = 0,
+                 stage_x: bool = False):
         cfg = B.dfs_config_default()
         cfg.device = device
         cfg.fusion = 1 if fusion else 0
@@ -78,6 +80,10 @@ class Runtime:
         self.tile_max = tile_max
         self.min_points = min_points
         self._alive = True
+        # SpMV x windows staged in shared memory (the optional window argument
+        # of DFS_OP_SPMV); matrices register here to follow tiling changes
+        self.stage_x = stage_x
+        self._csrs = weakref.WeakSet()
         L = B.lib()
         self._lib_submit = L.dfs_submit
         self._lib_create = L.dfs_store_create
@@ -280,6 +286,8 @@ class Runtime:
         if min_points is not None:
             self.min_points = min_points
         self._layouts.clear()
+        for m in list(self._csrs):
+            m.prepare_windows()
 
     def read_scalars(self, arrays) -> list:
         """Values of many 0-d arrays with one gather and one copy (dfs_read_scalars)."""
@@ -560,6 +568,9 @@ def norm(x: Array) -> Array:
 class CSR:
     """CSR matrix (int32 row pointers and columns), the Legate Sparse layout."""
 
+    _win = None    # tile -> window store (staged SpMV), when the runtime stages x
+    _host = None   # host copies of (rowptr, col), kept only while staging
+
     def __init__(self, rt: Runtime, rowptr: np.ndarray, col: np.ndarray, val: np.ndarray, ncols: int | None = None):
         self.rt = rt
         self.nrows = len(rowptr) - 1
@@ -569,6 +580,24 @@ class CSR:
         self.col = rt.array(np.asarray(col, dtype=np.int32))
         self.val = rt.array(np.asarray(val))
         self.dtype = self.val.dtype
+        # x windows per tile of rows (staged SpMV); the structure is kept on
+        # the host to compute them for the tile in use, outside batches,
+        # captures and recordings (an upload is not allowed inside them)
+        if rt.stage_x:
+            self._win = {}
+            self._host = (np.asarray(rowptr, dtype=np.int32), np.asarray(col, dtype=np.int32))
+            rt._csrs.add(self)
+            self.prepare_windows()
+
+    def prepare_windows(self):
+        """Computes and uploads the x windows for the runtime's current tile
+        of this matrix's rows (no-op when staging is off or they exist)."""
+        if self._host is None:
+            return
+        t = self.rt.tile_1d(self.nrows)
+        if t not in self._win:
+            rec = B.dfs_spmv_windows(self._host[0], self._host[1], self.ncols, t, self.dtype.itemsize)
+            self._win[t] = self.rt.array(rec)
 
     def __matmul__(self, x: Array) -> Array:
         y = self.rt._new((self.nrows,), self.dtype)
@@ -584,5 +613,10 @@ class CSR:
         _ARG.pack_into(rt._argbuf, 64, self.val.handle, n, _R, 0, 0.0)
         _ARG.pack_into(rt._argbuf, 96, x.handle, n, _R, 0, 0.0)
         _ARG.pack_into(rt._argbuf, 128, y.handle, lay[1], _W, 0, 0.0)
-        rt._issue(96, lay, 5)
+        win = self._win.get(rt.tile_1d(self.nrows)) if self._win and y.shape[0] == self.nrows else None
+        if win is not None:
+            _ARG.pack_into(rt._argbuf, 160, win.handle, rt.tiling((6,)), _R, 0, 0.0)
+            rt._issue(96, lay, 6)
+        else:
+            rt._issue(96, lay, 5)
         return y

@@ -41,7 +41,8 @@ EXPORTS = ("dfs_config_default", "dfs_init", "dfs_shutdown", "dfs_store_create",
            "dfs_read_scalars_async", "dfs_record", "dfs_wait", "dfs_poll", "dfs_ticket_elapsed_ms",
            "dfs_ticket_release", "dfs_template_begin", "dfs_template_end", "dfs_template_inputs",
            "dfs_template_replay", "dfs_template_free", "dfs_rowblock_bounds", "dfs_rowblock_sizes",
-           "dfs_rowblock_plan")
+           "dfs_rowblock_plan", "dfs_spmv_windows")
+SPMV_STAGE_BYTES = 53248          # DFS_SPMV_STAGE_BYTES
 
 
 class dfs_config(C.Structure):
@@ -129,6 +130,7 @@ def lib():
             "dfs_rowblock_bounds": (C.c_int, [I64, I32, I32, pI64, pI64]),
             "dfs_rowblock_sizes": (C.c_int, [P, P, I64, I32, I32, C.POINTER(dfs_rowblock_sizes_t)]),
             "dfs_rowblock_plan": (C.c_int, [P, P, I64, I32, I32, P, P, P, P, P, P]),
+            "dfs_spmv_windows": (C.c_int, [P, P, I64, I64, I64, I32, I64, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -437,4 +439,18 @@ def dfs_rowblock_plan(rowptr, col, nranks: int, rank: int) -> dict:
                                      out["local_rowptr"].ctypes.data, out["local_col"].ctypes.data,
                                      out["halo_cols"].ctypes.data, out["recv_counts"].ctypes.data,
                                      out["send_idx"].ctypes.data, out["send_counts"].ctypes.data))
+    return out
+
+
+def dfs_spmv_windows(rowptr, col, ncols: int, tile: int, elem_bytes: int, budget_bytes: int = SPMV_STAGE_BYTES):
+    """The x windows of every SpMV point (tiles of `tile` rows) of a CSR
+    matrix: an int32 array of 6 entries per point (see dfs_spmv_windows in
+    diffuse.h)."""
+    import numpy as np
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    nrows = len(rowptr) - 1
+    out = np.zeros(6 * max(1, -(-nrows // tile) if tile > 0 else 1), np.int32)   # the C call checks tile
+    _check(None, lib().dfs_spmv_windows(rowptr.ctypes.data, col.ctypes.data, nrows, ncols, tile, elem_bytes,
+                                        budget_bytes, out.ctypes.data))
     return out

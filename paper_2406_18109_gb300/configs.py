@@ -22,9 +22,10 @@ BLACK_SCHOLES = dict(n=1 << 26, seed=1, r=0.02, sigma=0.3, tile=16384, block=512
 # int32 indices, x* ~ U[-1,1] (seed 0), b = A x*, x0 = 0; five iterations
 # share one flush window (one persistent launch) in the captured solve
 CG = dict(m=256, iters=50, seed=0, tile=512, block=256, unroll=2, iters_per_flush=5, window_size=1024,
-          # ncu counters of the five-iteration window kernel named `kernel`
-          # (None: none taken on the current generated code)
-          counters=None)
+          # ncu counters of the steady five-iteration window kernel named
+          # `kernel` (this launch shape): DRAM bytes per iteration; the rest of
+          # the traffic is served by L2 (profiles/)
+          counters=dict(kernel="dfs_k0ee0e6ccc94c32d2", dram_bytes_per_iteration=5.865984e6 / 5))
 
 # Batched CG: 256 independent solves of uneven size (half 2-D Poisson with m
 # log-uniform in [32, 1024], half random diagonally dominant SPD with n
@@ -34,9 +35,11 @@ CG = dict(m=256, iters=50, seed=0, tile=512, block=256, unroll=2, iters_per_flus
 # points per problem, at most tile_max elements); the bench autotunes
 # tile_max and the launch shape before capturing.
 BATCHED_CG = dict(count=256, seed=4, iters=100, dtype="f64", tile_max=2048, min_points=2, block=256, unroll=2,
-                  # ncu counters of the batched iteration kernel named `kernel`
-                  # (None: none taken on the current generated code)
-                  counters=None)
+                  # ncu counters of the batched iteration kernel named `kernel`,
+                  # FP64 and FP32, at this launch shape: DRAM bytes (read + write)
+                  # per launch (profiles/)
+                  counters=[dict(kernel="dfs_b0fc715b3e5f18a2c", dram_bytes_per_launch=3.019141e9 + 0.672542e9),
+                            dict(kernel="dfs_b0a54bf6785d3c28c", dram_bytes_per_launch=1.865591e9 + 0.315713e9)])
 
 # Jacobi: Fig. 1 stencil on an 8192x8192 FP32 grid (8190^2 interior),
 # 200 sweeps, interior U[0,1] (seed 2), boundary 1.0

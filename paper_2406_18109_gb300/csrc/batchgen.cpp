@@ -57,6 +57,7 @@ class BatchGen {
   std::map<int, int> group_pslot;         // vector group -> prefix slot
   int nbar = 0;
   int nreg = 0;
+  bool stage = false;  // some SpMV carries x windows, staged in shared memory
 
   const LaunchRoot& R(int64_t r) const { return S.roots[S.root_index.at(r)]; }
   std::string T(int dt) const { return dtype_cname(dt); }
@@ -279,7 +280,8 @@ void BatchGen::vector_group(int g) {
         }
       }
       if (t.op == DFS_OP_SPMV)
-        for (size_t ai = 0; ai < 4; ++ai) need_base(t, ai);
+        for (size_t ai = 0; ai < t.args.size(); ++ai)
+          if (ai != 4) need_base(t, ai);
       if (is_red(t.op)) {
         const Arg& out = t.args.back();
         Acc ac{k, bc.nred++, "acc" + std::to_string(bc.nred), out.dtype};
@@ -313,6 +315,21 @@ void BatchGen::vector_group(int g) {
       }
     }
     std::map<int, std::string> spre;  // SpMV task -> value computed before the body
+    // the first SpMV of the nest that carries x windows: stage them for this
+    // point (every thread of the CTA is here, at the same point)
+    int staged = -1;
+    for (int k = i; k < j && stage && staged < 0; ++k)
+      if (S.tasks[k].op == DFS_OP_SPMV && S.tasks[k].args.size() == 6) staged = k;
+    if (staged >= 0) {
+      const Task& t = S.tasks[staged];
+      const Arg& x = t.args[3];
+      const int xb = vslots(t, 3);
+      const std::string tn = T(x.dtype);
+      o << ind << "  const XWin xw_ = xstage<" << tn << ">((" << tn << "*)dfs_xs_raw, " << DFS_SPMV_STAGE_BYTES / (int)dtype_size(x.dtype)
+        << ", " << P_(x.root) << " + " << base.at(akey(x)) << ", D.v[" << xb + 1 << "] - D.v[" << xb
+        << "], (const int*)" << P_(t.args[5].root) << " + " << base.at(akey(t.args[5]))
+        << ", &xs_mbar_, xs_ph_, xs_live_, ctl, P.timeout_ns);\n";
+    }
     auto body = [&](int w, const std::vector<std::string>& slots, const std::vector<std::string>& ef,
                     const std::string& pad) {
       const int ns = (int)slots.size();
@@ -340,7 +357,7 @@ void BatchGen::vector_group(int g) {
           LaneOps lane;
           for (int k = i; k < j; ++k) {
             const Task& t = S.tasks[k];
-            const int dt = t.args.back().dtype;
+            const int dt = space(t).dtype;   // the output's (y for an SpMV, whose last arg may be its windows)
             auto val = [&](size_t ai) -> std::string {
               const Arg& a = t.args[ai];
               if (a.imm) return immv.at({k, (int)ai});
@@ -361,10 +378,11 @@ void BatchGen::vector_group(int g) {
               const int yb = vslots(t, 4);
               const std::string row = "(" + base.at(akey(y)) + " - D.v[" + std::to_string(yb + 2) + "] + " + ef[s] +
                                       " + " + std::to_string(l) + ")";
-              o << pad << "const " << T(dt) << " " << res << " = spmv_row<" << T(dt) << ">(" << P_(t.args[0].root)
-                << " + " << base.at(akey(t.args[0])) << ", " << P_(t.args[1].root) << " + "
-                << base.at(akey(t.args[1])) << ", " << P_(t.args[2].root) << " + " << base.at(akey(t.args[2]))
-                << ", " << P_(t.args[3].root) << " + " << base.at(akey(t.args[3])) << ", " << row << ");\n";
+              o << pad << "const " << T(dt) << " " << res << " = " << (k == staged ? "spmv_row_xs<" : "spmv_row<")
+                << T(dt) << ">(" << P_(t.args[0].root) << " + " << base.at(akey(t.args[0])) << ", "
+                << P_(t.args[1].root) << " + " << base.at(akey(t.args[1])) << ", " << P_(t.args[2].root) << " + "
+                << base.at(akey(t.args[2])) << ", " << P_(t.args[3].root) << " + " << base.at(akey(t.args[3])) << ", "
+                << row << (k == staged ? ", (const " + T(dt) + "*)dfs_xs_raw, xw_" : std::string()) << ");\n";
               cur[akey(y)] = res;
             } else if (is_red(t.op)) {
               const Acc* ac = nullptr;
@@ -517,9 +535,18 @@ bool BatchGen::run(BatchCode& out, std::string& why) {
     if (r.param >= 0) bc.ptr_roots[r.param] = r.root;
   for (const LaunchRoot& r : S.roots) produced[r.root] = false;
 
+  // staging x windows needs one-row-per-lane SpMVs (no lanes shared)
+  for (const Task& t : S.tasks)
+    if (!coop && t.op == DFS_OP_SPMV && t.args.size() == 6) stage = true;
   o << "  __shared__ double red_buf[" << S.block << "];\n";
   o << "  __shared__ i64 s_ticket;\n";
   o << "  Ctl* ctl = P.ctl;\n  const i64 NI = P.ninst;\n";
+  if (stage) {
+    bc.dyn_smem = DFS_SPMV_STAGE_BYTES;
+    o << "  extern __shared__ __align__(128) unsigned char dfs_xs_raw[];\n";
+    o << "  __shared__ __align__(8) u64 xs_mbar_;\n  u32 xs_ph_ = 0;\n  bool xs_live_ = true;\n";
+    o << "  xstage_init(&xs_mbar_);\n";
+  }
   o << "  do {\n";
   bool in_scalar = false, first = true;
   for (int g = 0; g < (int)S.groups.size(); ++g) {

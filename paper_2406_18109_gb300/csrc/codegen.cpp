@@ -122,6 +122,7 @@ class Gen {
   std::vector<Red> pending_red;           // reductions awaiting finalisation
   int nbar = 0;
   int nbc = 0;  // shared broadcast slots of finished reductions
+  bool stage = false;  // some per-point SpMV nest stages x windows in shared memory
 
   const LaunchRoot& R(int64_t root) const { return S.roots[S.root_index.at(root)]; }
   bool temp_in(int g, int64_t root) const;
@@ -521,6 +522,22 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
     if (t.op != DFS_OP_SPMV) continue;
     for (int ai = 0; ai < 4; ++ai) need_base(t.args[ai]);
   }
+  // the first SpMV of a per-point nest that carries x windows: stage them for
+  // this point (every thread of the CTA is here, at the same point)
+  int staged = -1;
+  if (stage && !flat && n.dims == 1 && !n.coop)
+    for (int i = n.first; i < n.last && staged < 0; ++i)
+      if (S.tasks[i].op == DFS_OP_SPMV && S.tasks[i].args.size() == 6) staged = i;
+  if (staged >= 0) {
+    const Task& t = S.tasks[staged];
+    const Arg& x = t.args[3];
+    const std::string tn = T(x.dtype);
+    const std::string wb = need_base(t.args[5]);
+    o << ind << "  const XWin xw_ = xstage<" << tn << ">((" << tn << "*)dfs_xs_raw, "
+      << DFS_SPMV_STAGE_BYTES / (int)dtype_size(x.dtype) << ", " << ptr(x.root) << " + " << base.at(akey(x)) << ", "
+      << (x.part.vhi[0] - x.part.vlo[0]) << "LL, (const int*)" << ptr(t.args[5].root) << " + " << wb
+      << ", &xs_mbar_, xs_ph_, xs_live_, ctl, P.timeout_ns);\n";
+  }
   // immediates hoisted once per nest
   std::map<std::pair<int, int>, std::string> immv;
   for (int i = n.first; i < n.last; ++i) {
@@ -588,7 +605,7 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
         for (int i = n.first; i < n.last; ++i) {
           const Task& t = S.tasks[i];
           if (t.scalar()) continue;
-          const int dt = t.args.back().dtype;
+          const int dt = space_arg(t).dtype;   // the output's (y for an SpMV, whose last arg may be its windows)
           auto val = [&](size_t ai) -> std::string {
             const Arg& a = t.args[ai];
             if (a.imm) return immv.at({i, (int)ai});
@@ -608,10 +625,11 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
             const Arg& y = t.args[4];
             const std::string row = "(" + base.at(akey(y)) + " - " + std::to_string(y.part.vlo[0]) + "LL + " +
                                     eflat[s] + " + " + std::to_string(l) + ")";
-            o << pad << "const " << T(dt) << " " << res << " = spmv_row<" << T(dt) << ">(" << ptr(t.args[0].root)
-              << " + " << base.at(akey(t.args[0])) << ", " << ptr(t.args[1].root) << " + "
-              << base.at(akey(t.args[1])) << ", " << ptr(t.args[2].root) << " + " << base.at(akey(t.args[2]))
-              << ", " << ptr(t.args[3].root) << " + " << base.at(akey(t.args[3])) << ", " << row << ");\n";
+            o << pad << "const " << T(dt) << " " << res << " = " << (i == staged ? "spmv_row_xs<" : "spmv_row<")
+              << T(dt) << ">(" << ptr(t.args[0].root) << " + " << base.at(akey(t.args[0])) << ", "
+              << ptr(t.args[1].root) << " + " << base.at(akey(t.args[1])) << ", " << ptr(t.args[2].root) << " + "
+              << base.at(akey(t.args[2])) << ", " << ptr(t.args[3].root) << " + " << base.at(akey(t.args[3])) << ", "
+              << row << (i == staged ? ", (const " + T(dt) + "*)dfs_xs_raw, xw_" : std::string()) << ");\n";
             cur[akey(y)] = res;
           } else if (is_reduction(t.op)) {
             const Acc* ac = nullptr;
@@ -925,8 +943,28 @@ KernelCode Gen::run() {
   emit_params();
   std::ostringstream body;
   // the kernel body is generated into `o`; header assembled afterwards
+  // x windows are staged by per-point nests whose SpMV rows are not shared
+  // between lanes (the same test emit_vector_group and emit_nest apply)
+  for (int g = 0; g < (int)S.groups.size() && !stage; ++g) {
+    if (S.groups[g].scalar) continue;
+    const std::vector<Nest> ns = nests_of(g);
+    bool flat = ns.size() == 1;
+    for (int i = S.groups[g].begin; i < S.groups[g].end && flat; ++i)
+      if (is_reduction(S.tasks[i].op)) flat = false;
+    if (flat && space_arg(S.tasks[S.groups[g].begin]).nd > 3) flat = false;
+    for (const Nest& n : ns)
+      if (!flat && n.dims == 1 && !n.coop)
+        for (int i = n.first; i < n.last; ++i)
+          if (S.tasks[i].op == DFS_OP_SPMV && S.tasks[i].args.size() == 6) stage = true;
+  }
   o << "  __shared__ double red_buf[" << S.block << "];\n";
   o << "  Ctl* ctl = P.ctl;\n";
+  if (stage) {
+    kc.dyn_smem = DFS_SPMV_STAGE_BYTES;
+    o << "  extern __shared__ __align__(128) unsigned char dfs_xs_raw[];\n";
+    o << "  __shared__ __align__(8) u64 xs_mbar_;\n  u32 xs_ph_ = 0;\n  bool xs_live_ = true;\n";
+    o << "  xstage_init(&xs_mbar_);\n";
+  }
   emit_prologue();
   o << "  do {\n";
   for (int g = 0; g < (int)S.groups.size(); ++g) {

@@ -318,6 +318,135 @@ __device__ __forceinline__ i64 take_ticket(Ctl* ctl, int q, i64* s_ticket) {
   return t;
 }
 
+// ------------------------------------------------ staged SpMV x windows
+// An SpMV point (a tile of rows) reads x at the columns of its rows.  When the
+// task carries a window argument, up to three windows [lo_k, lo_k + len_k) of
+// x covering most of those columns are copied into shared memory by the bulk
+// copy engine (TMA, cp.async.bulk) at the start of the point, completing on
+// one mbarrier; the rows then read x from shared memory inside the windows
+// and from global memory outside them.  The values are the same either way,
+// so results do not depend on the staging.  Windows come from host data:
+// every field is checked here (bounds, 16-byte alignment of source and size,
+// the shared-memory capacity) and a point whose record fails the checks is
+// simply not staged.
+struct XWin {
+  int lo[3];
+  int len[3];
+};
+
+enum { ERR_COPY_TIMEOUT = 2 };
+
+__device__ __forceinline__ u32 smem_u32(const void* p) { return (u32)__cvta_generic_to_shared(p); }
+
+// Once per CTA, by every thread, before the first xstage.
+__device__ __forceinline__ void xstage_init(u64* mbar) {
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ bool mbar_try(u64* mbar, u32 phase) {
+  u32 done;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+      : "=r"(done)
+      : "r"(smem_u32(mbar)), "r"(phase)
+      : "memory");
+  return done != 0;
+}
+
+// Stages the point's windows (record w: lo0, len0, lo1, len1, lo2, len2 in
+// elements of x, whose extent is xlen) into xs (cap elements).  Called by
+// every thread of the CTA at the same point.  Returns the windows in use (all
+// lengths 0 when nothing is staged).  The wait for the bytes gives up after
+// timeout_ns: the CTA then records ERR_COPY_TIMEOUT, waits once more (bounded)
+// for its copy, and stops staging for the rest of the launch (`live`).
+template <typename T>
+__device__ __forceinline__ XWin xstage(T* xs, int cap, const T* x, i64 xlen, const int* w, u64* mbar, u32& phase,
+                                       bool& live, Ctl* ctl, u64 timeout_ns) {
+  XWin win;
+  i64 tot = 0;
+  bool ok = live;
+  for (int k = 0; k < 3; ++k) {
+    const int lo = ldro(w + 2 * k), len = ldro(w + 2 * k + 1);
+    const bool good = len >= 0 && len <= cap && lo >= 0 && (i64)lo + len <= xlen &&
+                      ((unsigned long long)(x + lo) & 15ull) == 0 && ((len * (int)sizeof(T)) & 15) == 0;
+    ok = ok && good;
+    win.lo[k] = lo;
+    win.len[k] = good ? len : 0;
+    tot += good ? len : 0;
+  }
+  if (!ok || tot == 0 || tot > cap) {
+    for (int k = 0; k < 3; ++k) win.len[k] = 0;
+    return win;
+  }
+  __syncthreads();  // every read of the previous point's windows is done
+  if (threadIdx.x == 0) {
+    // the generic-proxy writes of x (earlier phases, ordered by the grid
+    // barrier) and of xs (the previous point) before the async-proxy copy
+    asm volatile("fence.proxy.async;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)),
+                 "r"((u32)tot * (u32)sizeof(T))
+                 : "memory");
+    int off = 0;
+    for (int k = 0; k < 3; ++k) {
+      if (win.len[k] > 0)
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         smem_u32(xs + off)),
+                     "l"(x + win.lo[k]), "r"(win.len[k] * (int)sizeof(T)), "r"(smem_u32(mbar))
+                     : "memory");
+      off += win.len[k];
+    }
+  }
+  bool done = mbar_try(mbar, phase);
+  const u64 t0 = globaltimer_ns();
+  while (!done && globaltimer_ns() - t0 <= timeout_ns) done = mbar_try(mbar, phase);
+  if (!__syncthreads_and(done ? 1 : 0)) {
+    if (threadIdx.x == 0 && atomicCAS(&ctl->err, 0, (int)ERR_COPY_TIMEOUT) == 0) ctl->err_where = -1;
+    const u64 t1 = globaltimer_ns();
+    while (!mbar_try(mbar, phase) && globaltimer_ns() - t1 <= timeout_ns) {
+    }
+    __syncthreads();
+    live = false;
+    for (int k = 0; k < 3; ++k) win.len[k] = 0;
+    return win;
+  }
+  phase ^= 1u;
+  return win;
+}
+
+// x[c] from the staged windows when c falls in one, else from global memory.
+template <typename T>
+__device__ __forceinline__ T xsv(const T* x, const T* xs, const XWin& w, int c) {
+  unsigned d;
+  if ((d = (unsigned)(c - w.lo[0])) < (unsigned)w.len[0]) return xs[d];
+  if ((d = (unsigned)(c - w.lo[1])) < (unsigned)w.len[1]) return xs[w.len[0] + d];
+  if ((d = (unsigned)(c - w.lo[2])) < (unsigned)w.len[2]) return xs[w.len[0] + w.len[1] + d];
+  return ld(x + c);
+}
+
+// spmv_row with x read through the staged windows: the same entries in the
+// same order with the same fma, so the same bits.
+template <typename T>
+__device__ __forceinline__ T spmv_row_xs(const int* __restrict__ rowptr, const int* __restrict__ col,
+                                         const T* __restrict__ val, const T* x, i64 r, const T* xs, const XWin& w) {
+  const int k0 = __ldg(rowptr + r), k1 = __ldg(rowptr + r + 1);
+  T acc = T(0);
+  int k = k0;
+  for (; k + 1 < k1; k += 2) {
+    const int c0 = __ldg(col + k), c1 = __ldg(col + k + 1);
+    const T v0 = __ldg(val + k), v1 = __ldg(val + k + 1);
+    const T x0 = xsv(x, xs, w, c0), x1 = xsv(x, xs, w, c1);
+    acc = red_fma(v0, x0, acc);
+    acc = red_fma(v1, x1, acc);
+  }
+  if (k < k1) acc = red_fma(__ldg(val + k), xsv(x, xs, w, __ldg(col + k)), acc);
+  return acc;
+}
+
 // --------------------------------------------------------------- reductions
 template <typename T> __device__ __forceinline__ T warp_sum_xor(T v) {
 #pragma unroll

@@ -46,6 +46,7 @@ bool driver_load(Driver& d, std::string& err) {
             resolve("cuOccupancyMaxActiveBlocksPerMultiprocessor", d.OccupancyMaxActiveBlocksPerMultiprocessor,
                     err) &&
             resolve("cuFuncGetAttribute", d.FuncGetAttribute, err) &&
+            resolve("cuFuncSetAttribute", d.FuncSetAttribute, err) &&
             resolve("cuGetErrorString", d.GetErrorString, err);
   d.loaded = ok;
   return ok;
@@ -106,7 +107,8 @@ size_t Jit::compile_only(const std::string& source, const std::string& name, std
   return cubin.size();
 }
 
-const Compiled* Jit::get(const std::string& source, const std::string& name, int block, std::string& err) {
+const Compiled* Jit::get(const std::string& source, const std::string& name, int block, std::string& err,
+                         int dyn_smem) {
   auto it = cache_.find(source);
   if (it != cache_.end()) {
     ++hits_;
@@ -153,7 +155,18 @@ const Compiled* Jit::get(const std::string& source, const std::string& name, int
     return nullptr;
   }
   drv_->FuncGetAttribute(&c.regs, CU_FUNC_ATTRIBUTE_NUM_REGS, c.fn);
-  drv_->OccupancyMaxActiveBlocksPerMultiprocessor(&c.occupancy, c.fn, block, 0);
+  if (dyn_smem > 0) {
+    cr = drv_->FuncSetAttribute(c.fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, dyn_smem);
+    if (cr != CUDA_SUCCESS) {
+      const char* s = nullptr;
+      drv_->GetErrorString(cr, &s);
+      err = std::string("dynamic shared memory of ") + name + ": " + (s ? s : "unknown driver error");
+      drv_->ModuleUnload(c.module);
+      return nullptr;
+    }
+  }
+  c.dyn_smem = dyn_smem;
+  drv_->OccupancyMaxActiveBlocksPerMultiprocessor(&c.occupancy, c.fn, block, (size_t)dyn_smem);
   const auto t1 = std::chrono::steady_clock::now();
   c.compile_s = std::chrono::duration<double>(t1 - t0).count();
   compile_s_ += c.compile_s;

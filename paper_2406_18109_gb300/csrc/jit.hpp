@@ -20,6 +20,7 @@ struct Driver {  // driver entry points, resolved through the runtime at first u
                                       unsigned, CUstream, void**) = nullptr;
   CUresult (*OccupancyMaxActiveBlocksPerMultiprocessor)(int*, CUfunction, int, size_t) = nullptr;
   CUresult (*FuncGetAttribute)(int*, CUfunction_attribute, CUfunction) = nullptr;
+  CUresult (*FuncSetAttribute)(CUfunction, CUfunction_attribute, int) = nullptr;
   CUresult (*GetErrorString)(CUresult, const char**) = nullptr;
   bool loaded = false;
 };
@@ -31,7 +32,8 @@ struct Compiled {
   CUmodule module = nullptr;
   CUfunction fn = nullptr;
   int regs = 0;
-  int occupancy = 0;  // resident CTAs per SM at the block size
+  int occupancy = 0;  // resident CTAs per SM at the block size and dynamic shared memory
+  int dyn_smem = 0;   // dynamic shared memory per CTA the kernel is launched with
   double compile_s = 0.0;
   bool from_disk = false;
 };
@@ -41,9 +43,11 @@ class Jit {
   // `device_source` is the text of dfs_device.cuh.  `arch` e.g. "sm_103a".
   Jit(Driver* drv, std::string arch, std::string cache_dir);
   ~Jit();
-  // Compiles (or fetches) the kernel `name` from `source`; returns nullptr and
+  // Compiles (or fetches) the kernel `name` from `source`, to be launched with
+  // `dyn_smem` bytes of dynamic shared memory per CTA; returns nullptr and
   // sets `err` on failure.
-  const Compiled* get(const std::string& source, const std::string& name, int block, std::string& err);
+  const Compiled* get(const std::string& source, const std::string& name, int block, std::string& err,
+                      int dyn_smem = 0);
   // NVRTC only (no device needed): returns the cubin size, 0 on failure.
   size_t compile_only(const std::string& source, const std::string& name, std::string& err);
   double compile_seconds() const { return compile_s_; }

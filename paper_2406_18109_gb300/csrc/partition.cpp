@@ -1,4 +1,5 @@
-// partition.cpp -- row-block partition of a CSR matrix over ranks (host only).
+// partition.cpp -- host-side plans over a CSR matrix: its row-block
+// partition over ranks, and the x windows each SpMV point reads.
 //
 // Section 3.2: an index task's launch domain is split into point tasks, one
 // per processor; across GPUs a vector store is tiled by row blocks and every
@@ -9,6 +10,9 @@
 // rows renumbered to local columns (owned entries first, halo slots after),
 // the halo slots it receives from each rank and the owned entries it sends to
 // each rank.  The exchange itself and the solver steps run elsewhere.
+// The second plan (dfs_spmv_windows, at the end) lists, for each tile of
+// rows, the intervals of x its rows read, for kernels that stage them in
+// shared memory.
 #include <algorithm>
 #include <cstdint>
 #include <vector>
@@ -134,5 +138,63 @@ extern "C" int dfs_rowblock_plan(const int32_t* rowptr, const int32_t* col, int6
   std::copy(p.recv_counts.begin(), p.recv_counts.end(), recv_counts);
   std::copy(p.send_idx.begin(), p.send_idx.end(), send_idx);
   std::copy(p.send_counts.begin(), p.send_counts.end(), send_counts);
+  return DFS_OK;
+}
+
+// ------------------------------------------------------ SpMV x windows
+// For each point of an SpMV (a tile of rows), the columns its rows read,
+// as at most three intervals of x widened to 16-byte boundaries: the data a
+// kernel copies into shared memory before the rows run (see DFS_OP_SPMV).
+extern "C" int dfs_spmv_windows(const int32_t* rowptr, const int32_t* col, int64_t nrows, int64_t ncols,
+                                int64_t tile, int32_t elem_bytes, int64_t budget_bytes, int32_t* out) {
+  if (!rowptr || !out || nrows < 0 || ncols < 0 || ncols > INT32_MAX || tile < 1 ||
+      (elem_bytes != 4 && elem_bytes != 8) || rowptr[0] != 0)
+    return DFS_ERR_INVALID;
+  for (int64_t i = 0; i < nrows; ++i)
+    if (rowptr[i + 1] < rowptr[i]) return DFS_ERR_INVALID;
+  if (rowptr[nrows] > 0 && !col) return DFS_ERR_INVALID;
+  for (int64_t k = 0; k < rowptr[nrows]; ++k)
+    if (col[k] < 0 || col[k] >= ncols) return DFS_ERR_INVALID;
+  const int64_t q = 16 / elem_bytes;             // elements per 16 bytes
+  const int64_t end_al = ncols / q * q;          // the aligned part of [0, ncols)
+  const int64_t npts = (nrows + tile - 1) / tile;
+  std::vector<int32_t> cs;
+  std::vector<std::pair<int64_t, int64_t>> iv;
+  for (int64_t p = 0; p < npts; ++p) {
+    int32_t* rec = out + 6 * p;
+    for (int k = 0; k < 6; ++k) rec[k] = 0;
+    const int64_t r0 = p * tile, r1 = std::min(r0 + tile, nrows);
+    cs.assign(col + rowptr[r0], col + rowptr[r1]);
+    std::sort(cs.begin(), cs.end());
+    cs.erase(std::unique(cs.begin(), cs.end()), cs.end());
+    iv.clear();
+    for (int32_t c : cs) {
+      if (!iv.empty() && c <= iv.back().second + 64) iv.back().second = (int64_t)c + 1;
+      else iv.push_back({c, (int64_t)c + 1});
+    }
+    while (iv.size() > 3) {  // merge the two intervals with the smallest gap
+      size_t best = 0;
+      for (size_t k = 1; k + 1 < iv.size(); ++k)
+        if (iv[k + 1].first - iv[k].second < iv[best + 1].first - iv[best].second) best = k;
+      iv[best].second = iv[best + 1].second;
+      iv.erase(iv.begin() + (int64_t)best + 1);
+    }
+    // widen to 16-byte boundaries, clip to the aligned part of x, merge overlaps
+    std::vector<std::pair<int64_t, int64_t>> al;
+    for (const auto& v : iv) {
+      const int64_t lo = v.first / q * q;
+      const int64_t hi = std::min((v.second + q - 1) / q * q, end_al);
+      if (hi <= lo) continue;
+      if (!al.empty() && lo <= al.back().second) al.back().second = std::max(al.back().second, hi);
+      else al.push_back({lo, hi});
+    }
+    int64_t tot = 0;
+    for (const auto& v : al) tot += v.second - v.first;
+    if (al.empty() || tot * elem_bytes > budget_bytes) continue;
+    for (size_t k = 0; k < al.size(); ++k) {
+      rec[2 * k] = (int32_t)al[k].first;
+      rec[2 * k + 1] = (int32_t)(al[k].second - al[k].first);
+    }
+  }
   return DFS_OK;
 }

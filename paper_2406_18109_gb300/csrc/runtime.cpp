@@ -128,6 +128,7 @@ struct dfs_ctx {
     bool ok = false;
     CUfunction fn = nullptr;
     int grid = 0, block = 0, nbarriers = 0, ninst = 0;
+    int dyn_smem = 0;
     bool coop = false;
     uint64_t blob[8] = {};
     int64_t groups = 0;
@@ -225,7 +226,7 @@ bool arity_ok(int op, int nargs) {
   if (op >= DFS_OP_ADD && op <= DFS_OP_MIN) return nargs == 3;
   if (op == DFS_OP_DOT) return nargs == 3;
   if (op == DFS_OP_SUM) return nargs == 2;
-  if (op == DFS_OP_SPMV) return nargs == 5;
+  if (op == DFS_OP_SPMV) return nargs == 5 || nargs == 6;
   return false;
 }
 bool elementwise(int op) { return (op >= DFS_OP_COPY && op <= DFS_OP_NCDF) || (op >= DFS_OP_ADD && op <= DFS_OP_MIN); }
@@ -305,7 +306,7 @@ int validate(dfs_ctx* c, const Task& t) {
     if (op == DFS_OP_DOT && !same_substores(A[0], A[1])) return bad("DOT operands must have equal sub-store shapes");
     if (A[0].part.kind == 0 && t.npoints() != 1) return bad("reduction inputs need a tiling when the domain has several points");
   } else if (op == DFS_OP_SPMV) {
-    for (int k = 0; k < 5; ++k)
+    for (size_t k = 0; k < A.size(); ++k)
       if (A[k].imm) return bad("SPMV takes no immediates");
     const Arg &rp = A[0], &col = A[1], &val = A[2], &x = A[3], &y = A[4];
     if (rp.dtype != DFS_I32 || col.dtype != DFS_I32) return bad("SPMV rowptr and col are int32");
@@ -316,6 +317,17 @@ int validate(dfs_ctx* c, const Task& t) {
     const int64_t rows = y.part.vhi[0] - y.part.vlo[0];
     if (rp.part.vhi[0] - rp.part.vlo[0] != rows + 1) return bad("SPMV rowptr must have rows(y) + 1 entries");
     if (col.part.vhi[0] - col.part.vlo[0] != val.part.vhi[0] - val.part.vlo[0]) return bad("SPMV col and val lengths differ");
+    if (A.size() == 6) {
+      // the x-window hint: one record of 6 int32 per point of y's tiling
+      const Arg& w = A[5];
+      if (w.dtype != DFS_I32 || w.nd != 1 || w.priv != DFS_PRIV_R) return bad("SPMV windows are a 1-D int32 store read (R)");
+      if (y.part.kind != 1 || w.part.kind != 1 || w.part.tile[0] != 6 || w.part.off[0] != w.part.vlo[0] ||
+          w.part.proj[0] != y.part.proj[0])
+        return bad("SPMV windows are read through a Tiling of 6 elements per point, projected like y");
+      const int64_t ypts = (y.part.vhi[0] - y.part.off[0] + y.part.tile[0] - 1) / y.part.tile[0];
+      if (w.part.vhi[0] - w.part.vlo[0] < 6 * std::max<int64_t>(ypts, t.dom[y.part.proj[0]]))
+        return bad("SPMV windows need one 6-element record per point of the launch domain");
+    }
   } else {
     return bad("unknown op");
   }
@@ -533,7 +545,7 @@ int build_window(dfs_ctx* c, const WindowInfo& wi, std::unique_ptr<CachedWindow>
       if (!c->jit->compile_only(kc.source, kc.name, err)) return fail(c, DFS_ERR_COMPILE, err);
       continue;
     }
-    const Compiled* comp = c->jit->get(kc.source, kc.name, spec.block, err);
+    const Compiled* comp = c->jit->get(kc.source, kc.name, spec.block, err, kc.dyn_smem);
     if (!comp) return fail(c, DFS_ERR_COMPILE, err);
     CachedLaunch L;
     L.k = comp;
@@ -629,9 +641,11 @@ int run_window(dfs_ctx* c, const CachedWindow& cw, const WindowInfo& wi) {
       CUDA_OK(cudaEventRecord(tm.a, c->stream));
     }
     if (L.cooperative)
-      cr = c->drv.LaunchCooperativeKernel(L.k->fn, L.grid, 1, 1, L.block, 1, 1, 0, (CUstream)c->stream, params);
+      cr = c->drv.LaunchCooperativeKernel(L.k->fn, L.grid, 1, 1, L.block, 1, 1, (unsigned)L.k->dyn_smem,
+                                          (CUstream)c->stream, params);
     else
-      cr = c->drv.LaunchKernel(L.k->fn, L.grid, 1, 1, L.block, 1, 1, 0, (CUstream)c->stream, params, nullptr);
+      cr = c->drv.LaunchKernel(L.k->fn, L.grid, 1, 1, L.block, 1, 1, (unsigned)L.k->dyn_smem, (CUstream)c->stream,
+                               params, nullptr);
     if (cr != CUDA_SUCCESS) {
       const char* s = nullptr;
       c->drv.GetErrorString(cr, &s);
@@ -811,8 +825,9 @@ int launch_batched(dfs_ctx* c, const dfs_ctx::LastBatch& L) {
   uint64_t blob[8];
   std::memcpy(blob, L.blob, sizeof blob);
   void* params[] = {blob};
-  CUresult cr = L.coop ? c->drv.LaunchCooperativeKernel(L.fn, L.grid, 1, 1, L.block, 1, 1, 0, (CUstream)c->stream, params)
-                       : c->drv.LaunchKernel(L.fn, L.grid, 1, 1, L.block, 1, 1, 0, (CUstream)c->stream, params, nullptr);
+  const unsigned sm = (unsigned)L.dyn_smem;
+  CUresult cr = L.coop ? c->drv.LaunchCooperativeKernel(L.fn, L.grid, 1, 1, L.block, 1, 1, sm, (CUstream)c->stream, params)
+                       : c->drv.LaunchKernel(L.fn, L.grid, 1, 1, L.block, 1, 1, sm, (CUstream)c->stream, params, nullptr);
   if (cr != CUDA_SUCCESS) {
     const char* es = nullptr;
     c->drv.GetErrorString(cr, &es);
@@ -959,7 +974,7 @@ int flush_batch(dfs_ctx* c) {
       if (!ok) return fail(c, DFS_ERR_COMPILE, err);
       return fail(c, DFS_ERR_NO_DEVICE, "analysis-only context: batched kernel compiled, not launched");
     }
-    ne->k = c->jit->get(ne->code.source, ne->code.name, spec.block, err);
+    ne->k = c->jit->get(ne->code.source, ne->code.name, spec.block, err, ne->code.dyn_smem);
     if (!ne->k) {
       release_window(c);
       return fail(c, DFS_ERR_COMPILE, err);
@@ -1077,6 +1092,7 @@ int flush_batch(dfs_ctx* c) {
   L.fn = be->k->fn;
   L.grid = grid;
   L.block = spec.block;
+  L.dyn_smem = be->k->dyn_smem;
   L.coop = coop;
   L.nbarriers = bc.nbarriers;
   L.ninst = K;
@@ -1636,6 +1652,8 @@ static int check_device_error(dfs_ctx* c) {
   if (h.err != 0) {
     cudaMemset(c->ctl, 0, sizeof(Ctl));
     cudaDeviceSynchronize();
+    if (h.err == 2)
+      return fail(c, DFS_ERR_BARRIER_TIMEOUT, "a staged SpMV copy of x did not complete in time");
     return fail(c, DFS_ERR_BARRIER_TIMEOUT, "a grid barrier timed out (barrier " + std::to_string(h.err_where) + ")");
   }
   return DFS_OK;

@@ -190,6 +190,7 @@ struct KernelCode {
   std::vector<std::pair<int, int>> imm_src;  // (task, arg) of each immediate param
   std::vector<int64_t> ptr_roots;   // root handle of each pointer param
   size_t partial_bytes = 0;
+  int dyn_smem = 0;                 // dynamic shared memory per CTA (staged SpMV x windows)
 };
 
 KernelCode generate(const LaunchSpec& spec);
@@ -241,6 +242,7 @@ struct BatchCode {
   };
   std::vector<VSrc> v_src;
   std::vector<int> prefix_task;                // first task of the group each prefix array serves
+  int dyn_smem = 0;                            // dynamic shared memory per CTA (staged SpMV x windows)
 };
 
 // Lanes per row of the warp-cooperative SpMV (spmv_warp) for a CSR matrix

@@ -564,3 +564,108 @@ def test_template_recording_refuses_what_a_replay_cannot_repeat():
     with pytest.raises(B.DfsError) as e:
         B.dfs_template_end(rt.ctx)               # not recording any more
     assert e.value.code == -7
+
+
+# ------------------------------------------------- staged SpMV x windows
+def _fake_csr(rt, m, tile, dtype=np.float64, windows=True):
+    """A CSR of the 2-D Poisson pattern in an analysis-only context (stores
+    without data), with a window store for `tile` when asked."""
+    Am = A.CSR.__new__(A.CSR)
+    Am.rt, Am.nrows, Am.ncols, Am.nnz = rt, m * m, m * m, 5 * m * m - 4 * m
+    Am.rowptr = rt.empty((m * m + 1,), np.int32)
+    Am.col = rt.empty((Am.nnz,), np.int32)
+    Am.val = rt.empty((Am.nnz,), dtype)
+    Am.dtype = np.dtype(dtype)
+    Am._host = None
+    npts = -(-m * m // tile)
+    Am._win = {tile: rt.empty((6 * npts,), np.int32)} if windows else {}
+    return Am
+
+
+def test_staged_spmv_kernels_compile():
+    rt = rt0(tile=512)
+    Am = _fake_csr(rt, 40, 512)
+    s = W.CGInPlace(*(rt.empty((1600,)) for _ in range(4)), rt.empty(()))
+    W.cg_iteration_inplace(Am, s)
+    with pytest.raises(B.DfsError) as e:
+        rt.flush()
+    assert e.value.code == -2
+    src = rt.kernel_source()
+    assert "xstage<double>" in src and "spmv_row_xs<double>" in src and "dfs_xs_raw" in src
+    # batched: instances of different sizes, each with its own windows
+    probs = []
+    for m in (40, 33):
+        Am = _fake_csr(rt, m, 512, np.float32)
+        probs.append((Am, W.CGInPlace(*(rt.empty((m * m,), np.float32) for _ in range(4)),
+                                      rt.empty((), np.float32))))
+    with pytest.raises(B.DfsError) as e:
+        W.batched_cg_iteration(rt, probs)
+    assert e.value.code == -2 and "batched kernel compiled" in str(e.value)
+    src = rt.kernel_source()
+    assert "xstage<float>" in src and "spmv_row_xs<float>" in src and "find_inst" in src
+
+
+def test_spmv_window_argument_is_validated():
+    rt = rt0(tile=256)
+    n = 1000
+    rp, col = rt.empty((n + 1,), np.int32), rt.empty((5 * n,), np.int32)
+    val, x, y = rt.empty((5 * n,)), rt.empty((n,)), rt.empty((n,))
+    dom, part = rt.layout((n,))
+    none = rt.none
+
+    def submit(win, wpart, priv=B.DFS_PRIV_R):
+        args = [(a.handle, none, B.DFS_PRIV_R) for a in (rp, col, val, x)]
+        args += [(y.handle, part, B.DFS_PRIV_W), (win.handle, wpart, priv)]
+        rt.submit("SPMV", dom, args)
+
+    good = rt.empty((6 * dom[0],), np.int32)
+    submit(good, rt.tiling((6,)))                     # accepted
+    with pytest.raises(B.DfsError):
+        submit(rt.empty((6 * dom[0],), np.int64), rt.tiling((6,)))      # not int32
+    with pytest.raises(B.DfsError):
+        submit(good, rt.tiling((4,)))                                   # records of 6
+    with pytest.raises(B.DfsError):
+        submit(rt.empty((6 * dom[0] - 6,), np.int32), rt.tiling((6,)))  # one record short
+    with pytest.raises(B.DfsError):
+        submit(good, rt.tiling((6,)), B.DFS_PRIV_RW)                    # read only
+
+
+@pytest.mark.parametrize("kind", ["poisson2d", "poisson3d", "spd"])
+@pytest.mark.parametrize("elem", [4, 8])
+def test_spmv_windows_cover_the_rows(kind, elem):
+    """dfs_spmv_windows against brute force: records are 16-byte aligned,
+    inside the aligned part of x, within the budget, at most three disjoint
+    intervals, and cover every column the point's rows read below that
+    aligned end (or the point is not staged at all)."""
+    from synth import inputs
+    rp, col, _ = {"poisson2d": lambda: inputs.poisson2d_csr(45), "poisson3d": lambda: inputs.poisson3d_csr(13),
+                  "spd": lambda: inputs.random_spd_csr(3000, seed=3)}[kind]()
+    n = len(rp) - 1
+    q = 16 // elem
+    end_al = n // q * q
+    for tile, budget in ((256, B.SPMV_STAGE_BYTES), (700, B.SPMV_STAGE_BYTES), (512, 4096)):
+        rec = B.dfs_spmv_windows(rp, col, n, tile, elem, budget).reshape(-1, 6)
+        assert len(rec) == -(-n // tile)
+        staged = 0
+        for p, r in enumerate(rec):
+            lo, ln = r[0::2], r[1::2]
+            if ln.sum() == 0:
+                continue
+            staged += 1
+            assert ln.sum() * elem <= budget
+            ivs = sorted((int(a), int(a) + int(b)) for a, b in zip(lo, ln) if b > 0)
+            for a, b in ivs:
+                assert a % q == 0 and (b - a) % q == 0 and 0 <= a < b <= end_al
+            for (a0, b0), (a1, b1) in zip(ivs, ivs[1:]):
+                assert b0 <= a1
+            cols = np.unique(col[rp[p * tile]:rp[min((p + 1) * tile, n)]])
+            inside = np.zeros(len(cols), bool)
+            for a, b in ivs:
+                inside |= (cols >= a) & (cols < b)
+            assert inside[cols < end_al].all(), (p, tile)
+        if kind != "spd" and budget == B.SPMV_STAGE_BYTES:
+            assert staged == len(rec)                   # banded rows: every point fits
+    with pytest.raises(B.DfsError):
+        B.dfs_spmv_windows(rp, col, n, 0, elem)        # no tile
+    with pytest.raises(B.DfsError):
+        B.dfs_spmv_windows(rp, col, n, 256, 2)         # element size
