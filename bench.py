@@ -795,6 +795,10 @@ def measure(args, workload, env, steps, warmup, cpu_budget=(10.0, 8.0)) -> dict:
     for k in ("block", "unroll", "tile", "rows"):       # command-line overrides (tuning)
         if getattr(args, k):
             base[k] = getattr(args, k)
+    if "ctas_per_sm" in cfg:
+        base["ctas_per_sm"] = cfg["ctas_per_sm"]
+    if args.ctas >= 0:
+        base["ctas_per_sm"] = args.ctas
     if "stage_x" in cfg:
         base["stage_x"] = cfg["stage_x"]
     if args.stage_x:
@@ -1057,6 +1061,7 @@ def main():
     for k in ("block", "unroll", "tile", "rows"):
         ap.add_argument(f"--{k}", type=int, default=0, help=f"override the workload's {k} (tuning)")
     ap.add_argument("--ipf", type=int, default=0, help="CG: iterations per flush window (tuning)")
+    ap.add_argument("--ctas", type=int, default=-1, help="resident CTAs per SM to size for (tuning; 0 = as many as fit)")
     ap.add_argument("--e2e-chunk", type=int, default=0, help="Black-Scholes end to end: options per chunk (tuning)")
     ap.add_argument("--e2e-contexts", type=int, default=0, help="Black-Scholes end to end: streams (tuning)")
     ap.add_argument("--e2e-mode", default="", choices=["", "zero_copy", "pipeline"],

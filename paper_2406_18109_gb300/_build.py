@@ -108,7 +108,7 @@ def _build_locked(force: bool, verbose: bool) -> str:
     tmp = LIB + ".tmp"
     run([nvcc, "-shared", "-gencode", GENCODE, "-o", tmp, *objs, "-cudart", "static",
          "-L", os.path.join(cuda, "lib64"), "-lnvrtc",
-         "-Xlinker", "-rpath," + os.path.join(cuda, "lib64")])
+         "-Xlinker", "-rpath," + os.path.join(cuda, "lib64"), "-Xlinker", "--no-undefined"])
     os.replace(tmp, LIB)
     with open(stamp, "w") as f:
         f.write(digest)

@@ -135,6 +135,9 @@ class Gen {
   void emit_scalar_group(int g);
   void emit_vector_group(int g);
   void emit_nest(int g, const Nest& n, const std::string& red_pt, bool flat);
+  // Which tasks of nest n run two lanes per instruction in a body of w lanes
+  // (index: task - n.first).
+  std::vector<char> packed_tasks(const Nest& n, int w) const;
   void emit_finalise(const char* indent);
   int emit_warp0_scalars(int g);
   void realign(Nest& n, int vec);
@@ -415,6 +418,49 @@ void Gen::emit_vector_group(int g) {
   o << "    }\n";
 }
 
+// FP32 element-wise ADD, MUL and NCDF tasks run two lanes per instruction
+// (pk_add, pk_mul, pk_ncdf_*) when that cannot change a bit: the compiler
+// contracts a packed product whose value reaches a sum into a fused
+// multiply-add, so a product (MUL, or NCDF, whose last step multiplies),
+// possibly negated or copied on the way, that a sum of the body consumes
+// (ADD, SUB, a SUM reduction) keeps both operations scalar.  Values loaded
+// from memory or computed outside the body are not products of the body.
+std::vector<char> Gen::packed_tasks(const Nest& n, int w) const {
+  std::vector<char> pk(n.last - n.first, 0);
+  if (w < 2 || w % 2) return pk;
+  std::map<std::string, int> product_of;  // akey -> task whose product the value is
+  std::vector<char> blocked(n.last - n.first, 0);
+  for (int i = n.first; i < n.last; ++i) {
+    const Task& t = S.tasks[i];
+    if (t.scalar()) continue;
+    const bool sum = t.op == DFS_OP_ADD || t.op == DFS_OP_SUB || t.op == DFS_OP_SUM;
+    const size_t nin = t.op == DFS_OP_SPMV ? 0 : t.args.size() - 1;
+    int carried = -1;  // a product passed on by NEG or COPY
+    for (size_t ai = 0; ai < nin; ++ai) {
+      const Arg& a = t.args[ai];
+      if (a.imm || a.nd == 0) continue;
+      auto it = product_of.find(akey(a));
+      if (it == product_of.end()) continue;
+      if (sum) {
+        blocked[it->second - n.first] = 1;
+        blocked[i - n.first] = 1;
+      }
+      if (t.op == DFS_OP_NEG || t.op == DFS_OP_COPY) carried = it->second;
+    }
+    if (!is_elementwise(t.op)) continue;
+    const std::string out = akey(t.args.back());
+    product_of.erase(out);
+    if (t.op == DFS_OP_MUL || t.op == DFS_OP_NCDF) product_of[out] = i;
+    else if (carried >= 0) product_of[out] = carried;
+  }
+  for (int i = n.first; i < n.last; ++i) {
+    const Task& t = S.tasks[i];
+    if (t.scalar() || blocked[i - n.first] || space_arg(t).dtype != DFS_F32) continue;
+    pk[i - n.first] = t.op == DFS_OP_ADD || t.op == DFS_OP_MUL || t.op == DFS_OP_NCDF;
+  }
+  return pk;
+}
+
 void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
   const int BD = S.block;
   const int U = std::max(1, S.unroll);
@@ -591,28 +637,57 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
         }
       }
     }
-    // compute: per slot, per lane
+    // compute: per slot, tasks in program order, each over the lanes
+    const std::vector<char> pk = packed_tasks(n, w);
     std::map<std::string, std::vector<std::string>> outvars;  // akey -> per (slot*w+lane) value
     for (int s = 0; s < ns; ++s) {
-      std::map<std::string, std::string> fwd;  // akey -> lane-0 var prefix (per lane suffix)
-      for (int l = 0; l < w; ++l) {
-        std::map<std::string, std::string> cur;  // akey -> value expr for this lane
+      std::vector<std::map<std::string, std::string>> curs(w);  // per lane: akey -> value expr
+      std::vector<LaneOps> lanes(w);
+      for (int l = 0; l < w; ++l)
         for (const Rd& rd : reads) {
           const std::string v = rd.var + "_" + slots[s];
-          cur[rd.key] = (w > 1) ? v + ".v[" + std::to_string(l) + "]" : v;
+          curs[l][rd.key] = (w > 1) ? v + ".v[" + std::to_string(l) + "]" : v;
         }
-        LaneOps lane;
-        for (int i = n.first; i < n.last; ++i) {
-          const Task& t = S.tasks[i];
-          if (t.scalar()) continue;
-          const int dt = space_arg(t).dtype;   // the output's (y for an SpMV, whose last arg may be its windows)
-          auto val = [&](size_t ai) -> std::string {
-            const Arg& a = t.args[ai];
-            if (a.imm) return immv.at({i, (int)ai});
-            if (a.nd == 0) return "(" + T(dt) + ")" + sreg.at(a.root);
-            return cur.at(akey(a));
-          };
-          const std::string res = "v" + std::to_string(i) + "_" + slots[s] + "_" + std::to_string(l);
+      for (int i = n.first; i < n.last; ++i) {
+        const Task& t = S.tasks[i];
+        if (t.scalar()) continue;
+        const int dt = space_arg(t).dtype;   // the output's (y for an SpMV, whose last arg may be its windows)
+        auto res_of = [&](int l) { return "v" + std::to_string(i) + "_" + slots[s] + "_" + std::to_string(l); };
+        auto val_of = [&](int l, size_t ai) -> std::string {
+          const Arg& a = t.args[ai];
+          if (a.imm) return immv.at({i, (int)ai});
+          if (a.nd == 0) return "(" + T(dt) + ")" + sreg.at(a.root);
+          return curs[l].at(akey(a));
+        };
+        if (pk[i - n.first]) {
+          // two lanes per instruction
+          for (int l = 0; l < w; l += 2) {
+            const std::string r0 = res_of(l), r1 = res_of(l + 1), pr = r0 + "_p";
+            if (t.op == DFS_OP_NCDF) {
+              const std::string y = r0 + "_y2";
+              o << pad << "const float2 " << y << " = pk_ncdf_arg(" << val_of(l, 0) << ", " << val_of(l + 1, 0) << ");\n";
+              const std::string m0 = lanes[l].ncdf_mag(o, pad, "float", r0, val_of(l, 0), y + ".x");
+              const std::string m1 = lanes[l + 1].ncdf_mag(o, pad, "float", r1, val_of(l + 1, 0), y + ".y");
+              o << pad << "const float2 " << pr << " = pk_ncdf_of_erf(erf_sign(" << m0 << ", " << y << ".x), erf_sign("
+                << m1 << ", " << y << ".y));\n";
+            } else {
+              lanes[l].define(r0);
+              lanes[l + 1].define(r1);
+              o << pad << "const float2 " << pr << " = " << (t.op == DFS_OP_ADD ? "pk_add(" : "pk_mul(") << val_of(l, 0)
+                << ", " << val_of(l + 1, 0) << ", " << val_of(l, 1) << ", " << val_of(l + 1, 1) << ");\n";
+            }
+            o << pad << "const float " << r0 << " = " << pr << ".x;\n";
+            o << pad << "const float " << r1 << " = " << pr << ".y;\n";
+            curs[l][akey(t.args.back())] = r0;
+            curs[l + 1][akey(t.args.back())] = r1;
+          }
+          continue;
+        }
+        for (int l = 0; l < w; ++l) {
+          auto& cur = curs[l];
+          LaneOps& lane = lanes[l];
+          auto val = [&](size_t ai) { return val_of(l, ai); };
+          const std::string res = res_of(l);
           if (is_elementwise(t.op)) {
             std::vector<std::string> in{val(0)};
             if (t.args.size() == 3) in.push_back(val(1));
@@ -641,7 +716,9 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
               o << pad << ac->var << " = " << ac->var << " + " << val(0) << ";\n";
           }
         }
-        // collect outputs to store
+      }
+      // collect outputs to store
+      for (int l = 0; l < w; ++l)
         for (int i = n.first; i < n.last; ++i) {
           const Task& t = S.tasks[i];
           if (t.scalar()) continue;
@@ -652,9 +729,8 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
           const std::string k = akey(*out);
           auto& vv = outvars[k];
           if (vv.size() < (size_t)(ns * w)) vv.resize(ns * w);
-          vv[s * w + l] = cur.at(k);
+          vv[s * w + l] = curs[l].at(k);
         }
-      }
     }
     // stores (the last value written to each (root, partition) in the nest)
     for (auto& kv : outvars) {
@@ -1034,8 +1110,7 @@ std::string LaneOps::shared(const std::map<std::string, std::string>& m, const s
 
 void LaneOps::emit(std::ostream& o, const std::string& pad, const std::string& T, int op, const std::string& res,
                    const std::vector<std::string>& in) {
-  if (!defined_.insert(res).second)
-    throw std::runtime_error("code generator: value " + res + " defined twice in one loop body");
+  define(res);
   if (op == DFS_OP_ERF) {
     // |-a| = |a| bit for bit, so erf(|a|) serves a and its negation
     std::string m = shared(mag_, in[0]);
@@ -1068,6 +1143,23 @@ void LaneOps::emit(std::ostream& o, const std::string& pad, const std::string& T
     neg_.emplace(res, in[0]);
     neg_.emplace(in[0], res);
   }
+}
+
+std::string LaneOps::ncdf_mag(std::ostream& o, const std::string& pad, const std::string& T, const std::string& res,
+                              const std::string& in0, const std::string& y) {
+  define(res);
+  std::string m = shared(nmag_, in0);
+  if (m.empty()) {
+    m = res + "_m";
+    o << pad << "const " << T << " " << m << " = erf_mag(" << y << ");\n";
+  }
+  nmag_[in0] = m;
+  return m;
+}
+
+void LaneOps::define(const std::string& res) {
+  if (!defined_.insert(res).second)
+    throw std::runtime_error("code generator: value " + res + " defined twice in one loop body");
 }
 
 KernelCode generate(const LaunchSpec& spec) {

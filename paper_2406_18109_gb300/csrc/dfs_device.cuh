@@ -71,6 +71,27 @@ __device__ __forceinline__ double ncdf_of_erf(double e) { return op_mul(0.5, op_
 __device__ __forceinline__ float op_ncdf(float a) { return ncdf_of_erf(op_erf(ncdf_arg(a))); }
 __device__ __forceinline__ double op_ncdf(double a) { return ncdf_of_erf(op_erf(ncdf_arg(a))); }
 
+// Two FP32 lanes per instruction (the packed add and multiply of sm_100 and
+// later): each lane is rounded to nearest exactly as op_add / op_mul round
+// it.  The compiler may contract a packed product whose only use is a packed
+// or scalar sum into one fused multiply-add, whatever rounding the source
+// asks for (measured on GB300), which rounds once where the unfused tasks
+// round twice; so the code generator packs an operation only when no product
+// of the body feeds a sum of the body (add, subtract, SUM reduction).
+__device__ __forceinline__ float2 pk_add(float a0, float a1, float b0, float b1) {
+  return __fadd2_rn(make_float2(a0, a1), make_float2(b0, b1));
+}
+__device__ __forceinline__ float2 pk_mul(float a0, float a1, float b0, float b1) {
+  return __fmul2_rn(make_float2(a0, a1), make_float2(b0, b1));
+}
+// ncdf_arg and ncdf_of_erf of two lanes
+__device__ __forceinline__ float2 pk_ncdf_arg(float a0, float a1) {
+  return __fmul2_rn(make_float2(a0, a1), make_float2(0.70710678118654752440f, 0.70710678118654752440f));
+}
+__device__ __forceinline__ float2 pk_ncdf_of_erf(float e0, float e1) {
+  return __fmul2_rn(make_float2(0.5f, 0.5f), __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(e0, e1)));
+}
+
 // Reduction step and CSR row product: contraction into FMA is intended here
 // (one task's own arithmetic).
 __device__ __forceinline__ float red_fma(float a, float b, float acc) { return fmaf(a, b, acc); }

@@ -216,6 +216,13 @@ class LaneOps {
   // Emits `const T res = op(in...)` (possibly in several statements).
   void emit(std::ostream& o, const std::string& pad, const std::string& T, int op, const std::string& res,
             const std::vector<std::string>& in);
+  // The erf(|x / sqrt 2|) of NCDF task result `res` with argument `in0`,
+  // whose scaled argument is the expression `y` (computed by the caller, for
+  // two lanes at once): shared with a negation's, or emitted; returns its name.
+  std::string ncdf_mag(std::ostream& o, const std::string& pad, const std::string& T, const std::string& res,
+                       const std::string& in0, const std::string& y);
+  // Registers `res` as defined by the caller (an operation it emitted itself).
+  void define(const std::string& res);
 
  private:
   std::string shared(const std::map<std::string, std::string>& m, const std::string& a) const;

@@ -354,6 +354,52 @@ def test_erf_of_a_value_and_its_negation(dtype):
         assert ok.all(), (s, x[~ok], outs["persistent"][s][~ok], m.arrays[s][~ok])
 
 
+def test_packed_lanes_never_contract_a_product_into_a_sum():
+    """FP32 bodies run some tasks two lanes per instruction; a packed product
+    that reaches a sum would be contracted into one fused multiply-add by the
+    compiler.  Products that feed sums directly, through NEG or COPY, or
+    through a SUM reduction stay scalar, the rest is packed, and every store
+    equals the unfused tasks bit for bit."""
+    n, tile = 8195, 1024
+    dom = ((n + tile - 1) // tile,)
+    a, b, d = (inputs.uniform(40 + k, -2.0, 2.0, n, np.float32) for k in range(3))
+    stream = [("MUL", 3, [0, 1]), ("ADD", 4, [3, 2]),          # a*b + d: scalar pair
+              ("MUL", 5, [0, 2]), ("NEG", 6, [5]), ("SUB", 7, [2, 6]),   # d - (-(a*d)): scalar, through NEG
+              ("MUL", 8, [1, 2]), ("MUL", 9, [8, 1.5]),      # product of a product: packed
+              ("ADD", 10, [0, 2]), ("MUL", 11, [10, 0.25]),  # (a+d)*0.25: packed
+              ("NCDF", 12, [0]), ("ADD", 13, [12, 1.0])]     # N(a) + 1: scalar (NCDF ends with a multiply)
+    nst = 14
+    outs, srcs = {}, {}
+    for mode in MODES:
+        with gpu_runtime(mode, tile=tile) as rt:
+            arrs = [rt.array(x) for x in (a, b, d)] + [rt.array(np.zeros(n, np.float32)) for _ in range(3, nst)]
+            for op, o, ins in stream:
+                opnds = [arrs[i]._arg(B.DFS_PRIV_R) if isinstance(i, int) else i for i in ins]
+                rt.submit(op, dom, opnds + [arrs[o]._arg(B.DFS_PRIV_W)])
+            outs[mode] = [x.numpy() for x in arrs]
+            srcs[mode] = rt.kernel_source()
+    for mode in MODES[1:]:
+        for s in range(nst):
+            assert np.array_equal(_bits(outs[mode][s]), _bits(outs["persistent"][s])), (mode, s)
+    src = srcs["persistent"]
+    assert "pk_mul(" in src and "pk_add(" in src
+    for blocked in ("v0_", "v1_", "v2_", "v4_", "v9_", "v10_"):   # tasks kept scalar
+        assert f"const float2 {blocked}" not in src, blocked
+    for packed in ("v5_", "v6_", "v7_", "v8_"):                    # tasks run on lane pairs
+        assert f"const float2 {packed}" in src, packed
+    # and the values are the stored-dtype oracle's (each operation rounded once)
+    m = Machine("stored")
+    P = Tiling((tile,), (0,), IDENTITY, ((0,), (n,)))
+    for s, x in enumerate((a, b, d)):
+        m.add(s, x)
+    for s in range(3, nst):
+        m.add(s, np.zeros(n, np.float32))
+    for op, o, ins in stream:
+        m.run(XTask(op, dom, [Arg(i, P, "R") if isinstance(i, int) else Imm(i) for i in ins] + [Arg(o, P, "W")]))
+    for s in (3, 4, 5, 6, 7, 8, 9, 10, 11):
+        assert np.array_equal(_bits(outs["persistent"][s]), _bits(m.arrays[s])), s
+
+
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
 def test_erf_sharing_after_a_rewrite_in_the_window(dtype):
     """A value and its negation stop being negations once either store is
