@@ -403,8 +403,6 @@ class Arm:
             self._tune(window, {"tile": [256, 432, 512, 864, 1024, 2048], "block": [128, 256, 512], "unroll": [1, 2]},
                        f"cg-{cfg['m']}-{ipf}", 5, "ms_per_window")
         window()
-        window()                                    # a steady window (the first also holds the start tasks)
-        self.kernel_name = kernel_name_of(rt)       # the iteration window's kernel (replayed below)
         rt.capture_begin()
         W.cg_reset_inplace(self.s, self.b)
         rt.flush()
@@ -413,6 +411,7 @@ class Arm:
             if (it + 1) % ipf == 0 or it + 1 == cfg["iters"]:
                 rt.flush()
         self.graph = rt.capture_end()
+        self.kernel_name = kernel_name_of(rt)       # the last iteration window the graph replays
         self.step = self._cg_graph
         if self.e2e:
             # end to end: b uploaded from pinned host memory, x read back, every step
@@ -469,12 +468,12 @@ class Arm:
         # one normal pass of each window (compiles kernels, uploads descriptors), then capture
         reset()
         one_iteration()
-        self.kernel_name = kernel_name_of(rt)       # the batched iteration's kernel (replayed below)
         rt.capture_begin()
         reset()
         for _ in range(cfg["iters"]):
             one_iteration()
         self.graph = rt.capture_end()
+        self.kernel_name = kernel_name_of(rt)       # the last batched iteration the graph replays
         self.units = cfg["count"] * cfg["iters"]
         self.step = self._cg_graph
         if self.e2e:
