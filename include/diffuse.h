@@ -85,8 +85,10 @@ typedef enum { DFS_REDOP_NONE = 0, DFS_REDOP_SUM = 1 } dfs_redop;
  *     Rounding: every operation rounds once to the store dtype (no
  *     contraction across operations), so a fused window equals the unfused
  *     stream bit for bit.
- *     ERF(x) = copysign(erf(|x|), x): the odd extension of the CUDA math
- *     library's erf on [0, inf], so ERF(-x) = -ERF(x) bit for bit.
+ *     ERF(x) = copysign(erf(|x|), x): the odd extension of an erf on
+ *     [0, inf], so ERF(-x) = -ERF(x) bit for bit.  FP64 uses the CUDA math
+ *     library's erf; FP32 uses this library's own approximation, within
+ *     2 ulp of erf (the bound CUDA documents for erff).
  *     NCDF(x) = 0.5 * (1 + ERF(x * (1/sqrt 2))), evaluated in that order.
  *   DFS_OP_DOT  [x R, y R, out RD(SUM)]   out (+)= sum_e x[e]*y[e]
  *   DFS_OP_SUM  [x R, out RD(SUM)]        out (+)= sum_e x[e]

@@ -456,7 +456,7 @@ std::vector<char> Gen::packed_tasks(const Nest& n, int w) const {
   for (int i = n.first; i < n.last; ++i) {
     const Task& t = S.tasks[i];
     if (t.scalar() || blocked[i - n.first] || space_arg(t).dtype != DFS_F32) continue;
-    pk[i - n.first] = t.op == DFS_OP_ADD || t.op == DFS_OP_MUL || t.op == DFS_OP_NCDF;
+    pk[i - n.first] = t.op == DFS_OP_ADD || t.op == DFS_OP_MUL || t.op == DFS_OP_NCDF || t.op == DFS_OP_ERF;
   }
   return pk;
 }
@@ -663,13 +663,43 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
           // two lanes per instruction
           for (int l = 0; l < w; l += 2) {
             const std::string r0 = res_of(l), r1 = res_of(l + 1), pr = r0 + "_p";
-            if (t.op == DFS_OP_NCDF) {
-              const std::string y = r0 + "_y2";
-              o << pad << "const float2 " << y << " = pk_ncdf_arg(" << val_of(l, 0) << ", " << val_of(l + 1, 0) << ");\n";
-              const std::string m0 = lanes[l].ncdf_mag(o, pad, "float", r0, val_of(l, 0), y + ".x");
-              const std::string m1 = lanes[l + 1].ncdf_mag(o, pad, "float", r1, val_of(l + 1, 0), y + ".y");
-              o << pad << "const float2 " << pr << " = pk_ncdf_of_erf(erf_sign(" << m0 << ", " << y << ".x), erf_sign("
-                << m1 << ", " << y << ".y));\n";
+            if (t.op == DFS_OP_NCDF || t.op == DFS_OP_ERF) {
+              lanes[l].define(r0);
+              lanes[l + 1].define(r1);
+              const std::string a0 = val_of(l, 0), a1 = val_of(l + 1, 0);
+              // the argument of erf: x / sqrt 2 for NCDF, x itself for ERF
+              std::string y0 = a0, y1 = a1;
+              if (t.op == DFS_OP_NCDF) {
+                const std::string y = r0 + "_y2";
+                o << pad << "const float2 " << y << " = pk_ncdf_arg(" << a0 << ", " << a1 << ");\n";
+                y0 = y + ".x";
+                y1 = y + ".y";
+              }
+              // erf(|y|) of both lanes in one packed evaluation, unless the
+              // lanes reuse the magnitude of a negation (both do, or neither)
+              std::string m0 = lanes[l].mag_of(t.op, a0), m1 = lanes[l + 1].mag_of(t.op, a1);
+              if (m0.empty() && m1.empty()) {
+                o << pad << "const float2 " << r0 << "_m2 = erf_mag2(" << y0 << ", " << y1 << ");\n";
+                m0 = r0 + "_m2.x";
+                m1 = r0 + "_m2.y";
+              } else {
+                if (m0.empty()) {
+                  m0 = r0 + "_m";
+                  o << pad << "const float " << m0 << " = erf_mag(" << y0 << ");\n";
+                }
+                if (m1.empty()) {
+                  m1 = r1 + "_m";
+                  o << pad << "const float " << m1 << " = erf_mag(" << y1 << ");\n";
+                }
+              }
+              lanes[l].set_mag(t.op, a0, m0);
+              lanes[l + 1].set_mag(t.op, a1, m1);
+              if (t.op == DFS_OP_NCDF)
+                o << pad << "const float2 " << pr << " = pk_ncdf_of_erf(erf_sign(" << m0 << ", " << y0 << "), erf_sign("
+                  << m1 << ", " << y1 << "));\n";
+              else
+                o << pad << "const float2 " << pr << " = make_float2(erf_sign(" << m0 << ", " << y0 << "), erf_sign("
+                  << m1 << ", " << y1 << "));\n";
             } else {
               lanes[l].define(r0);
               lanes[l + 1].define(r1);
@@ -1145,16 +1175,12 @@ void LaneOps::emit(std::ostream& o, const std::string& pad, const std::string& T
   }
 }
 
-std::string LaneOps::ncdf_mag(std::ostream& o, const std::string& pad, const std::string& T, const std::string& res,
-                              const std::string& in0, const std::string& y) {
-  define(res);
-  std::string m = shared(nmag_, in0);
-  if (m.empty()) {
-    m = res + "_m";
-    o << pad << "const " << T << " " << m << " = erf_mag(" << y << ");\n";
-  }
-  nmag_[in0] = m;
-  return m;
+std::string LaneOps::mag_of(int op, const std::string& in0) const {
+  return shared(op == DFS_OP_NCDF ? nmag_ : mag_, in0);
+}
+
+void LaneOps::set_mag(int op, const std::string& in0, const std::string& m) {
+  (op == DFS_OP_NCDF ? nmag_ : mag_)[in0] = m;
 }
 
 void LaneOps::define(const std::string& res) {

@@ -216,11 +216,11 @@ class LaneOps {
   // Emits `const T res = op(in...)` (possibly in several statements).
   void emit(std::ostream& o, const std::string& pad, const std::string& T, int op, const std::string& res,
             const std::vector<std::string>& in);
-  // The erf(|x / sqrt 2|) of NCDF task result `res` with argument `in0`,
-  // whose scaled argument is the expression `y` (computed by the caller, for
-  // two lanes at once): shared with a negation's, or emitted; returns its name.
-  std::string ncdf_mag(std::ostream& o, const std::string& pad, const std::string& T, const std::string& res,
-                       const std::string& in0, const std::string& y);
+  // For callers that evaluate ERF or NCDF on two lanes at once: the name of
+  // an erf magnitude this lane already has for argument in0 (or for its
+  // negation), empty if none; and the record of the one the caller computed.
+  std::string mag_of(int op, const std::string& in0) const;
+  void set_mag(int op, const std::string& in0, const std::string& m);
   // Registers `res` as defined by the caller (an operation it emitted itself).
   void define(const std::string& res);
 
