@@ -357,6 +357,23 @@ class Arm:
         self.dS, self.dK, self.dT = self.rt.array(S), self.rt.array(K), self.rt.array(T)
         self.units = n
         self.step = self._bs
+        if not self.e2e and self.graph_mode:
+            # the batch's window (23 tasks, stores into call and put) issued
+            # once, then captured once and replayed per step, as a pricing
+            # loop over resident data would run it
+            rt = self.rt
+            self.dcall = rt.empty((n,), np.float32)
+            self.dput = rt.empty((n,), np.float32)
+
+            def window():
+                W.black_scholes(self.dS, self.dK, self.dT, cfg["r"], cfg["sigma"], out=(self.dcall, self.dput))
+                rt.flush()
+            window()
+            rt.capture_begin()
+            window()
+            self.graph = rt.capture_end()
+            self.kernel_name = kernel_name_of(rt)
+            self.step = self._cg_graph
         if not self.e2e:
             return
         # end to end: S, K, T from pinned host memory, call and put back to it
@@ -805,7 +822,7 @@ def measure(args, workload, env, steps, warmup, cpu_budget=(10.0, 8.0)) -> dict:
 
     # CG: the iteration windows are captured once (memoised windows + a CUDA
     # graph) and replayed; the Python-issued runs are reported beside them
-    graph = workload in ("cg", "batched")
+    graph = workload in ("cg", "batched", "bs")
 
     def arm(kw, steps, warmup, e2e=False, graph=graph, per_solve=False):
         a = Arm(workload, kw, torch, stream, e2e=e2e, graph=graph, per_solve=per_solve)
@@ -844,21 +861,25 @@ def measure(args, workload, env, steps, warmup, cpu_budget=(10.0, 8.0)) -> dict:
         k2 = max(3, steps // 4)
         unf = arm(dict(base, fusion=False, launch="per_task"), k2, 2)
         pt = arm(dict(base, fusion=True, launch="per_task"), k2, 2)
+        def kms(run, k):
+            # summed per-launch device times; launches replayed from a graph
+            # are not timed one by one (null then)
+            t = sum(v["ms"] for v in run["kernels"].values())
+            return t / k if t > 0 else None
         extra["unfused"] = {"value": unf["units"] / (unf["ms"] / 1e3), "ms_per_step": unf["ms"] / k2,
-                            "launches_per_step": unf["launches"] / k2,
-                            "kernel_ms_per_step": sum(v["ms"] for v in unf["kernels"].values()) / k2}
+                            "launches_per_step": unf["launches"] / k2, "kernel_ms_per_step": kms(unf, k2)}
         extra["fused_per_task"] = {"value": pt["units"] / (pt["ms"] / 1e3), "ms_per_step": pt["ms"] / k2,
-                                   "launches_per_step": pt["launches"] / k2,
-                                   "kernel_ms_per_step": sum(v["ms"] for v in pt["kernels"].values()) / k2}
+                                   "launches_per_step": pt["launches"] / k2, "kernel_ms_per_step": kms(pt, k2)}
         extra["fused_vs_unfused"] = value / world / extra["unfused"]["value"]
-        extra["fused_kernel_ms_per_step"] = sum(v["ms"] for v in fused["kernels"].values()) / steps
+        extra["fused_kernel_ms_per_step"] = kms(fused, steps)
         if graph:
             nf = arm(dict(base, fusion=True, launch="persistent"), k2, 2, graph=False)
             nu = arm(dict(base, fusion=False, launch="per_task"), k2, 2, graph=False)
             extra["python_issued"] = {
                 "fused": {"value": nf["units"] / (nf["ms"] / 1e3), "ms_per_step": nf["ms"] / k2},
                 "unfused": {"value": nu["units"] / (nu["ms"] / 1e3), "ms_per_step": nu["ms"] / k2},
-                "note": "each iteration issued from Python (11 tasks + flush); host-bound"}
+                "note": ("each batch issued from Python (23 tasks + flush)" if workload == "bs" else
+                         "each iteration issued from Python (11 tasks + flush); host-bound")}
     if not args.quick:
         # end to end through the public API: inputs from pinned host memory
         # and results back to it inside every timed step
@@ -899,10 +920,12 @@ def measure(args, workload, env, steps, warmup, cpu_budget=(10.0, 8.0)) -> dict:
     if graph:
         # launches replayed from a graph are not timed one by one: use the
         # replayed time per iteration (kernel plus the gap to the next node)
-        kern_ms = fused["ms"] / (steps * cfg["iters"])
-        fused["dominant"] = ("batched CG iteration kernel" if workload == "batched" else
-                             "CG iteration kernel") + ", graph replay (time per iteration incl. launch gap)"
-        fused["dominant_launches"] = steps * cfg["iters"]
+        its = cfg.get("iters", 1)
+        kern_ms = fused["ms"] / (steps * its)
+        fused["dominant"] = {"batched": "batched CG iteration kernel", "cg": "CG iteration kernel",
+                             "bs": "fused Black-Scholes kernel"}[workload] + \
+            ", graph replay (time per launch incl. the gap to the next)"
+        fused["dominant_launches"] = steps * its
     achieved = alg_bytes / (kern_ms / 1e3) / 1e9 if kern_ms > 0 else 0.0
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": None,
@@ -943,7 +966,7 @@ def measure(args, workload, env, steps, warmup, cpu_budget=(10.0, 8.0)) -> dict:
         peak_ti = sms * 4 * 32 * sm_max * 1e6 / 1e12
         # the instruction count and DRAM traffic (ncu) belong to one generated
         # kernel: used only when that kernel is the one timed now, else null
-        ctr = counters_for(cfg, fused["dominant"]) if cfg["n"] == 1 << 26 else None
+        ctr = counters_for(cfg, fused_arm.kernel_name or fused["dominant"]) if cfg["n"] == 1 << 26 else None
         hbm = {"achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                "peak_source": peaks["source"], "algorithmic_bytes_per_launch": alg_bytes}
         if ctr:
@@ -954,7 +977,7 @@ def measure(args, workload, env, steps, warmup, cpu_budget=(10.0, 8.0)) -> dict:
                         "inst_per_option": ctr["inst_per_option"], "hbm": hbm}
         else:
             roofline = dict(hbm, bound="hbm", traffic=None, inst_per_option=None)
-        roofline.update({"kernel": fused["dominant"], "kernel_name": fused["dominant"],
+        roofline.update({"kernel": fused["dominant"], "kernel_name": fused_arm.kernel_name or fused["dominant"],
                          "counters_kernel": counters_kernels(cfg), "kernel_ms": kern_ms,
                          "launches": fused["dominant_launches"]})
 
@@ -973,8 +996,10 @@ def measure(args, workload, env, steps, warmup, cpu_budget=(10.0, 8.0)) -> dict:
             "config": {"workload": WORKLOAD[workload],
                        "l2": "inputs larger than L2" if workload != "cg"
                        else "working set L2-resident (10 MB); no flush",
-                       "launch": "persistent fused" + (", each solve replayed from a CUDA graph of the memoised "
-                                                        "iteration windows" if graph else ""),
+                       "launch": "persistent fused" + ((", each batch replayed from a CUDA graph of the memoised "
+                                                         "window" if workload == "bs" else
+                                                         ", each solve replayed from a CUDA graph of the memoised "
+                                                         "iteration windows") if graph else ""),
                        "parallelism": f"replicas x{world}"},
             "e2e": extra.pop("e2e", None), "gpu_launches": fused["launches"], "roofline": roofline,
             "step_ms": fused["step_ms"],

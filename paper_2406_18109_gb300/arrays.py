@@ -530,6 +530,11 @@ def erf(x): return _unary(7, x, x)
 def absolute(x): return _unary(3, x, x)
 def ncdf(x): return _unary(8, x, x)
 def copy(x): return _unary(1, x, x)
+def subtract(a, b, out: Array | None = None):
+    """a - b, into `out` when given (as numpy.subtract(a, b, out=...))."""
+    return _binary(33, a, b, a if isinstance(a, Array) else b, out=out)
+
+
 def maximum(a, b): return _binary(37, a, b, a if isinstance(a, Array) else b)
 def minimum(a, b): return _binary(38, a, b, a if isinstance(a, Array) else b)
 

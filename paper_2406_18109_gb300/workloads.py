@@ -29,8 +29,9 @@ CG_TASKS_PER_ITERATION = 11
 JACOBI_TASKS_PER_SWEEP = 6
 
 
-def black_scholes(S: Array, K: Array, T: Array, r: float, sigma: float):
-    """European call and put under Black-Scholes, N(x) = 0.5 (1 + erf(x/sqrt 2))."""
+def black_scholes(S: Array, K: Array, T: Array, r: float, sigma: float, out=None):
+    """European call and put under Black-Scholes, N(x) = 0.5 (1 + erf(x/sqrt 2)).
+    out: optional (call, put) stores the last two tasks write into."""
     mu = r + 0.5 * sigma * sigma
     t1 = S / K
     t2 = A.log(t1)
@@ -47,14 +48,14 @@ def black_scholes(S: Array, K: Array, T: Array, r: float, sigma: float):
     n2 = A.ncdf(d2)
     c1 = S * n1
     c2 = kd * n2
-    call = c1 - c2
+    call = A.subtract(c1, c2, out=out[0] if out else None)
     m1 = -d1
     nm1 = A.ncdf(m1)
     m2 = -d2
     nm2 = A.ncdf(m2)
     p1 = kd * nm2
     p2 = S * nm1
-    put = p1 - p2
+    put = A.subtract(p1, p2, out=out[1] if out else None)
     return call, put
 
 
