@@ -25,7 +25,7 @@ CG = dict(m=256, iters=50, seed=0, tile=512, block=256, unroll=2, iters_per_flus
           # ncu counters of the steady five-iteration window kernel named
           # `kernel` (this launch shape): DRAM bytes per iteration; the rest of
           # the traffic is served by L2 (profiles/)
-          counters=dict(kernel="dfs_k0ee0e6ccc94c32d2", dram_bytes_per_iteration=5.865984e6 / 5))
+          counters=dict(kernel="dfs_kf956504968f200ce", dram_bytes_per_iteration=5.865472e6 / 5))
 
 # Batched CG: 256 independent solves of uneven size (half 2-D Poisson with m
 # log-uniform in [32, 1024], half random diagonally dominant SPD with n
