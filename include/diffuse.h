@@ -89,6 +89,9 @@ typedef enum { DFS_REDOP_NONE = 0, DFS_REDOP_SUM = 1 } dfs_redop;
  *     [0, inf], so ERF(-x) = -ERF(x) bit for bit.  FP64 uses the CUDA math
  *     library's erf; FP32 uses this library's own approximation, within
  *     2 ulp of erf (the bound CUDA documents for erff).
+ *     LOG(x): FP64 uses the CUDA math library's log; FP32 uses this
+ *     library's own approximation, within 1 ulp of log (the bound CUDA
+ *     documents for logf), with the IEEE results at 0, below 0, inf and NaN.
  *     NCDF(x) = 0.5 * (1 + ERF(x * (1/sqrt 2))), evaluated in that order.
  *   DFS_OP_DOT  [x R, y R, out RD(SUM)]   out (+)= sum_e x[e]*y[e]
  *   DFS_OP_SUM  [x R, out RD(SUM)]        out (+)= sum_e x[e]

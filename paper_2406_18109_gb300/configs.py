@@ -12,8 +12,8 @@ BLACK_SCHOLES = dict(n=1 << 26, seed=1, r=0.02, sigma=0.3, tile=16384, block=512
                      # thread instructions per option (smsp__inst_executed x 32
                      # / options; the kernel is bound by instruction issue) and
                      # DRAM bytes (read + write) of one launch at n = 2^26
-                     counters=dict(kernel="dfs_k21e80501a43df9ae", inst_per_option=117.51,
-                                   dram_bytes_per_launch=1305.36e6),
+                     counters=dict(kernel="dfs_k7ba08b70d2427287", inst_per_option=110.89,
+                                   dram_bytes_per_launch=1304.48e6),
                      # end to end (host arrays): kernels on mapped host memory
                      # ("zero_copy") or copies pipelined in chunks over contexts
                      e2e_mode="zero_copy", e2e_chunk=1 << 23, e2e_contexts=2)

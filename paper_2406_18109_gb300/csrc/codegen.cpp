@@ -418,13 +418,16 @@ void Gen::emit_vector_group(int g) {
   o << "    }\n";
 }
 
-// FP32 element-wise ADD, MUL and NCDF tasks run two lanes per instruction
-// (pk_add, pk_mul, pk_ncdf_*) when that cannot change a bit: the compiler
-// contracts a packed product whose value reaches a sum into a fused
-// multiply-add, so a product (MUL, or NCDF, whose last step multiplies),
-// possibly negated or copied on the way, that a sum of the body consumes
-// (ADD, SUB, a SUM reduction) keeps both operations scalar.  Values loaded
-// from memory or computed outside the body are not products of the body.
+// FP32 element-wise ADD, MUL, NCDF, ERF and LOG tasks run two lanes per
+// instruction (pk_add, pk_mul, pk_ncdf_*, erf_mag2, log_f32x2) when that
+// cannot change a bit.  The compiler contracts a packed product whose value
+// reaches a sum into a fused multiply-add, so a product (MUL, or NCDF, whose
+// last step multiplies), possibly negated or copied on the way, that a sum of
+// the body consumes (ADD, SUB, a SUM reduction) keeps both operations scalar.
+// ERF and LOG are neither products nor sums (inside, their products reach
+// sums only through explicit fused multiply-adds), so they always pair up.
+// Values loaded from memory or computed outside the body are not products of
+// the body.
 std::vector<char> Gen::packed_tasks(const Nest& n, int w) const {
   std::vector<char> pk(n.last - n.first, 0);
   if (w < 2 || w % 2) return pk;
@@ -456,7 +459,8 @@ std::vector<char> Gen::packed_tasks(const Nest& n, int w) const {
   for (int i = n.first; i < n.last; ++i) {
     const Task& t = S.tasks[i];
     if (t.scalar() || blocked[i - n.first] || space_arg(t).dtype != DFS_F32) continue;
-    pk[i - n.first] = t.op == DFS_OP_ADD || t.op == DFS_OP_MUL || t.op == DFS_OP_NCDF || t.op == DFS_OP_ERF;
+    pk[i - n.first] = t.op == DFS_OP_ADD || t.op == DFS_OP_MUL || t.op == DFS_OP_NCDF || t.op == DFS_OP_ERF ||
+                      t.op == DFS_OP_LOG;
   }
   return pk;
 }
@@ -700,6 +704,10 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
               else
                 o << pad << "const float2 " << pr << " = make_float2(erf_sign(" << m0 << ", " << y0 << "), erf_sign("
                   << m1 << ", " << y1 << "));\n";
+            } else if (t.op == DFS_OP_LOG) {
+              lanes[l].define(r0);
+              lanes[l + 1].define(r1);
+              o << pad << "const float2 " << pr << " = log_f32x2(" << val_of(l, 0) << ", " << val_of(l + 1, 0) << ");\n";
             } else {
               lanes[l].define(r0);
               lanes[l + 1].define(r1);

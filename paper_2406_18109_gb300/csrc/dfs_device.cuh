@@ -12,10 +12,10 @@
 // explicitly rounded intrinsics (__fadd_rn, __dmul_rn, ...).  The compiler
 // never contracts those into FMAs, so a fused kernel computes exactly what
 // the unfused kernels compute through memory.  Library math functions
-// (expf, logf, erff, ...) are called, never re-implemented.
+// (expf, powf, erf, ...) are called, never re-implemented.
 //
-// The one exception is the FP32 erf (erf_mag below), this library's own
-// approximation with a stated error bound.
+// The exceptions are the FP32 erf (erf_mag) and the FP32 log (log_f32), this
+// library's own approximations with stated error bounds.
 //
 // This file is embedded in the library and handed to NVRTC; it is also
 // compiled by nvcc at build time as a syntax and target check.
@@ -51,7 +51,6 @@ __device__ __forceinline__ float op_abs(float a) { return fabsf(a); }
 __device__ __forceinline__ double op_abs(double a) { return fabs(a); }
 __device__ __forceinline__ float op_exp(float a) { return expf(a); }
 __device__ __forceinline__ double op_exp(double a) { return exp(a); }
-__device__ __forceinline__ float op_log(float a) { return logf(a); }
 __device__ __forceinline__ double op_log(double a) { return log(a); }
 __device__ __forceinline__ float op_sqrt(float a) { return __fsqrt_rn(a); }
 __device__ __forceinline__ double op_sqrt(double a) { return __dsqrt_rn(a); }
@@ -140,6 +139,90 @@ __device__ __forceinline__ float2 erf_mag2(float a0, float a1) {
   r.y = x.y >= 3.92f ? 1.0f : (x.y < 1.0f ? ra.y : rb.y);
   return r;
 }
+// log(a) in FP32, this library's own approximation, written from the
+// mathematics (coefficients fitted by csrc/log_f32_fit.py, weighted least
+// squares on Chebyshev nodes against 40-digit log1p):
+//   a = 2^k m with m in [sqrt(1/2), sqrt(2)), read from the bits of a
+//   f = m - 1                      (exact: m lies within a factor 2 of 1)
+//   log(m) = f + f^2 Q(f)          Q of degree 8 fitted to (log1p(f) - f) / f^2,
+//                                  weighted by |f| (the error that reaches log)
+//   log(a) = k ln2_hi + (k ln2_lo + log(m)), ln2 split so that k ln2_hi is exact
+// Positive normal arguments take these steps directly; the others take them
+// after a subnormal is scaled by 2^23 (k lowered by 23), or are 0, negative,
+// inf or NaN, where the hardware log2 gives the IEEE result (-inf, NaN, inf,
+// NaN).  Error bound: 1 ulp, the bound CUDA documents for logf (in float32
+// emulation of these steps: 0.92 ulp at most over every float in [1/16, 16)
+// and 4 M random normal floats); the GPU tests check it against log in FP64.
+// log_f32x2 takes the same steps for two lanes with the packed operations,
+// each rounded as the scalar one, so both give the same bits; a pair with an
+// argument that is not positive normal goes through log_f32 lane by lane.
+#define DFS_LOG_C0 -0x1.fffff8p-2f
+#define DFS_LOG_C1 0x1.555550p-2f
+#define DFS_LOG_C2 -0x1.000428p-2f
+#define DFS_LOG_C3 0x1.99a46ap-3f
+#define DFS_LOG_C4 -0x1.54279ep-3f
+#define DFS_LOG_C5 0x1.226922p-3f
+#define DFS_LOG_C6 -0x1.0f2d10p-3f
+#define DFS_LOG_C7 0x1.08782ap-3f
+#define DFS_LOG_C8 -0x1.38d522p-4f
+#define DFS_LN2_HI 0x1.62e400p-1f
+#define DFS_LN2_LO 0x1.7f7d1cp-20f
+#define DFS_SQRT_HALF_BITS 0x3f3504f3
+__device__ __forceinline__ float lg2_ftz(float v) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return r;
+}
+// positive, normal and finite
+__device__ __forceinline__ bool log_plain(float a) { return (u32)__float_as_int(a) - 0x00800000u < 0x7f000000u; }
+// k and m of a positive normal a (d: the bits of a less those of sqrt(1/2))
+__device__ __forceinline__ float log_k(int d) { return (float)(d >> 23); }
+__device__ __forceinline__ float log_m(int d) { return __int_as_float((d & 0x007fffff) + DFS_SQRT_HALF_BITS); }
+__device__ __forceinline__ float log_mk(float f, float kf) {
+  const float f2 = __fmul_rn(f, f);
+  float q = DFS_LOG_C8;
+  q = __fmaf_rn(q, f, DFS_LOG_C7);
+  q = __fmaf_rn(q, f, DFS_LOG_C6);
+  q = __fmaf_rn(q, f, DFS_LOG_C5);
+  q = __fmaf_rn(q, f, DFS_LOG_C4);
+  q = __fmaf_rn(q, f, DFS_LOG_C3);
+  q = __fmaf_rn(q, f, DFS_LOG_C2);
+  q = __fmaf_rn(q, f, DFS_LOG_C1);
+  q = __fmaf_rn(q, f, DFS_LOG_C0);
+  const float lm = __fmaf_rn(f2, q, f);
+  return __fmaf_rn(kf, DFS_LN2_HI, __fmaf_rn(kf, DFS_LN2_LO, lm));
+}
+static __device__ __noinline__ float log_rare(float a) {
+  const bool sub = a < 0x1p-126f;                 // subnormals of either sign become normal
+  const float x = sub ? __fmul_rn(a, 0x1p23f) : a;
+  if (!log_plain(x)) return lg2_ftz(x);           // +-0 -> -inf, < 0 -> NaN, inf -> inf, NaN -> NaN
+  const int d = __float_as_int(x) - DFS_SQRT_HALF_BITS;  // x: a positive subnormal scaled by 2^23
+  return log_mk(__fsub_rn(log_m(d), 1.0f), __fsub_rn(log_k(d), 23.0f));
+}
+__device__ __forceinline__ float log_f32(float a) {
+  if (!log_plain(a)) return log_rare(a);
+  const int d = __float_as_int(a) - DFS_SQRT_HALF_BITS;
+  return log_mk(__fsub_rn(log_m(d), 1.0f), log_k(d));
+}
+__device__ __forceinline__ float2 log_f32x2(float a0, float a1) {
+  if (!(log_plain(a0) && log_plain(a1))) return make_float2(log_f32(a0), log_f32(a1));
+  const int d0 = __float_as_int(a0) - DFS_SQRT_HALF_BITS, d1 = __float_as_int(a1) - DFS_SQRT_HALF_BITS;
+  const float2 kf = make_float2(log_k(d0), log_k(d1));
+  const float2 f = __fadd2_rn(make_float2(log_m(d0), log_m(d1)), f2(-1.0f));
+  const float2 ff = __fmul2_rn(f, f);
+  float2 q = f2(DFS_LOG_C8);
+  q = __ffma2_rn(q, f, f2(DFS_LOG_C7));
+  q = __ffma2_rn(q, f, f2(DFS_LOG_C6));
+  q = __ffma2_rn(q, f, f2(DFS_LOG_C5));
+  q = __ffma2_rn(q, f, f2(DFS_LOG_C4));
+  q = __ffma2_rn(q, f, f2(DFS_LOG_C3));
+  q = __ffma2_rn(q, f, f2(DFS_LOG_C2));
+  q = __ffma2_rn(q, f, f2(DFS_LOG_C1));
+  q = __ffma2_rn(q, f, f2(DFS_LOG_C0));
+  const float2 lm = __ffma2_rn(ff, q, f);
+  return __ffma2_rn(kf, f2(DFS_LN2_HI), __ffma2_rn(kf, f2(DFS_LN2_LO), lm));
+}
+__device__ __forceinline__ float op_log(float a) { return log_f32(a); }
 __device__ __forceinline__ double erf_mag(double a) { return erf(fabs(a)); }
 __device__ __forceinline__ float erf_sign(float m, float a) { return copysignf(m, a); }
 __device__ __forceinline__ double erf_sign(double m, double a) { return copysign(m, a); }

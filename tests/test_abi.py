@@ -146,6 +146,7 @@ def test_black_scholes_plan_fuses_everything():
     assert packed > 0 and results % 4 == 0 and "ld4" in src and "st4" in src
     mags = src.count("erf_mag(") + 2 * src.count("erf_mag2(")      # erf_mag2 serves two lanes
     assert mags * 2 == results
+    assert "log_f32x2(" in src                                         # LOG of S/K, two lanes at a time
     # only the two outputs are stored: the 21 temporaries live in registers
     assert src.count("st4(") == src.count("st4(r3") + src.count("st4(r4")
 
