@@ -942,6 +942,8 @@ def measure(args, workload, env, steps, warmup, cpu_budget=(10.0, 8.0)) -> dict:
         roofline["traffic"] = ctr["dram_bytes_per_iteration"]
     elif ctr and workload == "batched" and cfg["count"] == 256:
         roofline["traffic"] = ctr["dram_bytes_per_launch"]
+    elif ctr and workload == "jacobi" and cfg["N"] == 8190:
+        roofline["traffic"] = ctr["dram_bytes_per_launch"]
     fp64_ops = None
     if workload == "cg":
         fp64_ops = nnz + 8 * nn

@@ -21,11 +21,11 @@ BLACK_SCHOLES = dict(n=1 << 26, seed=1, r=0.02, sigma=0.3, tile=16384, block=512
 # CG: 2-D 5-point Poisson on a 256x256 grid, 50 iterations, FP64 values,
 # int32 indices, x* ~ U[-1,1] (seed 0), b = A x*, x0 = 0; five iterations
 # share one flush window (one persistent launch) in the captured solve
-CG = dict(m=256, iters=50, seed=0, tile=512, block=256, unroll=2, iters_per_flush=5, window_size=1024,
+CG = dict(m=256, iters=50, seed=0, tile=512, block=256, unroll=1, iters_per_flush=5, window_size=1024,
           # ncu counters of the steady five-iteration window kernel named
           # `kernel` (this launch shape): DRAM bytes per iteration; the rest of
           # the traffic is served by L2 (profiles/)
-          counters=dict(kernel="dfs_kf956504968f200ce", dram_bytes_per_iteration=5.865472e6 / 5))
+          counters=dict(kernel="dfs_kd2a6167401cf8ba5", dram_bytes_per_iteration=5.851904e6 / 5))
 
 # Batched CG: 256 independent solves of uneven size (half 2-D Poisson with m
 # log-uniform in [32, 1024], half random diagonally dominant SPD with n
@@ -43,7 +43,10 @@ BATCHED_CG = dict(count=256, seed=4, iters=100, dtype="f64", tile_max=2048, min_
 
 # Jacobi: Fig. 1 stencil on an 8192x8192 FP32 grid (8190^2 interior),
 # 200 sweeps, interior U[0,1] (seed 2), boundary 1.0
-JACOBI = dict(N=8190, sweeps=200, seed=2, rows=8, block=512, unroll=8, sweeps_per_flush=1)
+JACOBI = dict(N=8190, sweeps=200, seed=2, rows=16, block=512, unroll=4, sweeps_per_flush=1,
+              # ncu counters (one-pass metrics, full size) of the sweep kernel
+              # named `kernel`: DRAM bytes (read + write) of one launch (one sweep)
+              counters=dict(kernel="dfs_kdfa35ea3aa3ff44c", dram_bytes_per_launch=540.49e6 + 487.49e6))
 
 # Serving: Poisson arrivals (exponential gaps, mean 2 ms, seed 3) of CG and
 # BiCGSTAB solves on 3-D 7-point Poisson operators (m from a log-spaced
