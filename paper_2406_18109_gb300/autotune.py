@@ -8,7 +8,11 @@ tuner changes the context's parameters between trials (dfs_set_launch_config
 and the front end's tiling), so the stores, matrices and solver state stay
 where they are: a trial advances the application's state, which the caller
 resets afterwards.  The search is coordinate descent: each parameter in turn
-takes the value of the fastest trial while the others stay fixed.
+takes the value of the fastest trial while the others stay fixed.  A
+challenger replaces the incumbent only when it is faster by more than
+`margin` (1 % by default, about the step-to-step noise of a timed step), so
+candidates that tie within noise leave the starting setting in place and
+repeated runs settle on the same kernels.
 
 Tile and block size decide how reductions are split, so they fix the
 rounding of a result; the chosen configuration is kept in a JSON cache (keyed
@@ -67,7 +71,7 @@ def measure(rt, step, warmup: int = 1, reps: int = 3) -> float:
 
 
 def tune(rt, step, space: dict | None = None, warmup: int = 1, reps: int = 3, key: str | None = None,
-         cache_path: str | None = None, gpu: str = "") -> tuple[dict, list]:
+         cache_path: str | None = None, gpu: str = "", margin: float = 0.01) -> tuple[dict, list]:
     """Tunes rt for `step`; leaves rt configured with the best setting and
     returns (setting, trials) where trials is a list of (setting, ms)."""
     space = dict(space) if space else dict(DEFAULT_SPACE)
@@ -103,7 +107,7 @@ def tune(rt, step, space: dict | None = None, warmup: int = 1, reps: int = 3, ke
                 continue
             cand = dict(base, **{p: v})
             ms = trial(cand)
-            if ms < best_ms:
+            if ms < best_ms * (1.0 - margin):
                 best, best_ms = cand, ms
     apply(rt, best)
     if ck and cache_path:

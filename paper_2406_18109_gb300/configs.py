@@ -12,8 +12,8 @@ BLACK_SCHOLES = dict(n=1 << 26, seed=1, r=0.02, sigma=0.3, tile=16384, block=512
                      # thread instructions per option (smsp__inst_executed x 32
                      # / options; the kernel is bound by instruction issue) and
                      # DRAM bytes (read + write) of one launch at n = 2^26
-                     counters=dict(kernel="dfs_k7ba08b70d2427287", inst_per_option=110.89,
-                                   dram_bytes_per_launch=1304.48e6),
+                     counters=dict(kernel="dfs_k612b342bb8be269d", inst_per_option=111.89,
+                                   dram_bytes_per_launch=1304.50e6),
                      # end to end (host arrays): kernels on mapped host memory
                      # ("zero_copy") or copies pipelined in chunks over contexts
                      e2e_mode="zero_copy", e2e_chunk=1 << 23, e2e_contexts=2)
@@ -46,7 +46,7 @@ BATCHED_CG = dict(count=256, seed=4, iters=100, dtype="f64", tile_max=2048, min_
 JACOBI = dict(N=8190, sweeps=200, seed=2, rows=16, block=512, unroll=4, sweeps_per_flush=1,
               # ncu counters (one-pass metrics, full size) of the sweep kernel
               # named `kernel`: DRAM bytes (read + write) of one launch (one sweep)
-              counters=dict(kernel="dfs_kdfa35ea3aa3ff44c", dram_bytes_per_launch=540.49e6 + 487.49e6))
+              counters=dict(kernel="dfs_ka23239f399de85c0", dram_bytes_per_launch=540.48e6 + 487.56e6))
 
 # Serving: Poisson arrivals (exponential gaps, mean 2 ms, seed 3) of CG and
 # BiCGSTAB solves on 3-D 7-point Poisson operators (m from a log-spaced

@@ -418,16 +418,19 @@ void Gen::emit_vector_group(int g) {
   o << "    }\n";
 }
 
-// FP32 element-wise ADD, MUL, NCDF, ERF and LOG tasks run two lanes per
-// instruction (pk_add, pk_mul, pk_ncdf_*, erf_mag2, log_f32x2) when that
-// cannot change a bit.  The compiler contracts a packed product whose value
-// reaches a sum into a fused multiply-add, so a product (MUL, or NCDF, whose
-// last step multiplies), possibly negated or copied on the way, that a sum of
-// the body consumes (ADD, SUB, a SUM reduction) keeps both operations scalar.
-// ERF and LOG are neither products nor sums (inside, their products reach
-// sums only through explicit fused multiply-adds), so they always pair up.
-// Values loaded from memory or computed outside the body are not products of
-// the body.
+// FP32 element-wise ADD, NCDF, ERF and LOG tasks run two lanes per
+// instruction (pk_add, pk_ncdf_*, erf_mag2, log_f32x2) when that cannot change
+// a bit.  The compiler contracts a packed product whose value reaches a sum
+// into a fused multiply-add, so an NCDF (whose last step multiplies) whose
+// value, possibly negated or copied on the way, reaches a sum of the body
+// (ADD, SUB, a SUM reduction) keeps both operations scalar, and so does a sum
+// of a MUL.  ERF and LOG are neither products nor sums (inside, their products
+// reach sums only through explicit fused multiply-adds), so they always pair
+// up.  MUL itself stays on single lanes: a packed multiply saves an issue slot
+// but waits on the packed pipe, and measured on the fused Black-Scholes
+// window, multiplies on lane pairs made the kernel 0.9 % slower.  Values
+// loaded from memory or computed outside the body are not products of the
+// body.
 std::vector<char> Gen::packed_tasks(const Nest& n, int w) const {
   std::vector<char> pk(n.last - n.first, 0);
   if (w < 2 || w % 2) return pk;
@@ -459,8 +462,7 @@ std::vector<char> Gen::packed_tasks(const Nest& n, int w) const {
   for (int i = n.first; i < n.last; ++i) {
     const Task& t = S.tasks[i];
     if (t.scalar() || blocked[i - n.first] || space_arg(t).dtype != DFS_F32) continue;
-    pk[i - n.first] = t.op == DFS_OP_ADD || t.op == DFS_OP_MUL || t.op == DFS_OP_NCDF || t.op == DFS_OP_ERF ||
-                      t.op == DFS_OP_LOG;
+    pk[i - n.first] = t.op == DFS_OP_ADD || t.op == DFS_OP_NCDF || t.op == DFS_OP_ERF || t.op == DFS_OP_LOG;
   }
   return pk;
 }
@@ -711,8 +713,8 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
             } else {
               lanes[l].define(r0);
               lanes[l + 1].define(r1);
-              o << pad << "const float2 " << pr << " = " << (t.op == DFS_OP_ADD ? "pk_add(" : "pk_mul(") << val_of(l, 0)
-                << ", " << val_of(l + 1, 0) << ", " << val_of(l, 1) << ", " << val_of(l + 1, 1) << ");\n";
+              o << pad << "const float2 " << pr << " = pk_add(" << val_of(l, 0) << ", " << val_of(l + 1, 0) << ", "
+                << val_of(l, 1) << ", " << val_of(l + 1, 1) << ");\n";
             }
             o << pad << "const float " << r0 << " = " << pr << ".x;\n";
             o << pad << "const float " << r1 << " = " << pr << ".y;\n";

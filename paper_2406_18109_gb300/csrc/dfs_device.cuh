@@ -242,13 +242,10 @@ __device__ __forceinline__ double op_ncdf(double a) { return ncdf_of_erf(op_erf(
 // it.  The compiler may contract a packed product whose only use is a packed
 // or scalar sum into one fused multiply-add, whatever rounding the source
 // asks for (measured on GB300), which rounds once where the unfused tasks
-// round twice; so the code generator packs an operation only when no product
+// round twice; so the code generator pairs an operation only when no product
 // of the body feeds a sum of the body (add, subtract, SUM reduction).
 __device__ __forceinline__ float2 pk_add(float a0, float a1, float b0, float b1) {
   return __fadd2_rn(make_float2(a0, a1), make_float2(b0, b1));
-}
-__device__ __forceinline__ float2 pk_mul(float a0, float a1, float b0, float b1) {
-  return __fmul2_rn(make_float2(a0, a1), make_float2(b0, b1));
 }
 // ncdf_arg and ncdf_of_erf of two lanes
 __device__ __forceinline__ float2 pk_ncdf_arg(float a0, float a1) {
