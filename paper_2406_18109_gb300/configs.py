@@ -12,8 +12,8 @@ BLACK_SCHOLES = dict(n=1 << 26, seed=1, r=0.02, sigma=0.3, tile=16384, block=512
                      # thread instructions per option (smsp__inst_executed x 32
                      # / options; the kernel is bound by instruction issue) and
                      # DRAM bytes (read + write) of one launch at n = 2^26
-                     counters=dict(kernel="dfs_k612b342bb8be269d", inst_per_option=111.89,
-                                   dram_bytes_per_launch=1304.50e6),
+                     counters=dict(kernel="dfs_k612b342bb8be269d", inst_per_option=112.03,
+                                   dram_bytes_per_launch=1306.58e6),
                      # end to end (host arrays): kernels on mapped host memory
                      # ("zero_copy") or copies pipelined in chunks over contexts
                      e2e_mode="zero_copy", e2e_chunk=1 << 23, e2e_contexts=2)

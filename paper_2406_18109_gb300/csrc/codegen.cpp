@@ -508,6 +508,7 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
   int64_t flat_cells = 1;  // elements of a flat range (constant)
   for (int d = 0; d < nd; ++d) {
     if (sa.part.kind == 0) {
+      flat_cells *= std::max<int64_t>(0, sa.part.vhi[d] - sa.part.vlo[d]);
       o << ind << "  const i64 ext" << d << " = " << (sa.part.vhi[d] - sa.part.vlo[d]) << "LL;\n";
     } else if (flat) {
       const int64_t cnt = first.dom[sa.part.proj[d]];
@@ -522,6 +523,7 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
         << "LL), " << sa.part.vlo[d] << "LL);\n";
     }
   }
+  if (flat) kc.min_flat_cells = std::min(kc.min_flat_cells, flat_cells);
   // ---- classify accesses
   // reads from memory: distinct (root, partition) read before any in-nest write of it
   struct Rd { std::string key; const Arg* a; std::string var; bool ro; };
