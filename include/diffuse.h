@@ -161,11 +161,9 @@ typedef struct {
   int32_t window_size;       /* tasks buffered before the window is analysed (>= 1) */
   void *stream;              /* cudaStream_t to use; NULL = the context creates one */
   int32_t block_threads;     /* threads per CTA: 128, 256, 512 or 1024 (0 = 256) */
-  int32_t ctas_per_sm;       /* CTAs per SM (0 = as many as fit): sizes the grid (one wave
-                              * of resident CTAs; two waves for kernels of large flat
-                              * sweeps with no grid barrier and no reduction) and, when > 0, is
-                              * the kernels' minimum resident CTAs per SM, which caps
-                              * their registers per thread */
+  int32_t ctas_per_sm;       /* CTAs per SM (0 = as many as fit): sizes the grid and, when
+                              * > 0, is the kernels' minimum resident CTAs per SM, which
+                              * caps their registers per thread */
   int32_t unroll;            /* vectors per thread per loop trip, 1..8 (0 = 2) */
   double barrier_timeout_s;  /* grid-barrier spin limit in seconds (0 = 2.0) */
   const char *cache_dir;     /* on-disk cubin cache directory, or NULL */

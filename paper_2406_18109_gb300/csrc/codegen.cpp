@@ -523,7 +523,6 @@ void Gen::emit_nest(int g, const Nest& n, const std::string& ptvar, bool flat) {
         << "LL), " << sa.part.vlo[d] << "LL);\n";
     }
   }
-  if (flat) kc.min_flat_cells = std::min(kc.min_flat_cells, flat_cells);
   // ---- classify accesses
   // reads from memory: distinct (root, partition) read before any in-nest write of it
   struct Rd { std::string key; const Arg* a; std::string var; bool ro; };

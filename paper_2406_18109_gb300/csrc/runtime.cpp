@@ -561,19 +561,7 @@ int build_window(dfs_ctx* c, const WindowInfo& wi, std::unique_ptr<CachedWindow>
     if (!all_scalar) want = kc.has_points ? kc.max_points : (kc.has_flat ? INT64_MAX : 1);
     int per_sm = comp->occupancy > 0 ? comp->occupancy : 1;
     if (c->cfg.ctas_per_sm > 0) per_sm = std::min(per_sm, c->cfg.ctas_per_sm);
-    int64_t cap = (int64_t)per_sm * c->sms;
-    // a kernel of flat sweeps with no grid barrier and no reduction, large
-    // enough that every CTA of two waves takes at least 8 trips of its
-    // grid-stride loop, launches two waves of resident CTAs: the second
-    // wave's CTAs start as the first wave's finish and even out the tail.
-    // The grid changes which thread takes an element, never a result.
-    // Measured on the fused Black-Scholes window (2^26 options): 0.2618 ms at
-    // one wave, 0.2590 at two, 0.2592 at four, 0.2647 at eight.  Small sweeps
-    // (the unfused CG tasks, 65,536 elements) only pay for the extra CTAs.
-    const int64_t per_trip = (int64_t)spec.block * std::max(1, spec.unroll) * 4;
-    if (!L.cooperative && !kc.has_points && kc.nred == 0 && kc.has_flat &&
-        kc.min_flat_cells / (2 * cap) >= 8 * per_trip)
-      cap *= 2;
+    const int64_t cap = (int64_t)per_sm * c->sms;
     if (L.cooperative && comp->occupancy <= 0) return fail(c, DFS_ERR_CUDA, "generated kernel cannot be resident for a cooperative launch");
     L.grid = (int)std::max<int64_t>(1, std::min(want, cap));
     L.nptr = kc.nptr;

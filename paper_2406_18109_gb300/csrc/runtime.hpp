@@ -184,7 +184,6 @@ struct KernelCode {
   int64_t max_points = 1;
   bool has_flat = false;    // some group sweeps a flat range
   bool has_points = false;  // some group deals points to CTAs (max_points of them)
-  int64_t min_flat_cells = INT64_MAX;  // elements of the smallest flat sweep (has_flat)
   int nbarriers = 0;
   std::vector<int64_t> red_points;  // points of each reduction slot
   std::vector<double> imms;         // immediate values in parameter order
