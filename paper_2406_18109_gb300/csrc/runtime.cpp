@@ -133,6 +133,7 @@ struct dfs_ctx {
     uint64_t blob[8] = {};
     int64_t groups = 0;
     std::string name;
+    const std::string* source = nullptr;  // the kernel's source (batch cache entries live as long as the context)
   };
   LastBatch lastb;
   // dfs_read_scalars: descriptors (pinned) and gathered values (device)
@@ -989,6 +990,7 @@ int flush_batch(dfs_ctx* c) {
     c->bcache[ckey] = std::move(ne);
   }
   const BatchCode& bc = be->code;
+  c->last_source = bc.source;  // cache hits too: the source of the most recent launch
   std::map<int64_t, int> ci0;
   for (size_t k = 0; k < canon[0].size(); ++k) ci0[canon[0][k]] = (int)k;
   const std::vector<int>& ptr_canon = be->ptr_canon;
@@ -1098,6 +1100,7 @@ int flush_batch(dfs_ctx* c) {
   L.ninst = K;
   L.groups = (int64_t)p0.groups.size() * K;
   L.name = bc.name;
+  L.source = &bc.source;
   std::memcpy(L.blob, blob, sizeof blob);
   c->lastb.ok = false;
   const int lrc = launch_batched(c, L);
@@ -2063,6 +2066,7 @@ int dfs_batch_repeat(dfs_ctx* c, int32_t n) {
     const int rc = flush(c);
     if (rc) return rc;
     if (!c->lastb.ok) return fail(c, DFS_ERR_STATE, "no steady batch to repeat");
+    if (n > 0 && c->lastb.source) c->last_source = *c->lastb.source;
     for (int32_t i = 0; i < n; ++i) {
       const int lrc = launch_batched(c, c->lastb);
       if (lrc) {

@@ -257,3 +257,21 @@ def test_batched_barrier_timeout_is_reported_and_next_batch_is_right():
     xa, _ = _run(specs, 6, batched=False)
     for i in range(len(specs)):
         assert np.array_equal(xb[i].view(np.uint64), xa[i].view(np.uint64))
+
+
+def test_kernel_source_names_the_batch_on_cache_hits():
+    """The source reported for the most recent launch is the batched kernel's
+    also when that kernel comes from the batch cache after another kernel ran
+    in between, and after steady repeats."""
+    with gpu_runtime("persistent", tile=512) as rt:
+        probs = _problems(rt, SPECS[:3])
+        W.batched_cg_iteration(rt, probs)                 # generated here
+        first = rt.kernel_source()
+        assert "find_inst" in first
+        (A.full(rt, (1000,), 1.0) * 3.0).numpy()          # a single-window launch in between
+        assert "find_inst" not in rt.kernel_source()
+        W.batched_cg_iteration(rt, probs)                 # a batch-cache hit
+        assert rt.kernel_source() == first
+        rt.batch_repeat(2)                                # steady repeats of the same kernel
+        assert rt.kernel_source() == first
+        assert rt.stats()["batch_fallbacks"] == 0
