@@ -682,8 +682,10 @@ def run_serving(args, env):
     seed = D.rank_seed(cfg["seed"], rank)
     count = args.requests or cfg["count"]
     peaks = load_peaks()
-    rt = A.Runtime(device=dev, stream=stream.cuda_stream, time_launches=True, tile=cfg["tile"],
-                   block=cfg["block"], unroll=cfg["unroll"], sms=sms, cache_dir=cache)
+    # command-line overrides of the launch shape (tuning), as for the other workloads
+    shape = {k: getattr(args, k) or cfg[k] for k in ("tile", "block", "unroll")}
+    rt = A.Runtime(device=dev, stream=stream.cuda_stream, time_launches=True, tile=shape["tile"],
+                   block=shape["block"], unroll=shape["unroll"], sms=sms, cache_dir=cache)
 
     def server():
         return SV.Server(rt, inputs.poisson3d_csr, budget_bytes=int(cfg["budget_gb"] * 1e9), tol=cfg["tol"],
@@ -779,7 +781,7 @@ def run_serving(args, env):
             "config": {"workload": WORKLOAD["serve"], "requests": n, "l2": "inputs larger than L2",
                        "launch": "continuous batching: one batched persistent launch per solver kind per "
                                  "iteration, dfs_batch_repeat within a tick",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}", "shape": shape},
             "p50_ms": offered["p50_ms"], "p99_ms": offered["p99_ms"],
             "e2e": {"value": value, "unit": "requests/s",
                     "h2d_bytes_per_step": offered["h2d_bytes"] / max(1, n),

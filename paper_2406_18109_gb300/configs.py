@@ -55,4 +55,4 @@ JACOBI = dict(N=8190, sweeps=200, seed=2, rows=16, block=512, unroll=4, sweeps_p
 # iterations per tick; at most 64 active solves per kind.  `count` requests
 # per run (a bounded stand-in for an open-ended stream).
 SERVING = dict(count=240, seed=3, mean_gap_ms=2.0, budget_gb=120, tol=1e-8, iters_per_tick=8, max_active=64,
-               tile=2048, block=256, unroll=2, load_fraction=0.8)
+               tile=4096, block=256, unroll=2, load_fraction=0.8)
