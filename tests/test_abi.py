@@ -675,3 +675,30 @@ def test_spmv_windows_cover_the_rows(kind, elem):
         B.dfs_spmv_windows(rp, col, n, 0, elem)        # no tile
     with pytest.raises(B.DfsError):
         B.dfs_spmv_windows(rp, col, n, 256, 2)         # element size
+
+
+def test_lane_pair_decisions():
+    """Which FP32 tasks of a vector body run on lane pairs (generated code, no
+    device): adds, NCDF, ERF and LOG pair up; multiplies stay on single lanes;
+    a sum that a product (MUL, or NCDF through NEG) reaches stays scalar, and
+    so does that NCDF."""
+    rt = rt0(tile=1024)
+    n = 8195
+    a, b, d = (rt.empty((n,), np.float32) for _ in range(3))
+    outs = [rt.empty((n,), np.float32) for _ in range(12)]
+    dom, _ = rt.layout((n,))
+    P = B.DFS_PRIV_R
+    stream = [("MUL", [a, b], 0), ("ADD", [outs[0], d], 1),        # v0 product, v1 its sum: scalar
+              ("ADD", [a, d], 2),                                  # v2 a sum of loads: pair
+              ("NCDF", [a], 3), ("NEG", [outs[3]], 4), ("SUB", [d, outs[4]], 5),   # v3..v5: NCDF reaches a sum
+              ("NCDF", [b], 6), ("MUL", [outs[6], b], 7),          # v6 NCDF into a product: pair; v7 MUL: single
+              ("ERF", [a], 8), ("LOG", [b], 9), ("ADD", [outs[8], 1.0], 10)]        # v8, v9, v10: pair
+    for op, ins, o in stream:
+        args = [x._arg(P) if not isinstance(x, float) else x for x in ins]
+        rt.submit(op, dom, args + [outs[o]._arg(B.DFS_PRIV_W)])
+    with pytest.raises(B.DfsError):
+        rt.flush()
+    src = rt.kernel_source()
+    paired = {k for k in range(11) if f"const float2 v{k}_" in src}
+    assert paired == {2, 6, 8, 9, 10}, paired
+    assert "pk_mul(" not in src and "log_f32x2(" in src and "erf_mag2(" in src
