@@ -518,6 +518,24 @@ class Arm:
                 rt.flush()
             self._tune(sweep, {"rows": [8, 16, 32], "block": [256, 512], "unroll": [4, 8], "ctas_per_sm": [0, 4, 6]},
                        f"jacobi-{cfg['N']}", 3, "ms_per_sweep")
+        if self.graph_mode:
+            # the step's sweeps (one window per sweep, memoised) issued once,
+            # then captured once and replayed per step, so no host issue
+            # sits between the kernels
+            per = cfg["sweeps_per_flush"]
+
+            def window():
+                for s in range(cfg["sweeps"]):
+                    W.jacobi_sweep(self.views)
+                    if (s + 1) % per == 0:
+                        rt.flush()
+                rt.flush()
+            window()
+            rt.capture_begin()
+            window()
+            self.graph = rt.capture_end()
+            self.kernel_name = kernel_name_of(rt)
+            self.step = self._cg_graph
         if self.e2e:
             hg = self._pin(grid)
             self.h2d = self.d2h = hg.nbytes
@@ -824,7 +842,7 @@ def measure(args, workload, env, steps, warmup, cpu_budget=(10.0, 8.0)) -> dict:
 
     # CG: the iteration windows are captured once (memoised windows + a CUDA
     # graph) and replayed; the Python-issued runs are reported beside them
-    graph = workload in ("cg", "batched", "bs")
+    graph = workload in ("cg", "batched", "bs", "jacobi")
 
     def arm(kw, steps, warmup, e2e=False, graph=graph, per_solve=False):
         a = Arm(workload, kw, torch, stream, e2e=e2e, graph=graph, per_solve=per_solve)
@@ -880,8 +898,9 @@ def measure(args, workload, env, steps, warmup, cpu_budget=(10.0, 8.0)) -> dict:
             extra["python_issued"] = {
                 "fused": {"value": nf["units"] / (nf["ms"] / 1e3), "ms_per_step": nf["ms"] / k2},
                 "unfused": {"value": nu["units"] / (nu["ms"] / 1e3), "ms_per_step": nu["ms"] / k2},
-                "note": ("each batch issued from Python (23 tasks + flush)" if workload == "bs" else
-                         "each iteration issued from Python (11 tasks + flush); host-bound")}
+                "note": {"bs": "each batch issued from Python (23 tasks + flush)",
+                         "jacobi": "each sweep issued from Python (6 tasks + flush)"}.get(
+                             workload, "each iteration issued from Python (11 tasks + flush); host-bound")}
     if not args.quick:
         # end to end through the public API: inputs from pinned host memory
         # and results back to it inside every timed step
@@ -922,10 +941,10 @@ def measure(args, workload, env, steps, warmup, cpu_budget=(10.0, 8.0)) -> dict:
     if graph:
         # launches replayed from a graph are not timed one by one: use the
         # replayed time per iteration (kernel plus the gap to the next node)
-        its = cfg.get("iters", 1)
+        its = cfg.get("iters", cfg.get("sweeps", 1))
         kern_ms = fused["ms"] / (steps * its)
         fused["dominant"] = {"batched": "batched CG iteration kernel", "cg": "CG iteration kernel",
-                             "bs": "fused Black-Scholes kernel"}[workload] + \
+                             "bs": "fused Black-Scholes kernel", "jacobi": "Jacobi sweep kernel"}[workload] + \
             ", graph replay (time per launch incl. the gap to the next)"
         fused["dominant_launches"] = steps * its
     achieved = alg_bytes / (kern_ms / 1e3) / 1e9 if kern_ms > 0 else 0.0
@@ -1002,6 +1021,8 @@ def measure(args, workload, env, steps, warmup, cpu_budget=(10.0, 8.0)) -> dict:
                        else "working set L2-resident (10 MB); no flush",
                        "launch": "persistent fused" + ((", each batch replayed from a CUDA graph of the memoised "
                                                          "window" if workload == "bs" else
+                                                         ", each step's sweeps replayed from a CUDA graph of the "
+                                                         "memoised sweep windows" if workload == "jacobi" else
                                                          ", each solve replayed from a CUDA graph of the memoised "
                                                          "iteration windows") if graph else ""),
                        "parallelism": f"replicas x{world}"},
